@@ -1,0 +1,40 @@
+"""FP64 CPU oracle for list-mode TOF-weighted MLEM (arXiv:1706.07075).
+
+TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py may import this package.  It shares no code with
+the CUDA library (paper_1706_07075_b300): the per-event arithmetic is plain C
+(oracle.c, FP64, one rounding per operation), the iteration is plain numpy
+(mlem.py), and the two sides meet only at seeded inputs.
+
+Parity status of each function (what pins it is in tests/test_oracle_*.py):
+  tof_sigma_mm ........ pinned (Sec. 2.5 prints sigma = 19.11 mm for 300 ps)
+  trace ............... pinned (brute-force per-voxel box intersection;
+                        analytic chord through the grid box)
+  system_row .......... pinned (closed-form truncated-Gaussian mass of the
+                        clipped window; unit sum inside the grid)
+  forward/backproject . pinned (dense matrix built by brute force; adjointness)
+  sensitivity ......... pinned (chord sums; brute force)
+  mlem ................ pinned (dense textbook MLEM on an 8x8x8 grid; the
+                        one-voxel closed form; conservation; monotone
+                        likelihood; nonnegativity)
+  region_codes ........ pinned (hand-built events at the boundaries; the
+                        one-or-two-regions property of Sec. 2.5)
+  region_slabs ........ pinned (the paper's 176-slice extended regions)
+  mlem_regions ........ pinned through mlem and region_codes; the stitched
+                        image's count total is a closed form (N events)
+"""
+from .core import (  # noqa: F401
+    Grid,
+    backproject,
+    count_visits,
+    forward,
+    region_codes,
+    region_members,
+    sensitivity,
+    system_row,
+    threads_used,
+    tof_sigma_mm,
+    tof_weight,
+    trace,
+)
+from .mlem import mlem, mlem_regions, region_bounds, region_slabs, slab_grid, stitch  # noqa: F401

@@ -1,0 +1,169 @@
+// The MLEM event pass (Sec. 2.4: list-mode TOF-weighted MLEM):
+//   p_i = sum_j a_ij lambda_j            forward projection (gather)
+//   r_i = w_i / p_i  (events with p_i = 0 are skipped)
+//   C_j += a_ij r_i                      backprojection (FP32 reductions)
+// fused in one kernel: one thread walks one event twice, the event's record
+// and walk setup staying in registers between the walks.  The same kernel
+// body, with the pass kind as a template argument, gives the standalone
+// forward and backward projectors.
+//
+// Work distribution: either a flat grid (one event per thread) or a
+// persistent grid of (SMs x blocks_per_sm) blocks in which each warp takes
+// `chunk` consecutive events at a time from a global counter.  Events of the
+// batched (region-divided) form are stored region by region; a thread looks
+// its region up in a shared-memory table of event ranges and slab grids.
+#include <algorithm>
+
+#include "recon_device.cuh"
+
+namespace recon {
+
+namespace {
+
+struct SharedTable {
+    int n;
+    long long ev_begin[kMaxRegions + 1];
+    GridDev grid[kMaxRegions];
+};
+
+__device__ __forceinline__ int find_region(const SharedTable& t, long long i)
+{
+    int r = 0;
+    while (r + 1 < t.n && i >= t.ev_begin[r + 1]) ++r;
+    return r;
+}
+
+template <int Fmt>
+__device__ __forceinline__ Event load_event(const PassArgs& a, long long i)
+{
+    if (Fmt == FMT_F32) return load_event_f32(static_cast<const float4*>(a.events), i);
+    return load_event_packed(static_cast<const int4*>(a.events), i, a.lattice);
+}
+
+__device__ __forceinline__ float gather(const PassArgs& a, bool bf16, long long j)
+{
+    if (bf16) {
+        unsigned short h = __ldg(reinterpret_cast<const unsigned short*>(a.lam_bf16) + j);
+        return __uint_as_float(((unsigned)h) << 16);
+    }
+    return __ldg(a.lam + j);
+}
+
+// One event; returns the weight it adds to N_eff (0 when p_i = 0).
+template <int Kind, int Fmt>
+__device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& t, long long i, bool bf16,
+                                          int& region)
+{
+    region = find_region(t, i);
+    const GridDev& g = t.grid[region];
+    Event e = load_event<Fmt>(a, i);
+    float3 c, u;
+    Walk w;
+    w.valid = false;
+    if (event_line(e, c, u)) w = make_walk(g, c, u, -a.tof.half_window, a.tof.half_window);
+    const long long base = g.vox_offset;
+    if (Kind == PASS_BACK) {
+        const float r = a.r_in[i];
+        if (r != 0.f)
+            walk<true>(g, a.tof, w, [&](int j, float m) {
+                if (m != 0.f) atomicAdd(a.C + base + j, m * r);
+            });
+        return 0.f;
+    }
+    float p = 0.f;
+    walk<true>(g, a.tof, w, [&](int j, float m) { p = fmaf(m, gather(a, bf16, base + j), p); });
+    if (Kind == PASS_FORWARD) {
+        a.p_out[i] = p;
+        return 0.f;
+    }
+    if (!(p > 0.f)) return 0.f;
+    const float r = e.w / p;
+    walk<true>(g, a.tof, w, [&](int j, float m) {
+        if (m != 0.f) atomicAdd(a.C + base + j, m * r);
+    });
+    return e.w;
+}
+
+template <int Kind, int Fmt, bool Persistent>
+__global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl, int chunk)
+{
+    __shared__ SharedTable t;
+    __shared__ float neff[kMaxRegions];
+    if (threadIdx.x == 0) t.n = tbl.n;
+    for (int k = threadIdx.x; k <= tbl.n; k += blockDim.x) t.ev_begin[k] = tbl.ev_begin[k];
+    for (int k = threadIdx.x; k < tbl.n; k += blockDim.x) {
+        t.grid[k] = tbl.grid[k];
+        neff[k] = 0.f;
+    }
+    __syncthreads();
+    const bool bf16 = a.lam_bf16 != nullptr;
+    const int lane = threadIdx.x & 31;
+    if (Persistent) {
+        for (;;) {
+            unsigned long long start = 0;
+            if (lane == 0) start = atomicAdd(a.work, (unsigned long long)chunk);
+            start = __shfl_sync(0xffffffffu, start, 0);
+            if ((long long)start >= a.n) break;
+            const long long end = min((long long)start + chunk, a.n);
+            for (long long i = (long long)start + lane; i < end; i += 32) {
+                int r;
+                float w = do_event<Kind, Fmt>(a, t, i, bf16, r);
+                if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
+            }
+        }
+    } else {
+        const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        if (i < a.n) {
+            int r;
+            float w = do_event<Kind, Fmt>(a, t, i, bf16, r);
+            if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
+        }
+    }
+    if (Kind == PASS_FUSED) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < t.n; k += blockDim.x)
+            a.partial[(long long)blockIdx.x * t.n + k] = (double)neff[k];
+    }
+}
+
+template <int Kind, int Fmt>
+cudaError_t launch_kind(const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl, int num_sms,
+                        cudaStream_t s)
+{
+    const int blocks = pass_blocks(cfg, a.n, num_sms);
+    if (blocks == 0) return cudaSuccess;
+    if (cfg.blocks_per_sm > 0)
+        k_event_pass<Kind, Fmt, true><<<blocks, cfg.threads, 0, s>>>(a, tbl, cfg.chunk);
+    else
+        k_event_pass<Kind, Fmt, false><<<blocks, cfg.threads, 0, s>>>(a, tbl, cfg.chunk);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int pass_blocks(const LaunchCfg& cfg, long long n, int num_sms)
+{
+    if (n <= 0) return 0;
+    if (cfg.blocks_per_sm > 0) {
+        long long want = (long long)num_sms * cfg.blocks_per_sm;
+        long long warps_needed = (n + cfg.chunk - 1) / cfg.chunk;
+        long long blocks_needed = (warps_needed + cfg.threads / 32 - 1) / (cfg.threads / 32);
+        return (int)std::max(1LL, std::min(want, blocks_needed));
+    }
+    return (int)((n + cfg.threads - 1) / cfg.threads);
+}
+
+cudaError_t launch_pass(PassKind kind, EventFmt fmt, const LaunchCfg& cfg, const PassArgs& a,
+                        const RegionTable& tbl, int num_sms, cudaStream_t s)
+{
+    if (fmt == FMT_F32) {
+        if (kind == PASS_FUSED) return launch_kind<PASS_FUSED, FMT_F32>(cfg, a, tbl, num_sms, s);
+        if (kind == PASS_FORWARD) return launch_kind<PASS_FORWARD, FMT_F32>(cfg, a, tbl, num_sms, s);
+        return launch_kind<PASS_BACK, FMT_F32>(cfg, a, tbl, num_sms, s);
+    }
+    if (kind == PASS_FUSED) return launch_kind<PASS_FUSED, FMT_PACKED>(cfg, a, tbl, num_sms, s);
+    if (kind == PASS_FORWARD) return launch_kind<PASS_FORWARD, FMT_PACKED>(cfg, a, tbl, num_sms, s);
+    return launch_kind<PASS_BACK, FMT_PACKED>(cfg, a, tbl, num_sms, s);
+}
+
+}  // namespace recon

@@ -1,0 +1,238 @@
+// Device-side building blocks of the list-mode TOF-MLEM projector for sm_103a.
+//
+// Geometry (Sec. 2.3 of arXiv:1706.07075, "TOF kernel"; exact voxel
+// intersections after Siddon): event i has endpoints P1, P2, unit direction
+// u = (P1 - P2)/|P1 - P2|, midpoint M and TOF offset d, so the most likely
+// annihilation point is c = M + d u.  The walker parameterises the line by
+// tau = t - d, the signed distance from c, which keeps every kernel argument
+// small (|tau| <= K sigma) and FP32-precise.  Voxel (ix,iy,iz) is the
+// half-open box [o + i v, o + (i+1) v); linear index ix + nx (iy + ny iz).
+//
+// System element of a voxel piece [tau_a, tau_b] (Sec. 2.3: Gaussian kernel
+// whose weights sum to one; truncated at +-K sigma and renormalised):
+//     a = [Phi(tau_b/sigma) - Phi(tau_a/sigma)] / (2 Phi(K) - 1).
+// It is evaluated from signed tails g(tau) = sign(tau) erfc(|tau|/(sigma
+// sqrt 2)):  Phi(b) - Phi(a) = ((s_b - s_a) + (g_a - g_b)) / 2, which keeps
+// full FP32 relative precision in both tails of the window.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "recon_kernels.h"
+
+namespace recon {
+
+using GridDev = GridH;
+using TofDev = TofH;
+
+// Event as the walker sees it.
+struct Event {
+    float3 p1, p2;
+    float d, w;
+};
+
+// Resident F32 layout: two float4 per event, (x1,y1,z1,d) and (x2,y2,z2,w),
+// so a thread's event arrives in two 16-byte loads and a warp's in 1 KB.
+__device__ __forceinline__ Event load_event_f32(const float4* __restrict__ ev, long long i)
+{
+    float4 a = __ldg(ev + 2 * i);
+    float4 b = __ldg(ev + 2 * i + 1);
+    Event e;
+    e.p1 = make_float3(a.x, a.y, a.z);
+    e.p2 = make_float3(b.x, b.y, b.z);
+    e.d = a.w;
+    e.w = b.w;
+    return e;
+}
+
+// Packed layout: 16 bytes per event, int16 endpoints on a lattice, FP16 d,
+// FP16 weight: one 16-byte load per thread.
+__device__ __forceinline__ Event load_event_packed(const int4* __restrict__ ev, long long i, float lattice)
+{
+    int4 r = __ldg(ev + i);
+    Event e;
+    e.p1 = make_float3((float)(short)(r.x & 0xFFFF) * lattice, (float)(short)(r.x >> 16) * lattice,
+                       (float)(short)(r.y & 0xFFFF) * lattice);
+    e.p2 = make_float3((float)(short)(r.y >> 16) * lattice, (float)(short)(r.z & 0xFFFF) * lattice,
+                       (float)(short)(r.z >> 16) * lattice);
+    e.d = __half2float(__ushort_as_half((unsigned short)(r.w & 0xFFFF)));
+    e.w = __half2float(__ushort_as_half((unsigned short)((unsigned)r.w >> 16)));
+    return e;
+}
+
+// Signed tail of the Gaussian at tau: sign(tau) * erfc(|tau| / (sigma sqrt 2)).
+struct Tail {
+    float g, s;
+};
+
+__device__ __forceinline__ Tail tail_at(float tau, float inv_sigma_sqrt2)
+{
+    Tail t;
+    t.s = tau >= 0.f ? 1.f : -1.f;
+    t.g = t.s * erfcf(fabsf(tau) * inv_sigma_sqrt2);
+    return t;
+}
+
+// Per-event walk state after clipping the line to the grid box and the TOF
+// window.  Everything the two walks (forward, back) need is here.
+struct Walk {
+    float tau_in, tau_out;    // clipped parameter range (relative to c)
+    int ix, iy, iz;           // voxel containing the start
+    int sx, sy, sz;           // +1 / -1 / 0 per axis
+    float t0x, t0y, t0z;      // tau of the first plane crossing per axis (inf if parallel)
+    float dtx, dty, dtz;      // tau between successive crossings per axis
+    bool valid;
+};
+
+// Set up the walk of segment [tau_lo, tau_hi] of the line through `c` with
+// unit direction `u` (tau measured from c).  Slab method for the box, then the
+// start voxel and the first crossing on each axis.  The first crossing is
+// expressed relative to c once, and later crossings as first + m * step, so
+// plane positions carry no accumulated rounding.
+__device__ __forceinline__ Walk make_walk(const GridDev& g, float3 c, float3 u, float tau_lo, float tau_hi)
+{
+    Walk w;
+    float a = tau_lo, b = tau_hi;
+    const float lo[3] = {g.ox, g.oy, g.oz};
+    const float v[3] = {g.vx, g.vy, g.vz};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const float cc[3] = {c.x, c.y, c.z};
+    const float uu[3] = {u.x, u.y, u.z};
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float hi = lo[k] + (float)n[k] * v[k];
+        if (uu[k] == 0.f) {
+            ok = ok && (cc[k] >= lo[k]) && (cc[k] < hi);
+        } else {
+            float t0 = (lo[k] - cc[k]) / uu[k];
+            float t1 = (hi - cc[k]) / uu[k];
+            a = fmaxf(a, fminf(t0, t1));
+            b = fminf(b, fmaxf(t0, t1));
+        }
+    }
+    w.valid = ok && (a < b);
+    w.tau_in = a;
+    w.tau_out = b;
+    int idx[3], st[3];
+    float t0[3], dt[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float x = fmaf(a, uu[k], cc[k]);
+        float fi = floorf((x - lo[k]) / v[k]);
+        fi = fminf(fmaxf(fi, 0.f), (float)(n[k] - 1));   // also maps NaN of an invalid walk to 0
+        int i = (int)fi;
+        idx[k] = i;
+        if (uu[k] > 0.f) {
+            st[k] = 1;
+            float plane = lo[k] + (float)(i + 1) * v[k];
+            t0[k] = (plane - cc[k]) / uu[k];
+            dt[k] = v[k] / uu[k];
+        } else if (uu[k] < 0.f) {
+            st[k] = -1;
+            float plane = lo[k] + (float)i * v[k];
+            t0[k] = (plane - cc[k]) / uu[k];
+            dt[k] = -v[k] / uu[k];
+        } else {
+            st[k] = 0;
+            t0[k] = __int_as_float(0x7f800000);  // +inf: never crossed
+            dt[k] = 0.f;
+        }
+    }
+    w.ix = idx[0]; w.iy = idx[1]; w.iz = idx[2];
+    w.sx = st[0]; w.sy = st[1]; w.sz = st[2];
+    w.t0x = t0[0]; w.t0y = t0[1]; w.t0z = t0[2];
+    w.dtx = dt[0]; w.dty = dt[1]; w.dtz = dt[2];
+    return w;
+}
+
+// Line of an event: c = M + d u and u; returns false for a degenerate LOR.
+__device__ __forceinline__ bool event_line(const Event& e, float3& c, float3& u)
+{
+    float dx = e.p1.x - e.p2.x, dy = e.p1.y - e.p2.y, dz = e.p1.z - e.p2.z;
+    float D = sqrtf(dx * dx + dy * dy + dz * dz);
+    if (!(D > 0.f) || !(D < 1e30f) || !(fabsf(e.d) < 1e30f)) return false;
+    float inv = 1.f / D;
+    u = make_float3(dx * inv, dy * inv, dz * inv);
+    c = make_float3(fmaf(e.d, u.x, 0.5f * (e.p1.x + e.p2.x)), fmaf(e.d, u.y, 0.5f * (e.p1.y + e.p2.y)),
+                    fmaf(e.d, u.z, 0.5f * (e.p1.z + e.p2.z)));
+    return true;
+}
+
+// Siddon walk over the voxel pieces of a prepared Walk.  `visit(j, a)` gets
+// the linear voxel index (relative to the grid) and the TOF mass of the piece.
+// With Weighted = false the mass is the piece length in mm (sensitivity).
+// The loop ends at tau_out, after nx+ny+nz+2 pieces at most, or when rounding
+// would step outside the grid (the remaining sliver is dropped), so every
+// index handed to `visit` lies inside the grid.
+template <bool Weighted, class Visit>
+__device__ __forceinline__ void walk(const GridDev& g, const TofDev& tof, const Walk& w, Visit&& visit)
+{
+    if (!w.valid) return;
+    int ix = w.ix, iy = w.iy, iz = w.iz;
+    const int sy_lin = w.sy * g.nx;
+    const int sz_lin = w.sz * g.nx * g.ny;
+    int j = ix + g.nx * (iy + g.ny * iz);
+    float mx = 0.f, my = 0.f, mz = 0.f;
+    float tx = w.t0x, ty = w.t0y, tz = w.t0z;
+    float tau = w.tau_in;
+    Tail cur;
+    if (Weighted) cur = tail_at(tau, tof.inv_sigma_sqrt2);
+    const int max_steps = g.nx + g.ny + g.nz + 2;
+    for (int step = 0; step < max_steps; ++step) {
+        float tn = fminf(fminf(tx, ty), tz);
+        bool last = tn >= w.tau_out;
+        tn = fmaxf(fminf(tn, w.tau_out), tau);
+        float a;
+        if (Weighted) {
+            Tail nxt = tail_at(tn, tof.inv_sigma_sqrt2);
+            a = tof.half_inv_norm * ((nxt.s - cur.s) + (cur.g - nxt.g));
+            cur = nxt;
+        } else {
+            a = tn - tau;
+        }
+        visit(j, a);
+        if (last) break;
+        tau = tn;
+        if (tx <= ty && tx <= tz) {
+            ix += w.sx; j += w.sx; mx += 1.f; tx = fmaf(mx, w.dtx, w.t0x);
+            if ((unsigned)ix >= (unsigned)g.nx) break;
+        } else if (ty <= tz) {
+            iy += w.sy; j += sy_lin; my += 1.f; ty = fmaf(my, w.dty, w.t0y);
+            if ((unsigned)iy >= (unsigned)g.ny) break;
+        } else {
+            iz += w.sz; j += sz_lin; mz += 1.f; tz = fmaf(mz, w.dtz, w.t0z);
+            if ((unsigned)iz >= (unsigned)g.nz) break;
+        }
+    }
+}
+
+// Warp-wide sum.
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of a double; result valid in thread 0.  `sh` holds 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = lane < (int)((blockDim.x + 31) >> 5) ? sh[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+}  // namespace recon

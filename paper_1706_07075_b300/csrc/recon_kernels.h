@@ -1,0 +1,105 @@
+// Host-visible launch interface of the CUDA kernels (internal to librecon).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace recon {
+
+constexpr int kMaxRegions = 64;
+
+// Grid of one image (or region slab): nx*ny*nz voxels of (vx,vy,vz) mm from
+// the low corner (ox,oy,oz); vox_offset places it in a shared image buffer.
+struct GridH {
+    int nx, ny, nz;
+    float vx, vy, vz;
+    float ox, oy, oz;
+    long long vox_offset;
+};
+
+// TOF kernel constants: half_window = K sigma (mm), inv_sigma_sqrt2 =
+// 1/(sigma sqrt 2), half_inv_norm = 0.5 / erf(K / sqrt 2).
+struct TofH {
+    float half_window, inv_sigma_sqrt2, half_inv_norm;
+};
+
+// Per-region grid and event range for the batched pass (plain = 1 region).
+struct RegionTable {
+    int n;
+    long long ev_begin[kMaxRegions + 1];
+    GridH grid[kMaxRegions];
+};
+
+enum EventFmt { FMT_F32 = 0, FMT_PACKED = 1 };
+enum PassKind { PASS_FUSED = 0, PASS_FORWARD = 1, PASS_BACK = 2 };
+
+struct LaunchCfg {
+    int threads;       // threads per block (64, 128, 256)
+    int blocks_per_sm; // persistent grid when > 0; flat one-event-per-thread grid when 0
+    int chunk;         // events per work-queue grab (persistent), multiple of 32
+};
+
+struct PassArgs {
+    const void* events;          // float4 pairs (FMT_F32) or int4 records (FMT_PACKED)
+    long long n;
+    float lattice;
+    const float* lam;            // FP32 image (gather source unless lam_bf16 is set)
+    const uint16_t* lam_bf16;    // optional BF16 copy for the forward gather
+    float* C;                    // backprojection accumulator
+    float* p_out;                // PASS_FORWARD: p_i
+    const float* r_in;           // PASS_BACK: r_i
+    double* partial;             // PASS_FUSED: per block and region, sum of w_i over events with p_i > 0
+    unsigned long long* work;    // work-queue counter (persistent launches; zero before the launch)
+    TofH tof;
+};
+
+// Number of blocks a pass launch uses (its partial array has blocks * regions doubles).
+int pass_blocks(const LaunchCfg& cfg, long long n, int num_sms);
+cudaError_t launch_pass(PassKind kind, EventFmt fmt, const LaunchCfg& cfg, const PassArgs& a,
+                        const RegionTable& tbl, int num_sms, cudaStream_t s);
+
+// Sensitivity: s[j] += chord length of each LOR (FP64 accumulation).  lor6: six
+// planes of n floats (device).
+cudaError_t launch_sensitivity(const float* lor6, long long n, const GridH& g, double* s_acc, cudaStream_t st);
+
+// FP32 copy of s64 and per-block FP64 sums of s over {s > 0} in partial[blocks].
+cudaError_t launch_sens_finish(const double* s64, long long n_vox, float* s32, double* partial, int blocks,
+                               cudaStream_t st);
+// lam = s > 0 ? value : 0 over n voxels.
+cudaError_t launch_fill_masked(float* lam, const float* s32, long long n_vox, float value, cudaStream_t st);
+// Update per region (reg_vox: device array of region voxel offsets, n_regions+1):
+// lam <- s > 0 ? lam * C / s : 0; C <- 0; optional BF16 copy; partial[r * bpr + b] = sum s*lam.
+int update_blocks(long long n_vox);
+cudaError_t launch_update(float* lam, float* C, const float* s32, uint16_t* lam_bf16, const long long* reg_vox,
+                          int n_regions, double* partial, int blocks_per_region, cudaStream_t st);
+// hist[(k * R + r) * 2 + {0,1}] = {N_eff, sum s lambda} of region r after iteration k = *iter; ++*iter.
+cudaError_t launch_finalize(const double* pass_partial, int pass_blocks, const double* upd_partial,
+                            int upd_blocks_per_region, int n_regions, double* hist, int* iter_counter,
+                            int max_iter, cudaStream_t st);
+cudaError_t launch_to_bf16(const float* src, uint16_t* dst, long long n, cudaStream_t st);
+// Caller SoA planes (device) -> resident float4 pairs; weight nullable.
+cudaError_t launch_ingest_f32(const float* const* planes, const float* weight, long long n, float4* out,
+                              cudaStream_t st);
+cudaError_t launch_ingest_packed(const int4* rec, const float* weight, long long n, int4* out, cudaStream_t st);
+// Per-block FP64 sums of the event weights in partial[blocks].
+cudaError_t launch_reduce_weights(const float4* ev_f32, const int4* ev_packed, long long n, double* partial,
+                                  int blocks, cudaStream_t st);
+// Stitch (host arrays reg_vox, slab_lo, slab_hi): out = sum of each slab at its slices.
+cudaError_t launch_stitch(const float* slabs, const long long* reg_vox, const int* slab_lo, const int* slab_hi,
+                          int n_regions, int nx, int ny, int nz, float* out, cudaStream_t st);
+
+// Region division.  counts: n_tiles * (R + 1) ints; offsets: R + 2 int64
+// (offsets[R] = total, offsets[R+1] = events in three or more regions);
+// base: n_tiles * R int64.
+cudaError_t launch_region_codes(const float4* ev_f32, const int4* ev_packed, double lattice, long long n,
+                                const double* z_bounds, int n_regions, double shell, uint8_t* codes,
+                                int* block_counts, int tile, cudaStream_t st);
+cudaError_t launch_region_scan(const int* block_counts, int n_tiles, int n_regions, long long* offsets,
+                               long long* block_base, cudaStream_t st);
+cudaError_t launch_region_scatter(const uint8_t* codes, long long n, int n_regions, const long long* block_base,
+                                  int tile, int* idx, cudaStream_t st);
+cudaError_t launch_region_gather(const float4* ev_f32, const int4* ev_packed, const uint8_t* codes,
+                                 const int* idx, long long total, float4* out_f32, int4* out_packed,
+                                 cudaStream_t st);
+
+}  // namespace recon

@@ -1,0 +1,251 @@
+/*
+ * librecon: list-mode TOF-weighted MLEM on one NVIDIA B300 (sm_103a).
+ *
+ * The method is that of arXiv:1706.07075 (RPC-PET whole-body reconstruction):
+ * list-mode MLEM with a Gaussian time-of-flight (TOF) kernel along each line
+ * of response (Sec. 2.3, 2.4) and the TOF-assisted division of the events
+ * into body regions reconstructed independently and summed (Sec. 2.5).  The
+ * projector uses exact voxel intersections (Siddon) with the Gaussian
+ * integrated over each voxel piece.
+ *
+ * Conventions used by every call
+ * -------------------------------
+ * Units: mm and ps.  Image layout: FP32 (sensitivity: FP64), x fastest,
+ * linear index ix + nx*(iy + ny*iz).  Voxel (ix,iy,iz) covers the half-open
+ * box [o + i*v, o + (i+1)*v) per axis; (ox,oy,oz) is the low corner.
+ *
+ * Event i: endpoints P1 = (x1,y1,z1), P2 = (x2,y2,z2) and TOF offset d in mm,
+ * positive toward P1 (d = c (t2 - t1) / 2), so the most likely annihilation
+ * point is M + d u with M = (P1 + P2)/2 and u = (P1 - P2)/|P1 - P2|.
+ *
+ * Ownership: the caller owns every buffer it passes.  Inputs are copied (host
+ * pointers) or read (device pointers) during the call only; outputs are
+ * written before the call returns (the call synchronises its stream).  Output
+ * pointers may be host or device memory: the copy direction is inferred
+ * through unified virtual addressing.  The context owns its device images,
+ * its resident copy of the events and the sensitivity image.
+ *
+ * Errors: no call aborts or exits.  Every call returns a recon_status; the
+ * message of the last failure is available from recon_last_error().  A CUDA
+ * failure inside a call returns RECON_ECUDA.  Calls on one context must not
+ * overlap (one host thread at a time); different contexts are independent.
+ */
+#ifndef RECON_H
+#define RECON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct recon_ctx recon_ctx;
+
+typedef enum {
+    RECON_OK = 0,
+    RECON_EINVAL = 1,   /* bad argument: NULL required pointer, n < 0, bad grid, ... */
+    RECON_ENOMEM = 2,   /* a device or host allocation failed */
+    RECON_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    RECON_ETIMEOUT = 4, /* a bounded device-side wait expired (reserved) */
+    RECON_ESTATE = 5    /* call out of order (e.g. MLEM before the sensitivity image) */
+} recon_status;
+
+/* Cylindrical scanner (Sec. 2, 2.1: RPC-PET with a long axial field of view). */
+typedef struct {
+    double radius_mm;           /* > 0 */
+    double axial_len_mm;        /* > 0 */
+    double max_axial_angle_deg; /* acceptance, (0, 90]; Sec. 2.1 uses 45 */
+} recon_geometry;
+
+/* Image grid: nx*ny*nz voxels of (vx,vy,vz) mm, low corner (ox,oy,oz).
+ * nx*ny*nz must stay below 2^31. */
+typedef struct {
+    int32_t nx, ny, nz;
+    double vx, vy, vz;
+    double ox, oy, oz;
+} recon_grid;
+
+typedef enum {
+    RECON_EV_F32_SOA = 0,       /* planes[0..6] = x1,y1,z1,x2,y2,z2,d: n floats each */
+    RECON_EV_PACKED_I16_F16 = 1 /* planes[0] = n records of 8 x int16: x1,y1,z1,x2,y2,z2 as
+                                   multiples of lattice_mm, the FP16 bits of d, 0 (16 bytes each,
+                                   16-byte aligned) */
+} recon_event_fmt;
+
+typedef struct {
+    int32_t fmt;            /* recon_event_fmt */
+    int32_t on_device;      /* 1: planes (and weight) are device pointers; 0: host pointers */
+    int64_t n;              /* number of events, >= 0 */
+    const void* planes[7];  /* see recon_event_fmt; unused entries ignored */
+    double lattice_mm;      /* packed format only: lattice step (> 0), e.g. 0.05 */
+    const float* weight;    /* optional per-event weight w_i (NULL: all 1), same residency as planes */
+} recon_events;
+
+/* One body region: core slice range [z_lo, z_hi) of the image grid (Sec. 2.5). */
+typedef struct {
+    int32_t z_lo, z_hi;
+} recon_region;
+
+/* Launch configuration of the event pass (chosen by the autotuner unless set). */
+typedef struct {
+    int32_t threads_per_block; /* 64, 128 or 256 */
+    int32_t blocks_per_sm;     /* > 0 (<= 32): persistent grid of SMs x this with a per-warp work
+                                  queue; 0: flat grid, one event per thread */
+    int32_t chunk_events;      /* events a warp takes from the queue at a time (multiple of 32) */
+} recon_launch;
+
+typedef struct {
+    double sigma_mm;           /* TOF kernel sigma along the LOR */
+    double k_sigma;            /* kernel truncation, in sigmas */
+    int64_t n_vox;
+    int64_t n_events_resident;
+    int32_t has_sensitivity;
+    int32_t num_sms;
+    double sens_total;         /* sum of s_j over {s_j > 0} */
+} recon_info;
+
+typedef struct {
+    int64_t kernel_launches;   /* kernels this context launched (graph nodes counted per replay) */
+    int64_t pass_launches;     /* event-pass launches with device timing (timing on) */
+    double pass_ms;            /* summed device time of those event passes */
+    double update_ms;          /* summed device time of the timed updates */
+    int64_t autotune_runs;     /* autotuner searches performed */
+} recon_stats;
+
+/* ------------------------------------------------------------------ setup */
+
+/* Create a context on the current CUDA device.  sigma = c * FWHM / (2 * 2 sqrt(2 ln 2))
+ * with c = 0.299792458 mm/ps (Sec. 2.5 prints sigma = 19.11 mm for 300 ps); the
+ * kernel is truncated at +-3 sigma (the ~3 sigma margin of Sec. 2.5) unless
+ * recon_set_kernel_window changes it.  Allocates the device images (about
+ * 20 bytes per voxel).  Errors: EINVAL (NULL pointers, non-positive sizes,
+ * non-finite values, too many voxels), ENOMEM, ECUDA.  *out is NULL on error. */
+recon_status recon_create(const recon_geometry* geom, const recon_grid* grid, double tof_fwhm_ps, recon_ctx** out);
+
+/* Release everything the context owns.  NULL-safe. */
+void recon_destroy(recon_ctx* ctx);
+
+/* Message of the last failed call on ctx (ctx NULL: of the last failed recon_create
+ * on this thread).  Valid until the next call on the same context. */
+const char* recon_last_error(const recon_ctx* ctx);
+
+/* Stream for all device work of ctx (a cudaStream_t; NULL restores the context's own
+ * non-blocking stream).  The caller keeps the stream alive while ctx uses it. */
+recon_status recon_set_stream(recon_ctx* ctx, void* cuda_stream);
+
+/* Kernel truncation in sigmas, 0.5 <= k <= 8 (default 3). */
+recon_status recon_set_kernel_window(recon_ctx* ctx, double k_sigma);
+
+/* Forward gather from a BF16 copy of the image (1) or the FP32 image (0, default).
+ * Backprojection always accumulates in FP32. */
+recon_status recon_set_gather_bf16(recon_ctx* ctx, int32_t on);
+
+/* Fix the event-pass launch (NULL: return to the autotuner).  EINVAL if invalid. */
+recon_status recon_set_launch(recon_ctx* ctx, const recon_launch* cfg);
+/* The launch the last event pass used. */
+recon_status recon_get_launch(const recon_ctx* ctx, recon_launch* out);
+
+/* Per-call device timing of event passes and updates into recon_stats (off by default).
+ * While on, iterations are launched one by one with CUDA events around each kernel. */
+recon_status recon_set_timing(recon_ctx* ctx, int32_t on);
+/* Capture each MLEM iteration in a CUDA graph and replay it (1, default) or launch
+ * kernels directly (0). */
+recon_status recon_set_graphs(recon_ctx* ctx, int32_t on);
+/* Let recon_mlem search launch configurations on the resident events the first time
+ * it meets a new (event count, format, grid) (1, default), or use the default (0). */
+recon_status recon_set_autotune(recon_ctx* ctx, int32_t on);
+
+recon_status recon_get_info(const recon_ctx* ctx, recon_info* out);
+recon_status recon_get_stats(const recon_ctx* ctx, recon_stats* out);
+recon_status recon_reset_stats(recon_ctx* ctx);
+
+/* ------------------------------------------------------------ sensitivity */
+
+/* Sensitivity image s_j = sum_l L_lj: the full chord length (mm) of each of the n
+ * lines through voxel j, no TOF, accumulated in FP64 (Sec. 2.4, the "sensitive
+ * matrix").  lor: 6 planes x1,y1,z1,x2,y2,z2 of n floats each, contiguous
+ * (plane k at lor + k*n); host (on_device = 0) or device (1).  sens_out: NULL or
+ * nx*ny*nz doubles (host or device) receiving s.  The mask {s_j > 0} is the
+ * support of every later image.  Errors: EINVAL (n < 0, NULL lor with n > 0). */
+recon_status recon_sensitivity(recon_ctx* ctx, const float* lor, int64_t n, int32_t on_device, double* sens_out);
+
+/* Use a given sensitivity image (nx*ny*nz doubles, host or device per on_device). */
+recon_status recon_set_sensitivity(recon_ctx* ctx, const double* sens, int32_t on_device);
+
+/* ------------------------------------------------------------------ events */
+
+/* Copy the events into the context's resident device layout (32 bytes per event for
+ * the F32 format, 16 for the packed one); they stay resident for later calls that pass
+ * events = NULL.  Errors: EINVAL (bad format, n < 0, NULL planes, lattice <= 0),
+ * ENOMEM. */
+recon_status recon_load_events(recon_ctx* ctx, const recon_events* events);
+
+/* ---------------------------------------------------------------- projector */
+
+/* Forward projection p_i = sum_j a_ij lambda_j (Sec. 2.3/2.4) with
+ * a_ij = [Phi(tau_b/sigma) - Phi(tau_a/sigma)] / (2 Phi(K) - 1) over the piece
+ * [tau_a, tau_b] of the LOR inside voxel j and inside +-K sigma of the TOF point.
+ * events: NULL = the resident events, else loaded first (and kept resident).
+ * image: nx*ny*nz floats (host or device); NULL = the context's current image.
+ * p_out: n floats (host or device).  Errors: EINVAL, ESTATE (no events). */
+recon_status recon_forward(recon_ctx* ctx, const recon_events* events, const float* image, float* p_out);
+
+/* Backprojection C_j = sum_i a_ij r_i of per-event values r (n floats, host or
+ * device) into image_out (nx*ny*nz floats, host or device). */
+recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const float* r, float* image_out);
+
+/* -------------------------------------------------------------------- MLEM */
+
+/* n_iter iterations of list-mode TOF-MLEM (Sec. 2.4):
+ *     p_i = sum_j a_ij lambda_j;  C_j = sum_{i: p_i > 0} a_ij w_i / p_i;
+ *     lambda_j <- lambda_j C_j / s_j on {s_j > 0}, 0 elsewhere.
+ * Start image: init (nx*ny*nz floats, host or device) if not NULL, else uniform on
+ * {s_j > 0} with sum_j s_j lambda_j = sum_i w_i.  image_out: NULL or nx*ny*nz floats
+ * receiving the final image (the image also stays in the context).
+ * conservation_out: NULL or n_iter x 2 doubles {N_eff, sum_j s_j lambda_j} after each
+ * iteration, FP64 sums (N_eff = sum of w_i over events with p_i > 0); the two agree up
+ * to FP32 rounding of the image (count conservation).
+ * Errors: EINVAL (n_iter < 0), ESTATE (no sensitivity image or no events). */
+recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_iter, const float* init,
+                        float* image_out, double* conservation_out);
+
+/* ------------------------------------------------------ region division */
+
+/* TOF-assisted division into body regions (Sec. 2.5, Fig. 4).  Regions are
+ * consecutive core slice ranges (regions[r].z_hi == regions[r+1].z_lo) inside
+ * [0, nz), each at least 2*shell_mm thick; core boundaries z_b[r] = oz + z_lo*vz.
+ * Each event's TOF-estimated z, z_tof = (z1+z2)*0.5 + (d*dz)/D with
+ * D = sqrt((dx*dx + dy*dy) + dz*dz) in FP64 rounded per operation, decides the
+ * regions: r takes the event iff z_b[r] - shell <= z_tof < z_b[r+1] + shell.
+ * Outputs (host or device, each nullable):
+ *   code_out:    n bytes; 0xFF no region, r one region, r|0x80 regions r and r+1;
+ *   offsets_out: n_regions+1 int64, start of each region's list in idx_out;
+ *   idx_out:     offsets_out[n_regions] int32 event indices, ascending within a region.
+ * 1 <= n_regions <= 64, n < 2^31.  margin_mm is only validated here (>= 0).
+ * Errors: EINVAL, ESTATE (no events). */
+recon_status recon_split_regions(recon_ctx* ctx, const recon_events* events, int32_t n_regions,
+                                 const recon_region* regions, double margin_mm, double shell_mm,
+                                 uint8_t* code_out, int64_t* offsets_out, int32_t* idx_out);
+
+/* Region-divided reconstruction (Sec. 2.5): split as recon_split_regions, give each
+ * event fed to two regions the weight w_i/2, reconstruct every region on its slab of
+ * slices [z_lo - m, z_hi + m) clipped to the grid, m = ceil(margin_mm / vz), with the
+ * global sensitivity restricted to the slab, then sum the slabs into image_out
+ * (nx*ny*nz floats, nullable).  All regions run in one event-pass launch per
+ * iteration.  region_images_out: NULL or the concatenated slab images (region order,
+ * each nx*ny*slab_nz floats; total from recon_region_slab_voxels).
+ * conservation_out: NULL or n_iter x n_regions x 2 doubles {N_eff, sum s lambda}.
+ * Errors: EINVAL, ESTATE (no sensitivity image or no events). */
+recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int32_t n_regions,
+                                const recon_region* regions, double margin_mm, double shell_mm, int32_t n_iter,
+                                float* image_out, float* region_images_out, double* conservation_out);
+
+/* Total voxels of the region slabs of a division (for sizing region_images_out). */
+recon_status recon_region_slab_voxels(const recon_ctx* ctx, int32_t n_regions, const recon_region* regions,
+                                      double margin_mm, int64_t* n_vox_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECON_H */

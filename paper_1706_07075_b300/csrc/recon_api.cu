@@ -1,0 +1,1092 @@
+// C-ABI of librecon (include/recon.h): contexts, device-resident state,
+// stream-ordered execution with per-iteration CUDA graphs, the launch
+// autotuner and the region-divided reconstruction of Sec. 2.5.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "recon.h"
+#include "recon_kernels.h"
+
+using namespace recon;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+cudaError_t ensure(DevBuf& b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.p && b.bytes >= bytes) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.bytes = bytes;
+    return cudaSuccess;
+}
+
+void release(DevBuf& b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+}  // namespace
+
+struct recon_ctx {
+    recon_geometry geom{};
+    recon_grid grid{};
+    double fwhm_ps = 0, sigma_mm = 0, k_sigma = 3.0;
+    int device = 0, num_sms = 148;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    std::string err;
+    long long n_vox = 0;
+
+    // whole-grid images
+    DevBuf s64, s32, lam, C, lam_bf16;
+    bool have_sens = false;
+    double sens_total = 0;
+
+    // resident events
+    DevBuf ev, staging;
+    int fmt = FMT_F32;
+    long long n_ev = 0;
+    double lattice = 0;
+    bool have_ev = false;
+    double w_total = 0;
+    long long ev_generation = 0;
+
+    // per-call scratch
+    DevBuf pass_partial, upd_partial, work, iter, hist, reg_vox, red_partial, vec;
+
+    // options
+    bool bf16 = false, timing = false, graphs = true, autotune = true;
+    bool user_cfg = false;
+    LaunchCfg cfg{256, 0, 256};
+    LaunchCfg last_cfg{256, 0, 256};
+    std::map<std::tuple<long long, int, long long, int>, LaunchCfg> tuned;
+    recon_stats stats{};
+
+    // per-iteration graph
+    cudaGraphExec_t gexec = nullptr;
+    std::string gkey;
+
+    // region division
+    DevBuf codes, counts, offsets, base, idx, ev_reg, lam_reg, C_reg, s_reg, bf16_reg, reg_vox_reg;
+};
+
+namespace {
+
+recon_status fail(recon_ctx* c, recon_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+recon_status fail_cuda(recon_ctx* c, cudaError_t e, const char* what, int line)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s (recon_api.cu:%d)", (int)e, cudaGetErrorString(e), what, line);
+    cudaGetLastError();  // clear a sticky launch error where possible
+    return fail(c, e == cudaErrorMemoryAllocation ? RECON_ENOMEM : RECON_ECUDA, buf);
+}
+
+#define CK(x)                                                        \
+    do {                                                             \
+        cudaError_t e_ = (x);                                        \
+        if (e_ != cudaSuccess) return fail_cuda(ctx, e_, #x, __LINE__); \
+    } while (0)
+
+#define CHECK_CTX()                                           \
+    do {                                                      \
+        if (!ctx) return RECON_EINVAL;                        \
+        ctx->err.clear();                                     \
+        cudaError_t e0_ = cudaSetDevice(ctx->device);         \
+        if (e0_ != cudaSuccess) return fail_cuda(ctx, e0_, "cudaSetDevice", __LINE__); \
+    } while (0)
+
+bool finite(double x) { return std::isfinite(x); }
+
+TofH make_tof(const recon_ctx* c)
+{
+    TofH t;
+    t.half_window = (float)(c->k_sigma * c->sigma_mm);
+    t.inv_sigma_sqrt2 = (float)(1.0 / (c->sigma_mm * std::sqrt(2.0)));
+    t.half_inv_norm = (float)(0.5 / std::erf(c->k_sigma / std::sqrt(2.0)));
+    return t;
+}
+
+GridH grid_h(const recon_grid& g, int z_lo = 0, int z_hi = -1, long long vox_offset = 0)
+{
+    if (z_hi < 0) z_hi = g.nz;
+    GridH h;
+    h.nx = g.nx;
+    h.ny = g.ny;
+    h.nz = z_hi - z_lo;
+    h.vx = (float)g.vx;
+    h.vy = (float)g.vy;
+    h.vz = (float)g.vz;
+    h.ox = (float)g.ox;
+    h.oy = (float)g.oy;
+    h.oz = (float)(g.oz + (double)z_lo * g.vz);
+    h.vox_offset = vox_offset;
+    return h;
+}
+
+int reduce_blocks(long long n) { return (int)std::max(1LL, std::min((n + 1023) / 1024, 592LL)); }
+
+// Sum of `blocks` doubles left by a reduction kernel (synchronises the stream).
+recon_status host_sum(recon_ctx* ctx, const double* dev, int blocks, double* out)
+{
+    std::vector<double> h(blocks);
+    CK(cudaMemcpyAsync(h.data(), dev, sizeof(double) * blocks, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double s = 0;
+    for (double v : h) s += v;
+    *out = s;
+    return RECON_OK;
+}
+
+void invalidate_graph(recon_ctx* ctx)
+{
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+    ctx->gkey.clear();
+}
+
+recon_status validate_events(recon_ctx* ctx, const recon_events* e)
+{
+    if (!e) return fail(ctx, RECON_EINVAL, "events is NULL");
+    if (e->fmt != RECON_EV_F32_SOA && e->fmt != RECON_EV_PACKED_I16_F16)
+        return fail(ctx, RECON_EINVAL, "unknown event format");
+    if (e->n < 0) return fail(ctx, RECON_EINVAL, "event count is negative");
+    if (e->n > (1LL << 34)) return fail(ctx, RECON_EINVAL, "event count too large");
+    if (e->n > 0) {
+        const int np = e->fmt == RECON_EV_F32_SOA ? 7 : 1;
+        for (int k = 0; k < np; ++k)
+            if (!e->planes[k]) return fail(ctx, RECON_EINVAL, "event plane pointer is NULL");
+        if (e->fmt == RECON_EV_PACKED_I16_F16) {
+            if (!(e->lattice_mm > 0) || !finite(e->lattice_mm)) return fail(ctx, RECON_EINVAL, "lattice_mm must be > 0");
+            if (reinterpret_cast<uintptr_t>(e->planes[0]) % 16) return fail(ctx, RECON_EINVAL, "packed records must be 16-byte aligned");
+        }
+    }
+    return RECON_OK;
+}
+
+// Copy events into the resident layout (chunked through a staging buffer when
+// they live on the host).
+recon_status load_events(recon_ctx* ctx, const recon_events* e)
+{
+    recon_status s = validate_events(ctx, e);
+    if (s != RECON_OK) return s;
+    const long long n = e->n;
+    const bool packed = e->fmt == RECON_EV_PACKED_I16_F16;
+    const size_t rec = packed ? 16 : 32;
+    CK(ensure(ctx->ev, (size_t)n * rec));
+    if (n > 0) {
+        if (e->on_device) {
+            if (packed)
+                CK(launch_ingest_packed(static_cast<const int4*>(e->planes[0]), e->weight, n, ctx->ev.as<int4>(),
+                                        ctx->stream));
+            else
+                CK(launch_ingest_f32(reinterpret_cast<const float* const*>(e->planes), e->weight, n,
+                                     ctx->ev.as<float4>(), ctx->stream));
+            ctx->stats.kernel_launches += 1;
+        } else {
+            const long long chunk = std::min(n, 1LL << 23);
+            const size_t per = packed ? 16 + 4 : 8 * 4;
+            CK(ensure(ctx->staging, (size_t)chunk * per));
+            for (long long lo = 0; lo < n; lo += chunk) {
+                const long long m = std::min(chunk, n - lo);
+                if (packed) {
+                    int4* st = ctx->staging.as<int4>();
+                    float* wst = reinterpret_cast<float*>(st + chunk);
+                    CK(cudaMemcpyAsync(st, static_cast<const int4*>(e->planes[0]) + lo, (size_t)m * 16,
+                                       cudaMemcpyHostToDevice, ctx->stream));
+                    if (e->weight)
+                        CK(cudaMemcpyAsync(wst, e->weight + lo, (size_t)m * 4, cudaMemcpyHostToDevice, ctx->stream));
+                    CK(launch_ingest_packed(st, e->weight ? wst : nullptr, m, ctx->ev.as<int4>() + lo, ctx->stream));
+                } else {
+                    float* st = ctx->staging.as<float>();
+                    const float* pl[7];
+                    for (int k = 0; k < 7; ++k) {
+                        CK(cudaMemcpyAsync(st + (size_t)k * chunk, static_cast<const float*>(e->planes[k]) + lo,
+                                           (size_t)m * 4, cudaMemcpyHostToDevice, ctx->stream));
+                        pl[k] = st + (size_t)k * chunk;
+                    }
+                    float* wst = st + (size_t)7 * chunk;
+                    if (e->weight)
+                        CK(cudaMemcpyAsync(wst, e->weight + lo, (size_t)m * 4, cudaMemcpyHostToDevice, ctx->stream));
+                    CK(launch_ingest_f32(pl, e->weight ? wst : nullptr, m, ctx->ev.as<float4>() + 2 * lo,
+                                         ctx->stream));
+                }
+                ctx->stats.kernel_launches += 1;
+            }
+        }
+    }
+    ctx->fmt = packed ? FMT_PACKED : FMT_F32;
+    ctx->lattice = packed ? e->lattice_mm : 0.0;
+    ctx->n_ev = n;
+    ctx->have_ev = true;
+    ctx->ev_generation++;
+    invalidate_graph(ctx);
+    ctx->w_total = 0;
+    if (n > 0) {
+        const int b = reduce_blocks(n);
+        CK(ensure(ctx->red_partial, sizeof(double) * 1024));
+        CK(launch_reduce_weights(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr, n,
+                                 ctx->red_partial.as<double>(), b, ctx->stream));
+        ctx->stats.kernel_launches += 1;
+        s = host_sum(ctx, ctx->red_partial.as<double>(), b, &ctx->w_total);
+        if (s != RECON_OK) return s;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
+recon_status finish_sensitivity(recon_ctx* ctx)
+{
+    const int b = reduce_blocks(ctx->n_vox);
+    CK(ensure(ctx->red_partial, sizeof(double) * 1024));
+    CK(launch_sens_finish(ctx->s64.as<double>(), ctx->n_vox, ctx->s32.as<float>(), ctx->red_partial.as<double>(), b,
+                          ctx->stream));
+    ctx->stats.kernel_launches += 1;
+    recon_status s = host_sum(ctx, ctx->red_partial.as<double>(), b, &ctx->sens_total);
+    if (s != RECON_OK) return s;
+    ctx->have_sens = true;
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+LaunchCfg default_cfg() { return LaunchCfg{256, 0, 256}; }
+
+bool valid_cfg(const recon_launch* c)
+{
+    if (!c) return false;
+    if (c->threads_per_block != 64 && c->threads_per_block != 128 && c->threads_per_block != 256) return false;
+    if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return false;
+    if (c->blocks_per_sm > 0 && (c->chunk_events < 32 || c->chunk_events % 32 || c->chunk_events > (1 << 20)))
+        return false;
+    return true;
+}
+
+RegionTable single_table(const recon_ctx* ctx)
+{
+    RegionTable t;
+    memset(&t, 0, sizeof t);
+    t.n = 1;
+    t.ev_begin[0] = 0;
+    t.ev_begin[1] = ctx->n_ev;
+    t.grid[0] = grid_h(ctx->grid);
+    return t;
+}
+
+PassArgs base_args(recon_ctx* ctx, const void* events, long long n)
+{
+    PassArgs a;
+    memset(&a, 0, sizeof a);
+    a.events = events;
+    a.n = n;
+    a.lattice = (float)ctx->lattice;
+    a.tof = make_tof(ctx);
+    return a;
+}
+
+// Time one fused pass per candidate launch and keep the fastest.  The pass
+// accumulates into C, which the caller clears afterwards; lambda is untouched.
+recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, LaunchCfg* best)
+{
+    std::vector<LaunchCfg> cands;
+    for (int th : {128, 256}) {
+        cands.push_back(LaunchCfg{th, 0, 0});
+        for (int bps : {2048 / th / 2, 2048 / th})
+            for (int ch : {64, 256}) cands.push_back(LaunchCfg{th, bps, ch});
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    *best = default_cfg();
+    for (const LaunchCfg& c : cands) {
+        const int blocks = pass_blocks(c, a.n, ctx->num_sms);
+        CK(ensure(ctx->pass_partial, sizeof(double) * (size_t)std::max(1, blocks) * tbl.n));
+        a.partial = ctx->pass_partial.as<double>();
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+            CK(cudaEventRecord(e0, ctx->stream));
+            CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, c, a, tbl, ctx->num_sms, ctx->stream));
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            ms_min = std::min(ms_min, ms);
+            ctx->stats.kernel_launches += 1;
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            *best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->stats.autotune_runs += 1;
+    return RECON_OK;
+}
+
+struct IterPlan {
+    PassArgs a;
+    RegionTable tbl;
+    LaunchCfg cfg;
+    float* lam;
+    float* C;
+    const float* s32;
+    uint16_t* bf16;
+    long long* reg_vox_dev;
+    int n_regions;
+    int upd_bpr;
+    int pass_blocks;
+    double* hist;
+    int* iter;
+    int hist_cap;
+};
+
+recon_status enqueue_iteration(recon_ctx* ctx, const IterPlan& p)
+{
+    if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+    CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, p.a, p.tbl, ctx->num_sms, ctx->stream));
+    CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(), p.upd_bpr,
+                     ctx->stream));
+    CK(launch_finalize(p.a.partial, p.pass_blocks, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions, p.hist,
+                       p.iter, p.hist_cap, ctx->stream));
+    return RECON_OK;
+}
+
+std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "%p %lld %d %d %d %d %p %p %p %p %p %d %d %d %p %p %d %p %lld %d %a %a %a", p.a.events,
+             p.a.n, ctx->fmt, p.cfg.threads, p.cfg.blocks_per_sm, p.cfg.chunk, (void*)p.lam, (void*)p.C,
+             (const void*)p.s32, (void*)p.bf16, (void*)p.reg_vox_dev, p.n_regions, p.upd_bpr, p.pass_blocks,
+             (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
+             (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
+    std::string k(buf);
+    for (int r = 0; r < p.tbl.n; ++r) {
+        snprintf(buf, sizeof buf, "|%lld %d %a %lld", p.tbl.ev_begin[r + 1], p.tbl.grid[r].nz,
+                 (double)p.tbl.grid[r].oz, p.tbl.grid[r].vox_offset);
+        k += buf;
+    }
+    return k;
+}
+
+// Run n_iter iterations of the plan: graph replay, or direct launches (timing).
+recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter)
+{
+    CK(cudaMemsetAsync(p.iter, 0, sizeof(int), ctx->stream));
+    if (n_iter == 0) return RECON_OK;
+    const bool legacy = ctx->stream == nullptr || ctx->stream == cudaStreamLegacy || ctx->stream == cudaStreamPerThread;
+    if (ctx->timing || !ctx->graphs || legacy) {
+        std::vector<cudaEvent_t> evs;
+        if (ctx->timing) {
+            evs.resize(3 * (size_t)n_iter);
+            for (auto& e : evs) CK(cudaEventCreate(&e));
+        }
+        for (int k = 0; k < n_iter; ++k) {
+            if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+            if (ctx->timing) CK(cudaEventRecord(evs[3 * k], ctx->stream));
+            CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, p.a, p.tbl, ctx->num_sms, ctx->stream));
+            if (ctx->timing) CK(cudaEventRecord(evs[3 * k + 1], ctx->stream));
+            CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(),
+                             p.upd_bpr, ctx->stream));
+            if (ctx->timing) CK(cudaEventRecord(evs[3 * k + 2], ctx->stream));
+            CK(launch_finalize(p.a.partial, p.pass_blocks, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions,
+                               p.hist, p.iter, p.hist_cap, ctx->stream));
+            ctx->stats.kernel_launches += p.pass_blocks > 0 ? 3 : 2;
+        }
+        if (ctx->timing) {
+            CK(cudaStreamSynchronize(ctx->stream));
+            for (int k = 0; k < n_iter; ++k) {
+                float a = 0, b = 0;
+                CK(cudaEventElapsedTime(&a, evs[3 * k], evs[3 * k + 1]));
+                CK(cudaEventElapsedTime(&b, evs[3 * k + 1], evs[3 * k + 2]));
+                ctx->stats.pass_ms += a;
+                ctx->stats.update_ms += b;
+                ctx->stats.pass_launches += 1;
+            }
+            for (auto& e : evs) cudaEventDestroy(e);
+        }
+        return RECON_OK;
+    }
+    const std::string key = plan_key(ctx, p);
+    if (!ctx->gexec || key != ctx->gkey) {
+        invalidate_graph(ctx);
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        recon_status s = enqueue_iteration(ctx, p);
+        cudaGraph_t g = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(ctx->stream, &g);
+        if (s != RECON_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (ee != cudaSuccess) return fail_cuda(ctx, ee, "cudaStreamEndCapture", __LINE__);
+        cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            ctx->gexec = nullptr;
+            return fail_cuda(ctx, ei, "cudaGraphInstantiate", __LINE__);
+        }
+        ctx->gkey = key;
+    }
+    for (int k = 0; k < n_iter; ++k) {
+        CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+        ctx->stats.kernel_launches += p.pass_blocks > 0 ? 3 : 2;
+    }
+    return RECON_OK;
+}
+
+LaunchCfg choose_cfg(recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl, recon_status* st)
+{
+    *st = RECON_OK;
+    if (ctx->user_cfg) return ctx->cfg;
+    if (!ctx->autotune || a.n < (1LL << 20)) return default_cfg();
+    auto key = std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n);
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) return it->second;
+    LaunchCfg best;
+    *st = autotune(ctx, a, tbl, &best);
+    if (*st != RECON_OK) return default_cfg();
+    ctx->tuned[key] = best;
+    return best;
+}
+
+recon_status validate_regions(recon_ctx* ctx, int R, const recon_region* regions, double margin_mm, double shell_mm)
+{
+    if (R < 1 || R > kMaxRegions) return fail(ctx, RECON_EINVAL, "n_regions must be in [1, 64]");
+    if (!regions) return fail(ctx, RECON_EINVAL, "regions is NULL");
+    if (!(margin_mm >= 0) || !finite(margin_mm)) return fail(ctx, RECON_EINVAL, "margin_mm must be >= 0");
+    if (!(shell_mm >= 0) || !finite(shell_mm)) return fail(ctx, RECON_EINVAL, "shell_mm must be >= 0");
+    for (int r = 0; r < R; ++r) {
+        const recon_region& g = regions[r];
+        if (g.z_lo < 0 || g.z_hi > ctx->grid.nz || g.z_lo >= g.z_hi)
+            return fail(ctx, RECON_EINVAL, "region slice range outside the grid or empty");
+        if (r + 1 < R && regions[r + 1].z_lo != g.z_hi) return fail(ctx, RECON_EINVAL, "regions must be consecutive");
+        if ((double)(g.z_hi - g.z_lo) * ctx->grid.vz < 2.0 * shell_mm)
+            return fail(ctx, RECON_EINVAL, "region core thinner than 2 * shell_mm");
+    }
+    return RECON_OK;
+}
+
+// Split the resident events; leaves codes, idx and offsets (host copy in
+// h_offsets, R+2 entries) in the context.
+recon_status split_internal(recon_ctx* ctx, int R, const recon_region* regions, double shell_mm,
+                            std::vector<long long>& h_offsets)
+{
+    const long long n = ctx->n_ev;
+    if (n >= (1LL << 31)) return fail(ctx, RECON_EINVAL, "region division takes fewer than 2^31 events");
+    std::vector<double> zb(R + 1);
+    for (int r = 0; r < R; ++r) zb[r] = ctx->grid.oz + (double)regions[r].z_lo * ctx->grid.vz;
+    zb[R] = ctx->grid.oz + (double)regions[R - 1].z_hi * ctx->grid.vz;
+    const int tile = 4096;
+    const long long tiles = std::max(1LL, (n + tile - 1) / tile);
+    CK(ensure(ctx->codes, (size_t)n));
+    CK(ensure(ctx->counts, sizeof(int) * (size_t)tiles * (R + 1)));
+    CK(ensure(ctx->offsets, sizeof(long long) * (R + 2)));
+    CK(ensure(ctx->base, sizeof(long long) * (size_t)tiles * R));
+    CK(cudaMemsetAsync(ctx->counts.p, 0, sizeof(int) * (size_t)tiles * (R + 1), ctx->stream));
+    const bool packed = ctx->fmt == FMT_PACKED;
+    CK(launch_region_codes(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr,
+                           ctx->lattice, n, zb.data(), R, shell_mm, ctx->codes.as<uint8_t>(), ctx->counts.as<int>(),
+                           tile, ctx->stream));
+    CK(launch_region_scan(ctx->counts.as<int>(), (int)tiles, R, ctx->offsets.as<long long>(),
+                          ctx->base.as<long long>(), ctx->stream));
+    ctx->stats.kernel_launches += n > 0 ? 2 : 1;
+    h_offsets.assign(R + 2, 0);
+    CK(cudaMemcpyAsync(h_offsets.data(), ctx->offsets.p, sizeof(long long) * (R + 2), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (h_offsets[R + 1] != 0) return fail(ctx, RECON_EINVAL, "events fall in three or more regions");
+    CK(ensure(ctx->idx, sizeof(int) * (size_t)std::max(1LL, h_offsets[R])));
+    CK(launch_region_scatter(ctx->codes.as<uint8_t>(), n, R, ctx->base.as<long long>(), tile, ctx->idx.as<int>(),
+                             ctx->stream));
+    if (n > 0) ctx->stats.kernel_launches += 1;
+    return RECON_OK;
+}
+
+void slab_ranges(const recon_ctx* ctx, int R, const recon_region* regions, double margin_mm, std::vector<int>& lo,
+                 std::vector<int>& hi)
+{
+    const int m = (int)std::ceil(margin_mm / ctx->grid.vz - 1e-12);
+    lo.resize(R);
+    hi.resize(R);
+    for (int r = 0; r < R; ++r) {
+        lo[r] = std::max(0, regions[r].z_lo - m);
+        hi[r] = std::min(ctx->grid.nz, regions[r].z_hi + m);
+    }
+}
+
+}  // namespace
+
+// ======================================================================= API
+
+extern "C" {
+
+recon_status recon_create(const recon_geometry* geom, const recon_grid* grid, double tof_fwhm_ps, recon_ctx** out)
+{
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is NULL";
+        return RECON_EINVAL;
+    }
+    *out = nullptr;
+    if (!geom || !grid) {
+        g_create_error = "geometry or grid is NULL";
+        return RECON_EINVAL;
+    }
+    if (!(geom->radius_mm > 0) || !(geom->axial_len_mm > 0) || !finite(geom->radius_mm) ||
+        !finite(geom->axial_len_mm) || !(geom->max_axial_angle_deg > 0) || !(geom->max_axial_angle_deg <= 90)) {
+        g_create_error = "invalid geometry";
+        return RECON_EINVAL;
+    }
+    if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || !(grid->vx > 0) || !(grid->vy > 0) || !(grid->vz > 0) ||
+        !finite(grid->vx) || !finite(grid->vy) || !finite(grid->vz) || !finite(grid->ox) || !finite(grid->oy) ||
+        !finite(grid->oz)) {
+        g_create_error = "invalid grid";
+        return RECON_EINVAL;
+    }
+    const long long nv = (long long)grid->nx * grid->ny * grid->nz;
+    if (nv >= (1LL << 31) - 1) {
+        g_create_error = "grid has 2^31 voxels or more";
+        return RECON_EINVAL;
+    }
+    if (!(tof_fwhm_ps > 0) || !finite(tof_fwhm_ps)) {
+        g_create_error = "tof_fwhm_ps must be > 0";
+        return RECON_EINVAL;
+    }
+    recon_ctx* ctx = new (std::nothrow) recon_ctx();
+    if (!ctx) {
+        g_create_error = "out of host memory";
+        return RECON_ENOMEM;
+    }
+    ctx->geom = *geom;
+    ctx->grid = *grid;
+    ctx->fwhm_ps = tof_fwhm_ps;
+    // sigma along the LOR: d = c (t2 - t1)/2, FWHM = 2 sqrt(2 ln 2) sigma
+    ctx->sigma_mm = 0.5 * 0.299792458 * tof_fwhm_ps / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    ctx->n_vox = nv;
+    auto bail = [&](cudaError_t e, const char* what) {
+        char buf[256];
+        snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+        g_create_error = buf;
+        recon_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? RECON_ENOMEM : RECON_ECUDA;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&ctx->device)) != cudaSuccess) return bail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device)) != cudaSuccess)
+        return bail(e, "cudaDeviceGetAttribute");
+    if ((e = cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(e, "cudaStreamCreateWithFlags");
+    ctx->stream = ctx->own_stream;
+    if ((e = ensure(ctx->s64, sizeof(double) * nv)) != cudaSuccess) return bail(e, "allocating s");
+    if ((e = ensure(ctx->s32, sizeof(float) * nv)) != cudaSuccess) return bail(e, "allocating s");
+    if ((e = ensure(ctx->lam, sizeof(float) * nv)) != cudaSuccess) return bail(e, "allocating lambda");
+    if ((e = ensure(ctx->C, sizeof(float) * nv)) != cudaSuccess) return bail(e, "allocating C");
+    if ((e = ensure(ctx->work, 64)) != cudaSuccess) return bail(e, "allocating work counter");
+    if ((e = ensure(ctx->iter, 64)) != cudaSuccess) return bail(e, "allocating iteration counter");
+    if ((e = cudaMemsetAsync(ctx->s64.p, 0, sizeof(double) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(ctx->s32.p, 0, sizeof(float) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(ctx->lam.p, 0, sizeof(float) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return bail(e, "cudaStreamSynchronize");
+    *out = ctx;
+    return RECON_OK;
+}
+
+void recon_destroy(recon_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    invalidate_graph(ctx);
+    DevBuf* bufs[] = {&ctx->s64, &ctx->s32, &ctx->lam, &ctx->C, &ctx->lam_bf16, &ctx->ev, &ctx->staging,
+                      &ctx->pass_partial, &ctx->upd_partial, &ctx->work, &ctx->iter, &ctx->hist, &ctx->reg_vox,
+                      &ctx->red_partial, &ctx->vec, &ctx->codes, &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
+                      &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg};
+    for (DevBuf* b : bufs) release(*b);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+}
+
+const char* recon_last_error(const recon_ctx* ctx)
+{
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+recon_status recon_set_stream(recon_ctx* ctx, void* cuda_stream)
+{
+    CHECK_CTX();
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->own_stream;
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_set_kernel_window(recon_ctx* ctx, double k_sigma)
+{
+    CHECK_CTX();
+    if (!(k_sigma >= 0.5 && k_sigma <= 8.0)) return fail(ctx, RECON_EINVAL, "k_sigma must be in [0.5, 8]");
+    ctx->k_sigma = k_sigma;
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_set_gather_bf16(recon_ctx* ctx, int32_t on)
+{
+    CHECK_CTX();
+    ctx->bf16 = on != 0;
+    if (ctx->bf16) CK(ensure(ctx->lam_bf16, sizeof(uint16_t) * ctx->n_vox));
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_set_launch(recon_ctx* ctx, const recon_launch* cfg)
+{
+    CHECK_CTX();
+    if (!cfg) {
+        ctx->user_cfg = false;
+        return RECON_OK;
+    }
+    if (!valid_cfg(cfg)) return fail(ctx, RECON_EINVAL, "invalid launch configuration");
+    ctx->user_cfg = true;
+    ctx->cfg = LaunchCfg{cfg->threads_per_block, cfg->blocks_per_sm, cfg->blocks_per_sm > 0 ? cfg->chunk_events : 0};
+    return RECON_OK;
+}
+
+recon_status recon_get_launch(const recon_ctx* ctx, recon_launch* out)
+{
+    if (!ctx || !out) return RECON_EINVAL;
+    out->threads_per_block = ctx->last_cfg.threads;
+    out->blocks_per_sm = ctx->last_cfg.blocks_per_sm;
+    out->chunk_events = ctx->last_cfg.chunk;
+    return RECON_OK;
+}
+
+recon_status recon_set_timing(recon_ctx* ctx, int32_t on)
+{
+    CHECK_CTX();
+    ctx->timing = on != 0;
+    return RECON_OK;
+}
+
+recon_status recon_set_graphs(recon_ctx* ctx, int32_t on)
+{
+    CHECK_CTX();
+    ctx->graphs = on != 0;
+    return RECON_OK;
+}
+
+recon_status recon_set_autotune(recon_ctx* ctx, int32_t on)
+{
+    CHECK_CTX();
+    ctx->autotune = on != 0;
+    return RECON_OK;
+}
+
+recon_status recon_get_info(const recon_ctx* ctx, recon_info* out)
+{
+    if (!ctx || !out) return RECON_EINVAL;
+    out->sigma_mm = ctx->sigma_mm;
+    out->k_sigma = ctx->k_sigma;
+    out->n_vox = ctx->n_vox;
+    out->n_events_resident = ctx->have_ev ? ctx->n_ev : 0;
+    out->has_sensitivity = ctx->have_sens ? 1 : 0;
+    out->num_sms = ctx->num_sms;
+    out->sens_total = ctx->sens_total;
+    return RECON_OK;
+}
+
+recon_status recon_get_stats(const recon_ctx* ctx, recon_stats* out)
+{
+    if (!ctx || !out) return RECON_EINVAL;
+    *out = ctx->stats;
+    return RECON_OK;
+}
+
+recon_status recon_reset_stats(recon_ctx* ctx)
+{
+    if (!ctx) return RECON_EINVAL;
+    ctx->stats = recon_stats{};
+    return RECON_OK;
+}
+
+recon_status recon_sensitivity(recon_ctx* ctx, const float* lor, int64_t n, int32_t on_device, double* sens_out)
+{
+    CHECK_CTX();
+    if (n < 0) return fail(ctx, RECON_EINVAL, "n is negative");
+    if (n > 0 && !lor) return fail(ctx, RECON_EINVAL, "lor is NULL");
+    CK(cudaMemsetAsync(ctx->s64.p, 0, sizeof(double) * ctx->n_vox, ctx->stream));
+    const GridH g = grid_h(ctx->grid);
+    if (n > 0) {
+        if (on_device) {
+            CK(launch_sensitivity(lor, n, g, ctx->s64.as<double>(), ctx->stream));
+            ctx->stats.kernel_launches += 1;
+        } else {
+            const long long chunk = std::min<long long>(n, 1LL << 23);
+            CK(ensure(ctx->staging, sizeof(float) * 6 * (size_t)chunk));
+            float* st = ctx->staging.as<float>();
+            for (long long lo = 0; lo < n; lo += chunk) {
+                const long long m = std::min(chunk, n - lo);
+                for (int k = 0; k < 6; ++k)
+                    CK(cudaMemcpyAsync(st + (size_t)k * m, lor + (size_t)k * n + lo, sizeof(float) * m,
+                                       cudaMemcpyHostToDevice, ctx->stream));
+                CK(launch_sensitivity(st, m, g, ctx->s64.as<double>(), ctx->stream));
+                ctx->stats.kernel_launches += 1;
+            }
+        }
+    }
+    recon_status s = finish_sensitivity(ctx);
+    if (s != RECON_OK) return s;
+    if (sens_out) CK(cudaMemcpyAsync(sens_out, ctx->s64.p, sizeof(double) * ctx->n_vox, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
+recon_status recon_set_sensitivity(recon_ctx* ctx, const double* sens, int32_t on_device)
+{
+    CHECK_CTX();
+    if (!sens) return fail(ctx, RECON_EINVAL, "sens is NULL");
+    CK(cudaMemcpyAsync(ctx->s64.p, sens, sizeof(double) * ctx->n_vox,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    recon_status s = finish_sensitivity(ctx);
+    if (s != RECON_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
+recon_status recon_load_events(recon_ctx* ctx, const recon_events* events)
+{
+    CHECK_CTX();
+    return load_events(ctx, events);
+}
+
+recon_status recon_forward(recon_ctx* ctx, const recon_events* events, const float* image, float* p_out)
+{
+    CHECK_CTX();
+    if (events) {
+        recon_status s = load_events(ctx, events);
+        if (s != RECON_OK) return s;
+    }
+    if (!ctx->have_ev) return fail(ctx, RECON_ESTATE, "no events loaded");
+    if (!p_out && ctx->n_ev > 0) return fail(ctx, RECON_EINVAL, "p_out is NULL");
+    if (image) CK(cudaMemcpyAsync(ctx->lam.p, image, sizeof(float) * ctx->n_vox, cudaMemcpyDefault, ctx->stream));
+    if (ctx->n_ev == 0) return RECON_OK;
+    CK(ensure(ctx->vec, sizeof(float) * (size_t)ctx->n_ev));
+    PassArgs a = base_args(ctx, ctx->ev.p, ctx->n_ev);
+    a.lam = ctx->lam.as<float>();
+    if (ctx->bf16) {
+        CK(launch_to_bf16(ctx->lam.as<float>(), ctx->lam_bf16.as<uint16_t>(), ctx->n_vox, ctx->stream));
+        a.lam_bf16 = ctx->lam_bf16.as<uint16_t>();
+        ctx->stats.kernel_launches += 1;
+    }
+    a.p_out = ctx->vec.as<float>();
+    LaunchCfg cfg = ctx->user_cfg ? ctx->cfg : default_cfg();
+    CK(ensure(ctx->work, 64));
+    a.work = ctx->work.as<unsigned long long>();
+    CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+    const RegionTable tbl = single_table(ctx);
+    CK(launch_pass(PASS_FORWARD, (EventFmt)ctx->fmt, cfg, a, tbl, ctx->num_sms, ctx->stream));
+    ctx->stats.kernel_launches += 1;
+    ctx->last_cfg = cfg;
+    CK(cudaMemcpyAsync(p_out, ctx->vec.p, sizeof(float) * ctx->n_ev, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
+recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const float* r, float* image_out)
+{
+    CHECK_CTX();
+    if (events) {
+        recon_status s = load_events(ctx, events);
+        if (s != RECON_OK) return s;
+    }
+    if (!ctx->have_ev) return fail(ctx, RECON_ESTATE, "no events loaded");
+    if (!image_out) return fail(ctx, RECON_EINVAL, "image_out is NULL");
+    if (!r && ctx->n_ev > 0) return fail(ctx, RECON_EINVAL, "r is NULL");
+    CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * ctx->n_vox, ctx->stream));
+    if (ctx->n_ev > 0) {
+        CK(ensure(ctx->vec, sizeof(float) * (size_t)ctx->n_ev));
+        CK(cudaMemcpyAsync(ctx->vec.p, r, sizeof(float) * ctx->n_ev, cudaMemcpyDefault, ctx->stream));
+        PassArgs a = base_args(ctx, ctx->ev.p, ctx->n_ev);
+        a.C = ctx->C.as<float>();
+        a.r_in = ctx->vec.as<float>();
+        LaunchCfg cfg = ctx->user_cfg ? ctx->cfg : default_cfg();
+        a.work = ctx->work.as<unsigned long long>();
+        CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+        const RegionTable tbl = single_table(ctx);
+        CK(launch_pass(PASS_BACK, (EventFmt)ctx->fmt, cfg, a, tbl, ctx->num_sms, ctx->stream));
+        ctx->stats.kernel_launches += 1;
+        ctx->last_cfg = cfg;
+    }
+    CK(cudaMemcpyAsync(image_out, ctx->C.p, sizeof(float) * ctx->n_vox, cudaMemcpyDefault, ctx->stream));
+    CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * ctx->n_vox, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
+recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_iter, const float* init,
+                        float* image_out, double* conservation_out)
+{
+    CHECK_CTX();
+    if (n_iter < 0) return fail(ctx, RECON_EINVAL, "n_iter is negative");
+    if (events) {
+        recon_status s = load_events(ctx, events);
+        if (s != RECON_OK) return s;
+    }
+    if (!ctx->have_sens) return fail(ctx, RECON_ESTATE, "no sensitivity image (call recon_sensitivity first)");
+    if (!ctx->have_ev) return fail(ctx, RECON_ESTATE, "no events loaded");
+    const long long nv = ctx->n_vox;
+    if (init) {
+        CK(cudaMemcpyAsync(ctx->lam.p, init, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
+    } else {
+        const double v = ctx->sens_total > 0 ? ctx->w_total / ctx->sens_total : 0.0;
+        CK(launch_fill_masked(ctx->lam.as<float>(), ctx->s32.as<float>(), nv, (float)v, ctx->stream));
+        ctx->stats.kernel_launches += 1;
+    }
+    CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
+    if (ctx->bf16) {
+        CK(ensure(ctx->lam_bf16, sizeof(uint16_t) * nv));
+        CK(launch_to_bf16(ctx->lam.as<float>(), ctx->lam_bf16.as<uint16_t>(), nv, ctx->stream));
+        ctx->stats.kernel_launches += 1;
+    }
+    IterPlan p;
+    p.a = base_args(ctx, ctx->ev.p, ctx->n_ev);
+    p.a.lam = ctx->lam.as<float>();
+    p.a.lam_bf16 = ctx->bf16 ? ctx->lam_bf16.as<uint16_t>() : nullptr;
+    p.a.C = ctx->C.as<float>();
+    p.a.work = ctx->work.as<unsigned long long>();
+    p.tbl = single_table(ctx);
+    recon_status st;
+    CK(ensure(ctx->pass_partial, sizeof(double) * 16));
+    p.a.partial = ctx->pass_partial.as<double>();
+    p.cfg = choose_cfg(ctx, p.a, p.tbl, &st);
+    if (st != RECON_OK) return st;
+    CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
+    p.pass_blocks = pass_blocks(p.cfg, ctx->n_ev, ctx->num_sms);
+    CK(ensure(ctx->pass_partial, sizeof(double) * (size_t)std::max(1, p.pass_blocks)));
+    p.a.partial = ctx->pass_partial.as<double>();
+    p.upd_bpr = update_blocks(nv);
+    CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)p.upd_bpr));
+    CK(ensure(ctx->reg_vox, sizeof(long long) * 2));
+    const long long rv[2] = {0, nv};
+    CK(cudaMemcpyAsync(ctx->reg_vox.p, rv, sizeof rv, cudaMemcpyHostToDevice, ctx->stream));
+    p.hist_cap = std::max(n_iter, 64);
+    CK(ensure(ctx->hist, sizeof(double) * 2 * (size_t)p.hist_cap));
+    p.hist = ctx->hist.as<double>();
+    p.iter = ctx->iter.as<int>();
+    p.lam = ctx->lam.as<float>();
+    p.C = ctx->C.as<float>();
+    p.s32 = ctx->s32.as<float>();
+    p.bf16 = ctx->bf16 ? ctx->lam_bf16.as<uint16_t>() : nullptr;
+    p.reg_vox_dev = ctx->reg_vox.as<long long>();
+    p.n_regions = 1;
+    if (p.pass_blocks == 0) {
+        // no events: the pass is empty, its partial sum is zero
+        CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double), ctx->stream));
+        p.pass_blocks = 1;
+    }
+    ctx->last_cfg = p.cfg;
+    recon_status s = run_iterations(ctx, p, n_iter);
+    if (s != RECON_OK) return s;
+    if (image_out) CK(cudaMemcpyAsync(image_out, ctx->lam.p, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
+    if (conservation_out && n_iter > 0)
+        CK(cudaMemcpyAsync(conservation_out, ctx->hist.p, sizeof(double) * 2 * n_iter, cudaMemcpyDefault,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
+recon_status recon_split_regions(recon_ctx* ctx, const recon_events* events, int32_t n_regions,
+                                 const recon_region* regions, double margin_mm, double shell_mm,
+                                 uint8_t* code_out, int64_t* offsets_out, int32_t* idx_out)
+{
+    CHECK_CTX();
+    recon_status s = validate_regions(ctx, n_regions, regions, margin_mm, shell_mm);
+    if (s != RECON_OK) return s;
+    if (events) {
+        s = load_events(ctx, events);
+        if (s != RECON_OK) return s;
+    }
+    if (!ctx->have_ev) return fail(ctx, RECON_ESTATE, "no events loaded");
+    std::vector<long long> off;
+    s = split_internal(ctx, n_regions, regions, shell_mm, off);
+    if (s != RECON_OK) return s;
+    if (code_out && ctx->n_ev > 0)
+        CK(cudaMemcpyAsync(code_out, ctx->codes.p, (size_t)ctx->n_ev, cudaMemcpyDefault, ctx->stream));
+    if (offsets_out)
+        CK(cudaMemcpyAsync(offsets_out, off.data(), sizeof(long long) * (n_regions + 1), cudaMemcpyDefault,
+                           ctx->stream));
+    if (idx_out && off[n_regions] > 0)
+        CK(cudaMemcpyAsync(idx_out, ctx->idx.p, sizeof(int) * (size_t)off[n_regions], cudaMemcpyDefault,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
+recon_status recon_region_slab_voxels(const recon_ctx* ctx, int32_t n_regions, const recon_region* regions,
+                                      double margin_mm, int64_t* n_vox_out)
+{
+    if (!ctx || !n_vox_out) return RECON_EINVAL;
+    if (validate_regions(const_cast<recon_ctx*>(ctx), n_regions, regions, margin_mm, 0.0) != RECON_OK)
+        return RECON_EINVAL;
+    std::vector<int> lo, hi;
+    slab_ranges(ctx, n_regions, regions, margin_mm, lo, hi);
+    long long t = 0;
+    for (int r = 0; r < n_regions; ++r) t += (long long)ctx->grid.nx * ctx->grid.ny * (hi[r] - lo[r]);
+    *n_vox_out = t;
+    return RECON_OK;
+}
+
+recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int32_t n_regions,
+                                const recon_region* regions, double margin_mm, double shell_mm, int32_t n_iter,
+                                float* image_out, float* region_images_out, double* conservation_out)
+{
+    CHECK_CTX();
+    if (n_iter < 0) return fail(ctx, RECON_EINVAL, "n_iter is negative");
+    recon_status s = validate_regions(ctx, n_regions, regions, margin_mm, shell_mm);
+    if (s != RECON_OK) return s;
+    if (events) {
+        s = load_events(ctx, events);
+        if (s != RECON_OK) return s;
+    }
+    if (!ctx->have_sens) return fail(ctx, RECON_ESTATE, "no sensitivity image (call recon_sensitivity first)");
+    if (!ctx->have_ev) return fail(ctx, RECON_ESTATE, "no events loaded");
+    const int R = n_regions;
+    std::vector<long long> off;
+    s = split_internal(ctx, R, regions, shell_mm, off);
+    if (s != RECON_OK) return s;
+    const long long total = off[R];
+    const bool packed = ctx->fmt == FMT_PACKED;
+    const size_t rec = packed ? 16 : 32;
+    CK(ensure(ctx->ev_reg, rec * (size_t)std::max(1LL, total)));
+    CK(launch_region_gather(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr,
+                            ctx->codes.as<uint8_t>(), ctx->idx.as<int>(), total,
+                            packed ? nullptr : ctx->ev_reg.as<float4>(), packed ? ctx->ev_reg.as<int4>() : nullptr,
+                            ctx->stream));
+    if (total > 0) ctx->stats.kernel_launches += 1;
+
+    std::vector<int> lo, hi;
+    slab_ranges(ctx, R, regions, margin_mm, lo, hi);
+    const long long plane = (long long)ctx->grid.nx * ctx->grid.ny;
+    std::vector<long long> rv(R + 1, 0);
+    for (int r = 0; r < R; ++r) rv[r + 1] = rv[r] + plane * (hi[r] - lo[r]);
+    const long long nvt = rv[R];
+    CK(ensure(ctx->lam_reg, sizeof(float) * nvt));
+    CK(ensure(ctx->C_reg, sizeof(float) * nvt));
+    CK(ensure(ctx->s_reg, sizeof(float) * nvt));
+    CK(ensure(ctx->reg_vox_reg, sizeof(long long) * (R + 1)));
+    CK(cudaMemcpyAsync(ctx->reg_vox_reg.p, rv.data(), sizeof(long long) * (R + 1), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(ensure(ctx->red_partial, sizeof(double) * 1024));
+    // per-region slab sensitivity (FP32 copy of the global s) and start image
+    for (int r = 0; r < R; ++r) {
+        const long long nr = rv[r + 1] - rv[r];
+        const int b = reduce_blocks(nr);
+        CK(launch_sens_finish(ctx->s64.as<double>() + lo[r] * plane, nr, ctx->s_reg.as<float>() + rv[r],
+                              ctx->red_partial.as<double>(), b, ctx->stream));
+        double S = 0, W = 0;
+        s = host_sum(ctx, ctx->red_partial.as<double>(), b, &S);
+        if (s != RECON_OK) return s;
+        const long long ne = off[r + 1] - off[r];
+        if (ne > 0) {
+            const int bw = reduce_blocks(ne);
+            CK(launch_reduce_weights(packed ? nullptr : ctx->ev_reg.as<float4>() + 2 * off[r],
+                                     packed ? ctx->ev_reg.as<int4>() + off[r] : nullptr, ne,
+                                     ctx->red_partial.as<double>(), bw, ctx->stream));
+            s = host_sum(ctx, ctx->red_partial.as<double>(), bw, &W);
+            if (s != RECON_OK) return s;
+            ctx->stats.kernel_launches += 1;
+        }
+        CK(launch_fill_masked(ctx->lam_reg.as<float>() + rv[r], ctx->s_reg.as<float>() + rv[r], nr,
+                              (float)(S > 0 ? W / S : 0.0), ctx->stream));
+        ctx->stats.kernel_launches += 2;
+    }
+    CK(cudaMemsetAsync(ctx->C_reg.p, 0, sizeof(float) * nvt, ctx->stream));
+    if (ctx->bf16) {
+        CK(ensure(ctx->bf16_reg, sizeof(uint16_t) * nvt));
+        CK(launch_to_bf16(ctx->lam_reg.as<float>(), ctx->bf16_reg.as<uint16_t>(), nvt, ctx->stream));
+        ctx->stats.kernel_launches += 1;
+    }
+
+    IterPlan p;
+    p.a = base_args(ctx, ctx->ev_reg.p, total);
+    p.a.lam = ctx->lam_reg.as<float>();
+    p.a.lam_bf16 = ctx->bf16 ? ctx->bf16_reg.as<uint16_t>() : nullptr;
+    p.a.C = ctx->C_reg.as<float>();
+    p.a.work = ctx->work.as<unsigned long long>();
+    memset(&p.tbl, 0, sizeof p.tbl);
+    p.tbl.n = R;
+    for (int r = 0; r <= R; ++r) p.tbl.ev_begin[r] = off[r];
+    for (int r = 0; r < R; ++r) p.tbl.grid[r] = grid_h(ctx->grid, lo[r], hi[r], rv[r]);
+    CK(ensure(ctx->pass_partial, sizeof(double) * 16 * R));
+    p.a.partial = ctx->pass_partial.as<double>();
+    p.cfg = choose_cfg(ctx, p.a, p.tbl, &s);
+    if (s != RECON_OK) return s;
+    CK(cudaMemsetAsync(ctx->C_reg.p, 0, sizeof(float) * nvt, ctx->stream));
+    p.pass_blocks = pass_blocks(p.cfg, total, ctx->num_sms);
+    CK(ensure(ctx->pass_partial, sizeof(double) * (size_t)std::max(1, p.pass_blocks) * R));
+    p.a.partial = ctx->pass_partial.as<double>();
+    if (p.pass_blocks == 0) {
+        CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * R, ctx->stream));
+        p.pass_blocks = 1;
+    }
+    p.upd_bpr = std::max(1, update_blocks(nvt) / R);
+    CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)p.upd_bpr * R));
+    p.hist_cap = std::max(n_iter, 64);
+    CK(ensure(ctx->hist, sizeof(double) * 2 * (size_t)p.hist_cap * R));
+    p.hist = ctx->hist.as<double>();
+    p.iter = ctx->iter.as<int>();
+    p.lam = ctx->lam_reg.as<float>();
+    p.C = ctx->C_reg.as<float>();
+    p.s32 = ctx->s_reg.as<float>();
+    p.bf16 = ctx->bf16 ? ctx->bf16_reg.as<uint16_t>() : nullptr;
+    p.reg_vox_dev = ctx->reg_vox_reg.as<long long>();
+    p.n_regions = R;
+    ctx->last_cfg = p.cfg;
+    s = run_iterations(ctx, p, n_iter);
+    if (s != RECON_OK) return s;
+    // stitch into the context's whole-grid image
+    CK(launch_stitch(ctx->lam_reg.as<float>(), rv.data(), lo.data(), hi.data(), R, ctx->grid.nx, ctx->grid.ny,
+                     ctx->grid.nz, ctx->lam.as<float>(), ctx->stream));
+    ctx->stats.kernel_launches += 1;
+    if (image_out) CK(cudaMemcpyAsync(image_out, ctx->lam.p, sizeof(float) * ctx->n_vox, cudaMemcpyDefault, ctx->stream));
+    if (region_images_out)
+        CK(cudaMemcpyAsync(region_images_out, ctx->lam_reg.p, sizeof(float) * nvt, cudaMemcpyDefault, ctx->stream));
+    if (conservation_out && n_iter > 0)
+        CK(cudaMemcpyAsync(conservation_out, ctx->hist.p, sizeof(double) * 2 * (size_t)n_iter * R, cudaMemcpyDefault,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
+}  // extern "C"

@@ -125,7 +125,7 @@ recon_status fail_cuda(recon_ctx* c, cudaError_t e, const char* what, int line)
         if (e0_ != cudaSuccess) return fail_cuda(ctx, e0_, "cudaSetDevice", __LINE__); \
     } while (0)
 
-bool finite(double x) { return std::isfinite(x); }
+bool is_finite(double x) { return std::isfinite(x); }
 
 TofH make_tof(const recon_ctx* c)
 {
@@ -186,7 +186,7 @@ recon_status validate_events(recon_ctx* ctx, const recon_events* e)
         for (int k = 0; k < np; ++k)
             if (!e->planes[k]) return fail(ctx, RECON_EINVAL, "event plane pointer is NULL");
         if (e->fmt == RECON_EV_PACKED_I16_F16) {
-            if (!(e->lattice_mm > 0) || !finite(e->lattice_mm)) return fail(ctx, RECON_EINVAL, "lattice_mm must be > 0");
+            if (!(e->lattice_mm > 0) || !is_finite(e->lattice_mm)) return fail(ctx, RECON_EINVAL, "lattice_mm must be > 0");
             if (reinterpret_cast<uintptr_t>(e->planes[0]) % 16) return fail(ctx, RECON_EINVAL, "packed records must be 16-byte aligned");
         }
     }
@@ -483,8 +483,8 @@ recon_status validate_regions(recon_ctx* ctx, int R, const recon_region* regions
 {
     if (R < 1 || R > kMaxRegions) return fail(ctx, RECON_EINVAL, "n_regions must be in [1, 64]");
     if (!regions) return fail(ctx, RECON_EINVAL, "regions is NULL");
-    if (!(margin_mm >= 0) || !finite(margin_mm)) return fail(ctx, RECON_EINVAL, "margin_mm must be >= 0");
-    if (!(shell_mm >= 0) || !finite(shell_mm)) return fail(ctx, RECON_EINVAL, "shell_mm must be >= 0");
+    if (!(margin_mm >= 0) || !is_finite(margin_mm)) return fail(ctx, RECON_EINVAL, "margin_mm must be >= 0");
+    if (!(shell_mm >= 0) || !is_finite(shell_mm)) return fail(ctx, RECON_EINVAL, "shell_mm must be >= 0");
     for (int r = 0; r < R; ++r) {
         const recon_region& g = regions[r];
         if (g.z_lo < 0 || g.z_hi > ctx->grid.nz || g.z_lo >= g.z_hi)
@@ -562,14 +562,14 @@ recon_status recon_create(const recon_geometry* geom, const recon_grid* grid, do
         g_create_error = "geometry or grid is NULL";
         return RECON_EINVAL;
     }
-    if (!(geom->radius_mm > 0) || !(geom->axial_len_mm > 0) || !finite(geom->radius_mm) ||
-        !finite(geom->axial_len_mm) || !(geom->max_axial_angle_deg > 0) || !(geom->max_axial_angle_deg <= 90)) {
+    if (!(geom->radius_mm > 0) || !(geom->axial_len_mm > 0) || !is_finite(geom->radius_mm) ||
+        !is_finite(geom->axial_len_mm) || !(geom->max_axial_angle_deg > 0) || !(geom->max_axial_angle_deg <= 90)) {
         g_create_error = "invalid geometry";
         return RECON_EINVAL;
     }
     if (grid->nx <= 0 || grid->ny <= 0 || grid->nz <= 0 || !(grid->vx > 0) || !(grid->vy > 0) || !(grid->vz > 0) ||
-        !finite(grid->vx) || !finite(grid->vy) || !finite(grid->vz) || !finite(grid->ox) || !finite(grid->oy) ||
-        !finite(grid->oz)) {
+        !is_finite(grid->vx) || !is_finite(grid->vy) || !is_finite(grid->vz) || !is_finite(grid->ox) || !is_finite(grid->oy) ||
+        !is_finite(grid->oz)) {
         g_create_error = "invalid grid";
         return RECON_EINVAL;
     }
@@ -578,7 +578,7 @@ recon_status recon_create(const recon_geometry* geom, const recon_grid* grid, do
         g_create_error = "grid has 2^31 voxels or more";
         return RECON_EINVAL;
     }
-    if (!(tof_fwhm_ps > 0) || !finite(tof_fwhm_ps)) {
+    if (!(tof_fwhm_ps > 0) || !is_finite(tof_fwhm_ps)) {
         g_create_error = "tof_fwhm_ps must be > 0";
         return RECON_EINVAL;
     }

@@ -1,0 +1,181 @@
+"""Edge cases of the GPU path: empty and one-event inputs, events that miss
+the grid, rays lying in voxel planes, axis-parallel rays, the one-voxel grid,
+zero iterations, launch configurations, device-resident buffers and call
+order errors."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_common import SIGMA, geometry, grid_tuple, rel_l2, tiny_inputs, workload_grid
+from paper_1706_07075_b300 import binding as B
+from paper_1706_07075_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def odd_events():
+    """Hand-built events on voxel planes, along axes, missing the grid, degenerate."""
+    g = workload_grid("tiny")           # 32x32x48 voxels of 4 mm from (-64, -64, -96)
+    rows = []
+    xp = g.ox + 10 * g.vx               # the plane between columns 9 and 10
+    rows.append([xp, -150.0, 3.0, xp, 150.0, -7.0, 12.0])        # in the x-plane
+    rows.append([xp, g.oy + 7 * g.vy, -200.0, xp, g.oy + 7 * g.vy, 200.0, -30.0])  # on an edge
+    rows.append([-150.0, 2.0, 2.0, 150.0, 2.0, 2.0, 5.0])        # along x
+    rows.append([1.0, 1.0, -200.0, 1.0, 1.0, 200.0, 40.0])       # along z
+    rows.append([-150.0, 90.0, 0.0, 150.0, 90.0, 0.0, 0.0])      # misses the grid (y = 90 > 64)
+    rows.append([-150.0, 0.0, 0.0, 150.0, 0.0, 0.0, 500.0])      # TOF point far outside
+    rows.append([5.0, 5.0, 5.0, 5.0, 5.0, 5.0, 0.0])             # P1 == P2
+    rows.append([g.ox + 32 * g.vx, -150.0, 0.0, g.ox + 32 * g.vx, 150.0, 1.0, 0.0])  # on the upper face
+    rows.append([g.ox, -150.0, 0.0, g.ox, 150.0, 1.0, 0.0])      # on the lower face
+    rows.append([100.0, 80.0, 60.0, -90.0, -70.0, -50.0, 17.0])  # oblique through the corner region
+    return np.array(rows, np.float32).T.copy()
+
+
+@pytest.fixture(scope="module")
+def ctx_tiny():
+    ev, lors = tiny_inputs()
+    g = workload_grid("tiny")
+    ctx = B.Context(geometry("tiny"), grid_tuple(g), 300.0)
+    ctx.sensitivity(lors)
+    yield ctx, g
+    ctx.close()
+
+
+def test_odd_rays_forward_match_oracle(ctx_tiny):
+    ctx, g = ctx_tiny
+    ev = odd_events()
+    rng = np.random.default_rng(5)
+    lam = rng.uniform(0.5, 1.5, g.n_vox).astype(np.float32)
+    p = np.zeros(ev.shape[1], np.float32)
+    ctx.forward(B.make_events(ev), lam, p)
+    p_ref = oracle.forward(g, ev.astype(np.float64), lam.astype(np.float64), SIGMA)
+    assert np.allclose(p, p_ref, rtol=2e-5, atol=1e-7)
+    assert p[4] == 0 and p[5] == 0 and p[6] == 0 and p[7] == 0
+    assert p[0] > 0 and p[1] > 0 and p[8] > 0
+
+
+def test_odd_rays_row_mass_is_one_inside(ctx_tiny):
+    ctx, g = ctx_tiny
+    ev = odd_events()
+    p = np.zeros(ev.shape[1], np.float32)
+    ctx.forward(B.make_events(ev), np.ones(g.n_vox, np.float32), p)
+    # rows 2 and 3 have their whole +-3 sigma window inside the grid: unit mass
+    assert p[2] == pytest.approx(1.0, abs=2e-6)
+    assert p[3] == pytest.approx(1.0, abs=2e-6)
+
+
+def test_empty_events_and_zero_iterations(ctx_tiny):
+    ctx, g = ctx_tiny
+    ev = np.zeros((7, 0), np.float32)
+    img = np.full(g.n_vox, -1.0, np.float32)
+    cons = np.full((2, 2), -1.0)
+    ctx.mlem(B.make_events(ev), 2, None, img, cons)
+    assert np.all(img == 0) and np.all(cons == 0)
+    ev1, _ = tiny_inputs()
+    init = np.random.default_rng(1).uniform(0, 1, g.n_vox).astype(np.float32)
+    ctx.mlem(B.make_events(ev1[:, :1000].copy()), 0, init, img, None)
+    assert np.array_equal(img, init)
+
+
+def test_single_event_and_ragged_counts(ctx_tiny):
+    ctx, g = ctx_tiny
+    ev_all, _ = tiny_inputs()
+    s = np.zeros(g.n_vox)
+    for n in [1, 31, 33, 257, 4099]:
+        ev = ev_all[:, :n].copy()
+        img = np.zeros(g.n_vox, np.float32)
+        cons = np.zeros((1, 2))
+        ctx.mlem(B.make_events(ev), 1, None, img, cons)
+        assert cons[0, 0] <= n and cons[0, 1] == pytest.approx(cons[0, 0], rel=1e-5)
+
+
+def test_one_voxel_grid_closed_form():
+    with B.Context((100.0, 100.0, 90.0), (1, 1, 1, 10.0, 10.0, 10.0, -5.0, -5.0, -5.0), 300.0) as ctx:
+        ctx.set_sensitivity(np.array([12.5]))
+        rng = np.random.default_rng(8)
+        n = 37
+        u = rng.normal(size=(n, 3))
+        u /= np.linalg.norm(u, axis=1, keepdims=True)
+        ev = np.concatenate([(50 * u).T, (-50 * u).T, rng.uniform(-3, 3, (1, n))]).astype(np.float32)
+        img = np.zeros(1, np.float32)
+        ctx.mlem(B.make_events(ev), 1, None, img, None)
+        assert img[0] == pytest.approx(n / 12.5, rel=1e-6)
+
+
+@pytest.mark.parametrize("cfg", [(64, 0, 0), (128, 0, 0), (256, 4, 32), (128, 16, 256), (256, 1, 1024)])
+def test_launch_configurations_agree(ctx_tiny, cfg):
+    ctx, g = ctx_tiny
+    ev, _ = tiny_inputs()
+    ctx.set_launch(None)
+    ref = np.zeros(g.n_vox, np.float32)
+    ctx.set_launch(256, 0, 0)
+    ctx.mlem(B.make_events(ev), 2, None, ref, None)
+    ctx.set_launch(*cfg)
+    img = np.zeros(g.n_vox, np.float32)
+    ctx.mlem(None, 2, None, img, None)
+    assert ctx.get_launch() == (cfg[0], cfg[1], cfg[2] if cfg[1] else 0)
+    ctx.set_launch(None)
+    assert rel_l2(img, ref) < 1e-6
+
+
+def test_device_buffers_match_host_buffers(ctx_tiny):
+    ctx, g = ctx_tiny
+    ev, lors = tiny_inputs()
+    img_h = np.zeros(g.n_vox, np.float32)
+    ctx.mlem(B.make_events(ev), 2, None, img_h, None)
+    evd = torch.from_numpy(ev).cuda()
+    img_d = torch.zeros(g.n_vox, dtype=torch.float32, device="cuda")
+    cons_d = torch.zeros((2, 2), dtype=torch.float64, device="cuda")
+    ctx.mlem(B.make_events(evd), 2, None, img_d, cons_d)
+    torch.cuda.synchronize()
+    assert rel_l2(img_d.cpu().numpy(), img_h) < 1e-6
+    s_d = torch.zeros(g.n_vox, dtype=torch.float64, device="cuda")
+    ctx.sensitivity(torch.from_numpy(lors).cuda(), s_d)
+    s_h = np.zeros(g.n_vox)
+    ctx.sensitivity(lors, s_h)
+    assert rel_l2(s_d.cpu().numpy(), s_h) < 1e-12
+
+
+def test_call_order_and_argument_errors():
+    g = workload_grid("tiny")
+    with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx:
+        ev = synth.events("tiny", 100, 3)
+        with pytest.raises(B.ReconError) as e:
+            ctx.mlem(B.make_events(ev), 1)
+        assert e.value.status == B.RECON_ESTATE
+        with pytest.raises(B.ReconError) as e:
+            ctx.forward(None, None, np.zeros(1, np.float32)) if False else ctx.mlem(None, -1)
+        assert e.value.status == B.RECON_EINVAL
+        with pytest.raises(B.ReconError):
+            ctx.set_launch(100, 0, 0)
+        with pytest.raises(B.ReconError):
+            ctx.set_launch(256, 4, 48)
+        with pytest.raises(B.ReconError):
+            ctx.set_kernel_window(0.1)
+        bad = B.make_events(ev)
+        bad.fmt = 7
+        with pytest.raises(B.ReconError):
+            ctx.load_events(bad)
+        rec = np.zeros((4, 8), np.int16)
+        pk = B.make_events(rec, packed=True, lattice_mm=0.0)
+        with pytest.raises(B.ReconError):
+            ctx.load_events(pk)
+    with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx2:
+        with pytest.raises(B.ReconError) as e:
+            ctx2.forward(None, None, np.zeros(4, np.float32))
+        assert e.value.status == B.RECON_ESTATE
+
+
+def test_kernel_window_changes_the_projector(ctx_tiny):
+    ctx, g = ctx_tiny
+    ev, _ = tiny_inputs()
+    sub = ev[:, :5000].copy()
+    lam = np.random.default_rng(3).uniform(0.5, 1.5, g.n_vox).astype(np.float32)
+    p = np.zeros(sub.shape[1], np.float32)
+    ctx.set_kernel_window(2.0)
+    ctx.forward(B.make_events(sub), lam, p)
+    ctx.set_kernel_window(3.0)
+    p_ref = oracle.forward(g, sub.astype(np.float64), lam.astype(np.float64), SIGMA, K=2.0)
+    sel = p_ref > 1e-3 * p_ref.max()
+    assert np.max(np.abs(p[sel] - p_ref[sel]) / p_ref[sel]) < 2e-5

@@ -1,0 +1,133 @@
+"""Region division (Sec. 2.5) on the GPU vs the oracle: codes, offsets and
+per-region index lists bit-exact; region-divided MLEM images within the image
+tolerances (relative L2 <= 1e-4, per-voxel <= 1e-3 above 1% of max)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import SIGMA, geometry, grid_tuple, max_rel_above, rel_l2, workload_grid
+from paper_1706_07075_b300 import binding as B
+from paper_1706_07075_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FULLBODY_REGIONS = [(0, 67), (67, 134), (134, 200), (200, 267), (267, 334), (334, 400), (400, 467),
+                    (467, 534), (534, 600)]
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "region_boundary_events.json")
+
+
+def gpu_split(ctx, events, regions, shell, n):
+    codes = np.zeros(n, np.uint8)
+    offs = np.zeros(len(regions) + 1, np.int64)
+    ctx.split_regions(events, regions, 0.0, shell, codes, offs, None)
+    idx = np.zeros(max(1, int(offs[-1])), np.int32)
+    ctx.split_regions(None, regions, 0.0, shell, None, None, idx)
+    return codes, offs, idx[: int(offs[-1])]
+
+
+def test_split_golden_boundary_events():
+    gd = json.load(open(GOLDEN))
+    evs = gd["events"]
+    ev = np.array([[e["p1"][k] for e in evs] for k in range(3)] + [[e["p2"][k] for e in evs] for k in range(3)] +
+                  [[e["d"] for e in evs]], np.float32)
+    # grid of the fixture: 60 slices of 4 mm from -120 mm, regions of 20 slices
+    with B.Context((400.0, 400.0, 90.0), (8, 8, 60, 4.0, 4.0, 4.0, -16.0, -16.0, -120.0), 300.0) as ctx:
+        codes, offs, idx = gpu_split(ctx, B.make_events(ev), [(0, 20), (20, 40), (40, 60)], gd["shell_mm"],
+                                     ev.shape[1])
+    assert list(codes) == [e["code"] for e in evs]
+
+
+@pytest.mark.parametrize("packed", [False, True])
+def test_split_bitexact_fullbody(packed):
+    n = 3_000_001
+    ev = synth.events("fullbody", n, 41)
+    g = workload_grid("fullbody")
+    if packed:
+        rec = synth.pack_events(ev)
+        q = rec[:, :6].astype(np.float64).T * synth.LATTICE_MM
+        d = rec[:, 6].view(np.float16).astype(np.float64)
+        ev64 = np.concatenate([q, d[None, :]])
+        events = B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM)
+    else:
+        ev64 = ev.astype(np.float64)
+        events = B.make_events(ev)
+    zb = oracle.region_bounds(g, FULLBODY_REGIONS)
+    codes_ref = oracle.region_codes(ev64, zb, 6.0)
+    offs_ref, idx_ref = oracle.region_members(codes_ref, 9)
+    with B.Context(geometry("fullbody"), grid_tuple(g), 300.0) as ctx:
+        codes, offs, idx = gpu_split(ctx, events, FULLBODY_REGIONS, 6.0, n)
+    assert np.array_equal(codes, codes_ref)
+    assert np.array_equal(offs, offs_ref)
+    assert np.array_equal(idx, idx_ref)
+    counts = np.diff(offs)
+    assert counts.min() > 0 and offs[-1] >= n * 0.95
+
+
+def test_region_mlem_matches_oracle_tiny():
+    ev = synth.events("tiny", 120_000, 17)
+    lors = synth.sensitivity_lors("tiny", 500_000, 17)
+    g = workload_grid("tiny")
+    regions = [(0, 16), (16, 32), (32, 48)]
+    margin = 3.0 * SIGMA + 6.0
+    s_ref = oracle.sensitivity(g, lors)
+    img_ref, imgs_ref, hists, codes, offs, idx = oracle.mlem_regions(g, ev.astype(np.float64), s_ref, regions, 6.0,
+                                                                     margin, 3, SIGMA)
+    with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx:
+        ctx.sensitivity(lors)
+        nslab = ctx.region_slab_voxels(regions, margin)
+        assert nslab == sum(im.size for im in imgs_ref)
+        img = np.zeros(g.n_vox, np.float32)
+        slabs = np.zeros(nslab, np.float32)
+        cons = np.zeros((3, 3, 2))
+        ctx.mlem_regions(B.make_events(ev), regions, margin, 6.0, 3, img, slabs, cons)
+    assert rel_l2(img, img_ref) <= 1e-4
+    assert max_rel_above(img, img_ref, 0.01) <= 1e-3
+    assert rel_l2(slabs, np.concatenate(imgs_ref)) <= 1e-4
+    for r in range(3):
+        for k in range(3):
+            assert cons[k, r, 0] == pytest.approx(hists[r][k][0], abs=0.5)
+            assert cons[k, r, 1] == pytest.approx(cons[k, r, 0], rel=1e-5)
+
+
+def test_region_mlem_matches_oracle_fullbody_reduced():
+    ev = synth.events("fullbody", 300_000, 23)
+    lors = synth.sensitivity_lors("fullbody", 400_000, 23)
+    g = workload_grid("fullbody")
+    margin = 3.0 * SIGMA + 6.0
+    s_ref = oracle.sensitivity(g, lors)
+    img_ref, imgs_ref, hists, codes, offs, idx = oracle.mlem_regions(g, ev.astype(np.float64), s_ref,
+                                                                     FULLBODY_REGIONS, 6.0, margin, 2, SIGMA)
+    with B.Context(geometry("fullbody"), grid_tuple(g), 300.0) as ctx:
+        ctx.sensitivity(lors)
+        img = np.zeros(g.n_vox, np.float32)
+        cons = np.zeros((2, 9, 2))
+        ctx.mlem_regions(B.make_events(ev), FULLBODY_REGIONS, margin, 6.0, 2, img, None, cons)
+    assert rel_l2(img, img_ref) <= 1e-4
+    assert max_rel_above(img, img_ref, 0.01) <= 1e-3
+    total = cons[-1, :, 1].sum()
+    assert total == pytest.approx(cons[-1, :, 0].sum(), rel=1e-5)
+
+
+def test_region_argument_checks():
+    g = workload_grid("tiny")
+    ev = synth.events("tiny", 1000, 3)
+    with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx:
+        ctx.load_events(B.make_events(ev))
+        with pytest.raises(B.ReconError) as e:
+            ctx.split_regions(None, [(0, 10), (12, 48)], 0.0, 6.0)       # not consecutive
+        assert e.value.status == B.RECON_EINVAL
+        with pytest.raises(B.ReconError):
+            ctx.split_regions(None, [(0, 2), (2, 48)], 0.0, 6.0)          # core 8 mm < 2 * shell
+        with pytest.raises(B.ReconError):
+            ctx.split_regions(None, [(0, 49)], 0.0, 6.0)                 # beyond the grid
+        with pytest.raises(B.ReconError):
+            ctx.split_regions(None, [(k, k + 1) for k in range(48)] + [(48, 48)], 0.0, 0.0)  # 49 regions, last empty
+        with pytest.raises(B.ReconError):
+            ctx.mlem_regions(None, [(0, 24), (24, 48)], 0.0, 6.0, 1)      # no sensitivity yet
+        # 48 one-slice regions with no shell is valid (R <= 64)
+        offs = np.zeros(49, np.int64)
+        ctx.split_regions(None, [(k, k + 1) for k in range(48)], 0.0, 0.0, None, offs, None)
+        assert offs[-1] <= 1000

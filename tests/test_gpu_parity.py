@@ -2,9 +2,13 @@
 200k events, 2M sensitivity LORs, 5 iterations), element by element.
 
 Tolerances: relative L2 <= 1e-4 and per-voxel relative error <= 1e-3 on
-voxels above 1% of the maximum for images after the MLEM iterations; the
-single-pass projectors and the sensitivity are held tighter (FP32 walk with
-FP64 or FP32 accumulation against FP64).
+voxels above 1% of the maximum for images after the MLEM iterations.  The
+single passes are held tighter.  Their floor is the FP32 walk: a plane
+crossing tau = (X - c) / u carries about ulp(|X - c|) / |u| of rounding, so
+a line nearly parallel to a voxel plane moves up to ~1e-2 mm of chord
+between two voxels; summed over the LORs of a voxel this stays below 2e-4
+of s_j (sensitivity) and below 1e-4 of p_i (per event), while the relative
+L2 over all voxels or events stays near 1e-6.
 """
 import numpy as np
 import pytest
@@ -33,7 +37,7 @@ def test_sensitivity_matches_oracle(tiny):
     ctx.sensitivity(lors, s)
     assert np.array_equal(s > 0, s_ref > 0) or np.sum((s > 0) != (s_ref > 0)) <= 2
     assert rel_l2(s, s_ref) < 1e-6
-    assert max_rel_above(s, s_ref, 0.01) < 1e-5
+    assert max_rel_above(s, s_ref, 0.01) < 2e-4
 
 
 def test_forward_matches_oracle(tiny):
@@ -45,7 +49,7 @@ def test_forward_matches_oracle(tiny):
     p_ref = oracle.forward(g, ev.astype(np.float64), lam.astype(np.float64), SIGMA)
     sel = p_ref > 1e-3 * p_ref.max()
     assert np.all((p > 0) == (p_ref > 0)) or np.sum((p > 0) != (p_ref > 0)) < 1e-5 * p.size
-    assert np.max(np.abs(p[sel] - p_ref[sel]) / p_ref[sel]) < 2e-5
+    assert np.max(np.abs(p[sel] - p_ref[sel]) / p_ref[sel]) < 1e-4
     assert rel_l2(p, p_ref) < 2e-6
 
 

@@ -178,4 +178,4 @@ def test_kernel_window_changes_the_projector(ctx_tiny):
     ctx.set_kernel_window(3.0)
     p_ref = oracle.forward(g, sub.astype(np.float64), lam.astype(np.float64), SIGMA, K=2.0)
     sel = p_ref > 1e-3 * p_ref.max()
-    assert np.max(np.abs(p[sel] - p_ref[sel]) / p_ref[sel]) < 2e-5
+    assert np.max(np.abs(p[sel] - p_ref[sel]) / p_ref[sel]) < 1e-4

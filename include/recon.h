@@ -92,6 +92,10 @@ typedef struct {
     int32_t blocks_per_sm;     /* > 0 (<= 32): persistent grid of SMs x this with a per-warp work
                                   queue; 0: flat grid, one event per thread */
     int32_t chunk_events;      /* events a warp takes from the queue at a time (multiple of 32) */
+    int32_t cached_pieces;     /* 0: the backprojection walks each line again; 8..256: the first
+                                  walk keeps up to this many (voxel, mass) pieces per event in shared
+                                  memory (8 bytes each, threads_per_block * cached_pieces * 8 <= 200 KB)
+                                  and the backprojection replays them */
 } recon_launch;
 
 typedef struct {

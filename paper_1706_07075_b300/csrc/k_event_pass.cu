@@ -2,10 +2,13 @@
 //   p_i = sum_j a_ij lambda_j            forward projection (gather)
 //   r_i = w_i / p_i  (events with p_i = 0 are skipped)
 //   C_j += a_ij r_i                      backprojection (FP32 reductions)
-// fused in one kernel: one thread walks one event twice, the event's record
-// and walk setup staying in registers between the walks.  The same kernel
-// body, with the pass kind as a template argument, gives the standalone
-// forward and backward projectors.
+// fused in one kernel: one thread walks one event, the event's record and
+// walk setup staying in registers between the two sweeps.  The second sweep
+// either walks the line again or, with a piece cache, replays the voxel
+// indices and masses the first sweep left in shared memory (no second Siddon
+// walk, no second erfc per piece).  The same kernel body, with the pass kind
+// as a template argument, gives the standalone forward and backward
+// projectors.
 //
 // Work distribution: either a flat grid (one event per thread) or a
 // persistent grid of (SMs x blocks_per_sm) blocks in which each warp takes
@@ -49,10 +52,19 @@ __device__ __forceinline__ float gather(const PassArgs& a, bool bf16, long long 
     return __ldg(a.lam + j);
 }
 
+// Per-thread cache of one walk's pieces in shared memory, laid out
+// [piece][thread] so that a warp's accesses fall in distinct banks.
+struct PieceCache {
+    int* j;
+    float* a;
+    int cap;     // pieces per thread (0: no cache)
+    int stride;  // blockDim.x
+};
+
 // One event; returns the weight it adds to N_eff (0 when p_i = 0).
-template <int Kind, int Fmt>
+template <int Kind, int Fmt, bool Cached>
 __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& t, long long i, bool bf16,
-                                          int& region)
+                                          const PieceCache& pc, int& region)
 {
     region = find_region(t, i);
     const GridDev& g = t.grid[region];
@@ -71,24 +83,48 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
         return 0.f;
     }
     float p = 0.f;
-    walk<true>(g, a.tof, w, [&](int j, float m) { p = fmaf(m, gather(a, bf16, base + j), p); });
+    int cnt = 0;
+    const int tid = threadIdx.x;
+    walk<true>(g, a.tof, w, [&](int j, float m) {
+        p = fmaf(m, gather(a, bf16, base + j), p);
+        if (Cached && Kind == PASS_FUSED) {
+            if (cnt < pc.cap) {
+                pc.j[cnt * pc.stride + tid] = j;
+                pc.a[cnt * pc.stride + tid] = m;
+            }
+            ++cnt;
+        }
+    });
     if (Kind == PASS_FORWARD) {
         a.p_out[i] = p;
         return 0.f;
     }
     if (!(p > 0.f)) return 0.f;
     const float r = e.w / p;
-    walk<true>(g, a.tof, w, [&](int j, float m) {
-        if (m != 0.f) atomicAdd(a.C + base + j, m * r);
-    });
+    if (Cached && cnt <= pc.cap) {
+        for (int k = 0; k < cnt; ++k) {
+            const float m = pc.a[k * pc.stride + tid];
+            if (m != 0.f) atomicAdd(a.C + base + pc.j[k * pc.stride + tid], m * r);
+        }
+    } else {
+        walk<true>(g, a.tof, w, [&](int j, float m) {
+            if (m != 0.f) atomicAdd(a.C + base + j, m * r);
+        });
+    }
     return e.w;
 }
 
-template <int Kind, int Fmt, bool Persistent>
-__global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl, int chunk)
+template <int Kind, int Fmt, bool Persistent, bool Cached>
+__global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl, int chunk, int cap)
 {
     __shared__ SharedTable t;
     __shared__ float neff[kMaxRegions];
+    extern __shared__ unsigned char dyn_smem[];
+    PieceCache pc;
+    pc.cap = Cached ? cap : 0;
+    pc.stride = blockDim.x;
+    pc.j = reinterpret_cast<int*>(dyn_smem);
+    pc.a = reinterpret_cast<float*>(dyn_smem) + (size_t)pc.cap * blockDim.x;
     if (threadIdx.x == 0) t.n = tbl.n;
     for (int k = threadIdx.x; k <= tbl.n; k += blockDim.x) t.ev_begin[k] = tbl.ev_begin[k];
     for (int k = threadIdx.x; k < tbl.n; k += blockDim.x) {
@@ -107,7 +143,7 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
             const long long end = min((long long)start + chunk, a.n);
             for (long long i = (long long)start + lane; i < end; i += 32) {
                 int r;
-                float w = do_event<Kind, Fmt>(a, t, i, bf16, r);
+                float w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, r);
                 if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
             }
         }
@@ -115,7 +151,7 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
         const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         if (i < a.n) {
             int r;
-            float w = do_event<Kind, Fmt>(a, t, i, bf16, r);
+            float w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, r);
             if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
         }
     }
@@ -126,17 +162,37 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
     }
 }
 
+constexpr int kMaxCacheBytes = 200 * 1024;
+
+template <int Kind, int Fmt, bool Persistent, bool Cached>
+cudaError_t launch_variant(int blocks, const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl,
+                           cudaStream_t s)
+{
+    auto kern = k_event_pass<Kind, Fmt, Persistent, Cached>;
+    size_t smem = 0;
+    if (Cached) {
+        smem = (size_t)cfg.cache * cfg.threads * 8;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<blocks, cfg.threads, smem, s>>>(a, tbl, cfg.chunk, cfg.cache);
+    return cudaGetLastError();
+}
+
 template <int Kind, int Fmt>
 cudaError_t launch_kind(const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl, int num_sms,
                         cudaStream_t s)
 {
     const int blocks = pass_blocks(cfg, a.n, num_sms);
     if (blocks == 0) return cudaSuccess;
-    if (cfg.blocks_per_sm > 0)
-        k_event_pass<Kind, Fmt, true><<<blocks, cfg.threads, 0, s>>>(a, tbl, cfg.chunk);
-    else
-        k_event_pass<Kind, Fmt, false><<<blocks, cfg.threads, 0, s>>>(a, tbl, cfg.chunk);
-    return cudaGetLastError();
+    if ((size_t)cfg.cache * cfg.threads * 8 > (size_t)kMaxCacheBytes) return cudaErrorInvalidValue;
+    const bool cached = Kind == PASS_FUSED && cfg.cache > 0;
+    if (cfg.blocks_per_sm > 0) {
+        if (cached) return launch_variant<Kind, Fmt, true, true>(blocks, cfg, a, tbl, s);
+        return launch_variant<Kind, Fmt, true, false>(blocks, cfg, a, tbl, s);
+    }
+    if (cached) return launch_variant<Kind, Fmt, false, true>(blocks, cfg, a, tbl, s);
+    return launch_variant<Kind, Fmt, false, false>(blocks, cfg, a, tbl, s);
 }
 
 }  // namespace

@@ -82,8 +82,8 @@ struct recon_ctx {
     // options
     bool bf16 = false, timing = false, graphs = true, autotune = true;
     bool user_cfg = false;
-    LaunchCfg cfg{256, 0, 256};
-    LaunchCfg last_cfg{256, 0, 256};
+    LaunchCfg cfg{256, 0, 0, 0};
+    LaunchCfg last_cfg{256, 0, 0, 0};
     std::map<std::tuple<long long, int, long long, int>, LaunchCfg> tuned;
     recon_stats stats{};
 
@@ -278,7 +278,7 @@ recon_status finish_sensitivity(recon_ctx* ctx)
     return RECON_OK;
 }
 
-LaunchCfg default_cfg() { return LaunchCfg{256, 0, 256}; }
+LaunchCfg default_cfg() { return LaunchCfg{256, 0, 0, 0}; }
 
 bool valid_cfg(const recon_launch* c)
 {
@@ -287,6 +287,8 @@ bool valid_cfg(const recon_launch* c)
     if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return false;
     if (c->blocks_per_sm > 0 && (c->chunk_events < 32 || c->chunk_events % 32 || c->chunk_events > (1 << 20)))
         return false;
+    if (c->cached_pieces != 0 && (c->cached_pieces < 8 || c->cached_pieces > 256)) return false;
+    if ((long long)c->cached_pieces * c->threads_per_block * 8 > 200 * 1024) return false;
     return true;
 }
 
@@ -316,12 +318,11 @@ PassArgs base_args(recon_ctx* ctx, const void* events, long long n)
 // accumulates into C, which the caller clears afterwards; lambda is untouched.
 recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, LaunchCfg* best)
 {
-    std::vector<LaunchCfg> cands;
-    for (int th : {128, 256}) {
-        cands.push_back(LaunchCfg{th, 0, 0});
-        for (int bps : {2048 / th / 2, 2048 / th})
-            for (int ch : {64, 256}) cands.push_back(LaunchCfg{th, bps, ch});
-    }
+    // flat and persistent grids, walking twice or replaying a shared-memory piece cache
+    const std::vector<LaunchCfg> cands = {
+        {128, 0, 0, 0},  {256, 0, 0, 0},   {128, 8, 64, 0}, {256, 4, 64, 0}, {256, 8, 256, 0},
+        {64, 0, 0, 64},  {128, 0, 0, 48},  {128, 0, 0, 64}, {64, 6, 64, 64}, {128, 3, 64, 64},
+    };
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -385,8 +386,8 @@ recon_status enqueue_iteration(recon_ctx* ctx, const IterPlan& p)
 std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
 {
     char buf[512];
-    snprintf(buf, sizeof buf, "%p %lld %d %d %d %d %p %p %p %p %p %d %d %d %p %p %d %p %lld %d %a %a %a", p.a.events,
-             p.a.n, ctx->fmt, p.cfg.threads, p.cfg.blocks_per_sm, p.cfg.chunk, (void*)p.lam, (void*)p.C,
+    snprintf(buf, sizeof buf, "%p %lld %d %d %d %d %d %p %p %p %p %p %d %d %d %p %p %d %p %lld %d %a %a %a",
+             p.a.events, p.a.n, ctx->fmt, p.cfg.threads, p.cfg.blocks_per_sm, p.cfg.chunk, p.cfg.cache, (void*)p.lam, (void*)p.C,
              (const void*)p.s32, (void*)p.bf16, (void*)p.reg_vox_dev, p.n_regions, p.upd_bpr, p.pass_blocks,
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
@@ -679,7 +680,8 @@ recon_status recon_set_launch(recon_ctx* ctx, const recon_launch* cfg)
     }
     if (!valid_cfg(cfg)) return fail(ctx, RECON_EINVAL, "invalid launch configuration");
     ctx->user_cfg = true;
-    ctx->cfg = LaunchCfg{cfg->threads_per_block, cfg->blocks_per_sm, cfg->blocks_per_sm > 0 ? cfg->chunk_events : 0};
+    ctx->cfg = LaunchCfg{cfg->threads_per_block, cfg->blocks_per_sm, cfg->blocks_per_sm > 0 ? cfg->chunk_events : 0,
+                         cfg->cached_pieces};
     return RECON_OK;
 }
 
@@ -689,6 +691,7 @@ recon_status recon_get_launch(const recon_ctx* ctx, recon_launch* out)
     out->threads_per_block = ctx->last_cfg.threads;
     out->blocks_per_sm = ctx->last_cfg.blocks_per_sm;
     out->chunk_events = ctx->last_cfg.chunk;
+    out->cached_pieces = ctx->last_cfg.cache;
     return RECON_OK;
 }
 

@@ -37,6 +37,7 @@ struct LaunchCfg {
     int threads;       // threads per block (64, 128, 256)
     int blocks_per_sm; // persistent grid when > 0; flat one-event-per-thread grid when 0
     int chunk;         // events per work-queue grab (persistent), multiple of 32
+    int cache;         // pieces per thread kept in shared memory for the backprojection (0: walk twice)
 };
 
 struct PassArgs {

@@ -103,18 +103,21 @@ def test_one_voxel_grid_closed_form():
         assert img[0] == pytest.approx(n / 12.5, rel=1e-6)
 
 
-@pytest.mark.parametrize("cfg", [(64, 0, 0), (128, 0, 0), (256, 4, 32), (128, 16, 256), (256, 1, 1024)])
+@pytest.mark.parametrize("cfg", [(64, 0, 0, 0), (128, 0, 0, 0), (256, 4, 32, 0), (128, 16, 256, 0),
+                                 (256, 1, 1024, 0), (128, 0, 0, 64), (64, 6, 64, 64), (128, 0, 0, 8),
+                                 (256, 2, 64, 96)])
 def test_launch_configurations_agree(ctx_tiny, cfg):
+    # (128, 0, 0, 8) caches fewer pieces than most walks have: those events walk twice
     ctx, g = ctx_tiny
     ev, _ = tiny_inputs()
     ctx.set_launch(None)
     ref = np.zeros(g.n_vox, np.float32)
-    ctx.set_launch(256, 0, 0)
+    ctx.set_launch(256, 0, 0, 0)
     ctx.mlem(B.make_events(ev), 2, None, ref, None)
     ctx.set_launch(*cfg)
     img = np.zeros(g.n_vox, np.float32)
     ctx.mlem(None, 2, None, img, None)
-    assert ctx.get_launch() == (cfg[0], cfg[1], cfg[2] if cfg[1] else 0)
+    assert ctx.get_launch() == (cfg[0], cfg[1], cfg[2] if cfg[1] else 0, cfg[3])
     ctx.set_launch(None)
     assert rel_l2(img, ref) < 1e-6
 
@@ -151,6 +154,10 @@ def test_call_order_and_argument_errors():
             ctx.set_launch(100, 0, 0)
         with pytest.raises(B.ReconError):
             ctx.set_launch(256, 4, 48)
+        with pytest.raises(B.ReconError):
+            ctx.set_launch(256, 0, 0, 128)          # 256 KB of shared memory
+        with pytest.raises(B.ReconError):
+            ctx.set_launch(128, 0, 0, 4)            # fewer than 8 pieces
         with pytest.raises(B.ReconError):
             ctx.set_kernel_window(0.1)
         bad = B.make_events(ev)

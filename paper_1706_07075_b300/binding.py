@@ -154,6 +154,10 @@ def make_events(data, packed=False, weight=None, lattice_mm=0.05):
     (n, 8) int16 array/tensor of packed records.  The struct keeps `data`
     and `weight` alive."""
     ev = recon_events()
+    if isinstance(data, np.ndarray):
+        data = np.ascontiguousarray(data)
+    elif hasattr(data, "contiguous"):
+        data = data.contiguous()
     if packed:
         n = int(data.shape[0])
         ev.fmt = RECON_EV_PACKED_I16_F16

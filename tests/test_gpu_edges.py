@@ -22,7 +22,7 @@ def odd_events():
     rows.append([xp, -150.0, 3.0, xp, 150.0, -7.0, 12.0])        # in the x-plane
     rows.append([xp, g.oy + 7 * g.vy, -200.0, xp, g.oy + 7 * g.vy, 200.0, -30.0])  # on an edge
     rows.append([-150.0, 2.0, 2.0, 150.0, 2.0, 2.0, 5.0])        # along x
-    rows.append([1.0, 1.0, -200.0, 1.0, 1.0, 200.0, 40.0])       # along z
+    rows.append([1.0, 1.0, -200.0, 1.0, 1.0, 200.0, 20.0])       # along z
     rows.append([-150.0, 90.0, 0.0, 150.0, 90.0, 0.0, 0.0])      # misses the grid (y = 90 > 64)
     rows.append([-150.0, 0.0, 0.0, 150.0, 0.0, 0.0, 500.0])      # TOF point far outside
     rows.append([5.0, 5.0, 5.0, 5.0, 5.0, 5.0, 0.0])             # P1 == P2
@@ -97,7 +97,7 @@ def test_one_voxel_grid_closed_form():
         n = 37
         u = rng.normal(size=(n, 3))
         u /= np.linalg.norm(u, axis=1, keepdims=True)
-        ev = np.concatenate([(50 * u).T, (-50 * u).T, rng.uniform(-3, 3, (1, n))]).astype(np.float32)
+        ev = np.ascontiguousarray(np.concatenate([(50 * u).T, (-50 * u).T, rng.uniform(-3, 3, (1, n))]), np.float32)
         img = np.zeros(1, np.float32)
         ctx.mlem(B.make_events(ev), 1, None, img, None)
         assert img[0] == pytest.approx(n / 12.5, rel=1e-6)

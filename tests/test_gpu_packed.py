@@ -64,8 +64,10 @@ def test_packed_events_bf16_gather_error_is_bounded(packed_case):
     err = rel_l2(img, lam_q)
     print(f"\npacked BF16-gather: rel L2 vs dequantized oracle {err:.2e}, vs unquantized {rel_l2(img, lam_f):.2e}")
     assert err <= 5e-3
-    # backprojection and the update stay FP32/FP64: counts are still conserved
-    assert cons[-1, 1] == pytest.approx(cons[-1, 0], rel=1e-5)
+    # p_i comes from the BF16 copy while the update multiplies the FP32 image, so
+    # sum_j s_j lambda_j = sum_i w_i p_i(FP32) / p_i(BF16) matches N_eff only to
+    # the BF16 rounding of p_i, averaged over the events
+    assert cons[-1, 1] == pytest.approx(cons[-1, 0], rel=1e-3)
 
 
 def test_fp32_events_bf16_gather(packed_case):

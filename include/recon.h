@@ -129,8 +129,9 @@ recon_status recon_create(const recon_geometry* geom, const recon_grid* grid, do
 /* Release everything the context owns.  NULL-safe. */
 void recon_destroy(recon_ctx* ctx);
 
-/* Message of the last failed call on ctx (ctx NULL: of the last failed recon_create
- * on this thread).  Valid until the next call on the same context. */
+/* Message of the last failed call on ctx (ctx NULL: of the last failed recon_create or
+ * recon_split_regions_noalloc on this thread).  Valid until the next call on the same
+ * context. */
 const char* recon_last_error(const recon_ctx* ctx);
 
 /* Stream for all device work of ctx (a cudaStream_t; NULL restores the context's own
@@ -247,6 +248,35 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
 /* Total voxels of the region slabs of a division (for sizing region_images_out). */
 recon_status recon_region_slab_voxels(const recon_ctx* ctx, int32_t n_regions, const recon_region* regions,
                                       double margin_mm, int64_t* n_vox_out);
+
+/* ------------------------------------------------- allocation-free split */
+
+/* The paper has no counterpart of this call: it is a service for callers that cannot
+ * allocate device memory — code recording a CUDA graph that must not gain allocation
+ * nodes, or a process whose GPU memory belongs to another allocator (a framework's
+ * caching pool, an acquisition service that reserves everything at start-up).
+ *
+ * Same split as recon_split_regions (same codes, offsets and ascending index lists),
+ * with no context and no cudaMalloc/cudaFree: the caller passes device inputs and
+ * outputs, and the per-tile counters live in one 8 MiB static device array that every
+ * GPU loading this library keeps until the process exits.
+ *   grid:        only nz, vz and oz are used (the z boundaries z_b[r] = oz + z_lo*vz).
+ *   events:      fmt RECON_EV_F32_SOA with on_device = 1 (the weight is ignored).
+ *   code_out:    n bytes, device.      idx_out: idx_capacity int32, device.
+ *   offsets_out: n_regions+1 int64, host.
+ *   cuda_stream: the stream to run on (NULL: the legacy default stream); the call
+ *                synchronises it before returning.
+ * Limit: n <= 32768 * floor((8 MiB - 1032 B) / (12 * n_regions + 4)) events and n < 2^31
+ * (any n below 2^31 for up to 10 regions, about 356 M events for 64); larger n returns
+ * RECON_EINVAL with a message.  The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (other host threads, other streams) race and must be serialised
+ * by the caller.  Errors: EINVAL (arguments, limit, idx_out too small), ECUDA; the
+ * message is available from recon_last_error(NULL). */
+recon_status recon_split_regions_noalloc(const recon_grid* grid, const recon_events* events, int32_t n_regions,
+                                         const recon_region* regions, double shell_mm, uint8_t* code_out,
+                                         int64_t* offsets_out, int32_t* idx_out, int64_t idx_capacity,
+                                         void* cuda_stream);
 
 #ifdef __cplusplus
 }

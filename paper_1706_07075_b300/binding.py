@@ -92,6 +92,8 @@ SIGNATURES = {
                                      C.c_double, C.c_double, C.c_int32, _VP, _VP, _VP]),
     "recon_region_slab_voxels": (C.c_int, [_CTX, C.c_int32, C.POINTER(recon_region), C.c_double,
                                            C.POINTER(C.c_int64)]),
+    "recon_split_regions_noalloc": (C.c_int, [C.POINTER(recon_grid), C.POINTER(recon_events), C.c_int32,
+                                              C.POINTER(recon_region), C.c_double, _VP, _VP, _VP, C.c_int64, _VP]),
 }
 
 _lib = None
@@ -306,6 +308,15 @@ def recon_region_slab_voxels(ctx, regions, margin_mm):
     out = C.c_int64()
     check(ctx, load().recon_region_slab_voxels(ctx, len(regions), arr, float(margin_mm), C.byref(out)))
     return out.value
+
+
+def recon_split_regions_noalloc(grid, events, regions, shell_mm, code_out, offsets_out, idx_out, idx_capacity,
+                                stream=None):
+    """Allocation-free region split (no context): device events/codes/indices, host offsets."""
+    arr = regions_array(regions)
+    return check(None, load().recon_split_regions_noalloc(C.byref(grid), C.byref(events), len(regions), arr,
+                                                          float(shell_mm), ptr(code_out), ptr(offsets_out),
+                                                          ptr(idx_out), int(idx_capacity), stream))
 
 
 # ------------------------------------------------------------ convenience

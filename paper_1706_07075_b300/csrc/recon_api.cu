@@ -644,6 +644,15 @@ const char* recon_last_error(const recon_ctx* ctx)
     return ctx->err.c_str();
 }
 
+}  // extern "C"
+
+namespace recon {
+// Message reported by recon_last_error(NULL) for calls that have no context.
+void set_thread_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace recon
+
+extern "C" {
+
 recon_status recon_set_stream(recon_ctx* ctx, void* cuda_stream)
 {
     CHECK_CTX();

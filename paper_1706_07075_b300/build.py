@@ -48,8 +48,29 @@ def _compile(src, verbose):
     return obj, r.stderr
 
 
+PROBE_DIR = os.path.join(CSRC, "probe")
+PROBE_LIB = os.path.join(HERE, "librecon_probe.so")
+
+
+def build_probe(force=False):
+    """Compile librecon_probe.so (roofline probes used by bench.py)."""
+    srcs = sorted(glob.glob(os.path.join(PROBE_DIR, "*.cu")))
+    deps = srcs + glob.glob(os.path.join(PROBE_DIR, "*.h"))
+    if not force and os.path.exists(PROBE_LIB) and all(os.path.getmtime(p) <= os.path.getmtime(PROBE_LIB) for p in deps):
+        return PROBE_LIB
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    cmd = [NVCC] + ARCH + FLAGS + ["-I" + PROBE_DIR, "-shared", "-cudart", "shared", "-o", tmp] + srcs + \
+        ["-Xlinker", "-rpath," + os.path.join(CUDA, "lib64")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"probe build failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def build(force=False, verbose=False):
     """Compile and link librecon.so unless it is newer than every source."""
+    build_probe(force)
     if not force and up_to_date():
         return LIB
     os.makedirs(OBJ_DIR, exist_ok=True)

@@ -1,0 +1,109 @@
+// Hardware probes that measure the roofline denominators of the MLEM event
+// pass on the running GPU (not part of the reconstruction): the rate of
+// scattered FP32 reductions into an L2-resident image, the rate of scattered
+// 4-byte gathers from it, and the FP32 issue rate of the pieces' Gaussian
+// tail evaluation.  Each probe times itself with CUDA events on `stream`
+// and returns operations per second.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "recon_probe.h"
+
+namespace {
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Each thread issues `per_thread` reductions to pseudo-random words of img.
+// With `runs` > 1 consecutive reductions of a thread go to consecutive words
+// (a run of a Siddon walk along x), else every address is independent.
+__global__ void k_red(float* img, uint32_t n_words, int per_thread, int runs)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t h = hash32(t * 0x9e3779b9u + 17u);
+    for (int k = 0; k < per_thread; k += runs) {
+        h = hash32(h + (uint32_t)k);
+        const uint32_t base = h % n_words;
+        for (int q = 0; q < runs && k + q < per_thread; ++q) atomicAdd(img + (base + q) % n_words, 1e-7f);
+    }
+}
+
+__global__ void k_gather(const float* img, uint32_t n_words, int per_thread, float* sink)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t h = hash32(t * 0x85ebca6bu + 3u);
+    float acc = 0.f;
+    for (int k = 0; k < per_thread; ++k) {
+        h = hash32(h + (uint32_t)k);
+        acc += __ldg(img + h % n_words);
+    }
+    if (acc == 1234.5f) sink[t] = acc;
+}
+
+__global__ void k_erfc(int per_thread, float* sink)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    float x = 0.001f * (t & 1023), acc = 0.f;
+    for (int k = 0; k < per_thread; ++k) {
+        acc += erfcf(x);
+        x += 0.0037f;
+        if (x > 2.2f) x -= 2.2f;
+    }
+    if (acc == 1234.5f) sink[t] = acc;
+}
+
+template <class F>
+int time_it(cudaStream_t s, F&& launch, double ops, double* out_ops_per_s)
+{
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return 3;
+    launch();  // warm-up
+    cudaEventRecord(a, s);
+    launch();
+    cudaEventRecord(b, s);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return 3;
+    *out_ops_per_s = ops / (ms * 1e-3);
+    return 0;
+}
+
+}  // namespace
+
+extern "C" int recon_probe_l2_red(float* img, int64_t n_words, int32_t runs, void* stream, double* ops_per_s)
+{
+    if (!img || n_words <= 0 || n_words >= (1LL << 32) || runs < 1 || !ops_per_s) return 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int threads = 256, blocks = 148 * 64, per_thread = 256;
+    return time_it(s, [&] { k_red<<<blocks, threads, 0, s>>>(img, (uint32_t)n_words, per_thread, runs); },
+                   (double)blocks * threads * per_thread, ops_per_s);
+}
+
+extern "C" int recon_probe_gather(const float* img, int64_t n_words, float* sink, void* stream, double* ops_per_s)
+{
+    if (!img || !sink || n_words <= 0 || n_words >= (1LL << 32) || !ops_per_s) return 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int threads = 256, blocks = 148 * 64, per_thread = 256;
+    return time_it(s, [&] { k_gather<<<blocks, threads, 0, s>>>(img, (uint32_t)n_words, per_thread, sink); },
+                   (double)blocks * threads * per_thread, ops_per_s);
+}
+
+extern "C" int recon_probe_erfc(float* sink, void* stream, double* ops_per_s)
+{
+    if (!sink || !ops_per_s) return 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int threads = 256, blocks = 148 * 64, per_thread = 2048;
+    return time_it(s, [&] { k_erfc<<<blocks, threads, 0, s>>>(per_thread, sink); },
+                   (double)blocks * threads * per_thread, ops_per_s);
+}

@@ -1,0 +1,35 @@
+/*
+ * librecon_probe: measurement probes for the roofline of the MLEM event pass
+ * (bench.py).  They measure the running GPU and have no counterpart in the
+ * paper; the reconstruction never calls them.
+ *
+ * Every probe launches its own kernels on `stream` (a cudaStream_t, NULL =
+ * legacy default stream), runs once to warm up and once timed with CUDA events,
+ * writes operations per second to *ops_per_s and returns 0 (1: bad argument,
+ * 3: CUDA error).  Buffers are caller-owned device memory.
+ */
+#ifndef RECON_PROBE_H
+#define RECON_PROBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Scattered FP32 reductions (red.global.add.f32) into img[0..n_words) at hashed
+ * addresses, `runs` consecutive words per hashed address (1: all independent).
+ * 148*64*256*256 reductions per run; img is modified. */
+int recon_probe_l2_red(float* img, int64_t n_words, int32_t runs, void* stream, double* ops_per_s);
+
+/* Scattered 4-byte read-only gathers from img[0..n_words); sink: 148*64*256 floats. */
+int recon_probe_gather(const float* img, int64_t n_words, float* sink, void* stream, double* ops_per_s);
+
+/* erfcf evaluations per second (FP32 ALU); sink: 148*64*256 floats. */
+int recon_probe_erfc(float* sink, void* stream, double* ops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECON_PROBE_H */

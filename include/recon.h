@@ -96,6 +96,9 @@ typedef struct {
                                   walk keeps up to this many (voxel, mass) pieces per event in shared
                                   memory (8 bytes each, threads_per_block * cached_pieces * 8 <= 200 KB)
                                   and the backprojection replays them */
+    int32_t tail_eval;         /* Gaussian tails erfc(|tau|/(sigma sqrt 2)) at the piece boundaries from
+                                  0: a shared-memory cubic Hermite table of erfc (step 1/64, error
+                                  below 1e-8), 1: CUDA's erfcf */
 } recon_launch;
 
 typedef struct {

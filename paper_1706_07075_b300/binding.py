@@ -48,7 +48,7 @@ class recon_region(C.Structure):
 
 class recon_launch(C.Structure):
     _fields_ = [("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk_events", C.c_int32),
-                ("cached_pieces", C.c_int32)]
+                ("cached_pieces", C.c_int32), ("tail_eval", C.c_int32)]
 
 
 class recon_info(C.Structure):
@@ -219,17 +219,17 @@ def recon_set_gather_bf16(ctx, on):
     return check(ctx, load().recon_set_gather_bf16(ctx, int(bool(on))))
 
 
-def recon_set_launch(ctx, threads_per_block=None, blocks_per_sm=0, chunk_events=0, cached_pieces=0):
+def recon_set_launch(ctx, threads_per_block=None, blocks_per_sm=0, chunk_events=0, cached_pieces=0, tail_eval=0):
     if threads_per_block is None:
         return check(ctx, load().recon_set_launch(ctx, None))
-    cfg = recon_launch(threads_per_block, blocks_per_sm, chunk_events, cached_pieces)
+    cfg = recon_launch(threads_per_block, blocks_per_sm, chunk_events, cached_pieces, tail_eval)
     return check(ctx, load().recon_set_launch(ctx, C.byref(cfg)))
 
 
 def recon_get_launch(ctx):
     cfg = recon_launch()
     check(ctx, load().recon_get_launch(ctx, C.byref(cfg)))
-    return (cfg.threads_per_block, cfg.blocks_per_sm, cfg.chunk_events, cfg.cached_pieces)
+    return (cfg.threads_per_block, cfg.blocks_per_sm, cfg.chunk_events, cfg.cached_pieces, cfg.tail_eval)
 
 
 def recon_set_timing(ctx, on):

@@ -16,6 +16,7 @@
 // batched (region-divided) form are stored region by region; a thread looks
 // its region up in a shared-memory table of event ranges and slab grids.
 #include <algorithm>
+#include <type_traits>
 
 #include "recon_device.cuh"
 
@@ -62,9 +63,9 @@ struct PieceCache {
 };
 
 // One event; returns the weight it adds to N_eff (0 when p_i = 0).
-template <int Kind, int Fmt, bool Cached>
+template <int Kind, int Fmt, bool Cached, class TailF>
 __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& t, long long i, bool bf16,
-                                          const PieceCache& pc, int& region)
+                                          const PieceCache& pc, const TailF& tail, int& region)
 {
     region = find_region(t, i);
     const GridDev& g = t.grid[region];
@@ -77,7 +78,7 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
     if (Kind == PASS_BACK) {
         const float r = a.r_in[i];
         if (r != 0.f)
-            walk<true>(g, a.tof, w, [&](int j, float m) {
+            walk<true>(g, a.tof, tail, w, [&](int j, float m) {
                 if (m != 0.f) atomicAdd(a.C + base + j, m * r);
             });
         return 0.f;
@@ -85,7 +86,7 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
     float p = 0.f;
     int cnt = 0;
     const int tid = threadIdx.x;
-    walk<true>(g, a.tof, w, [&](int j, float m) {
+    walk<true>(g, a.tof, tail, w, [&](int j, float m) {
         p = fmaf(m, gather(a, bf16, base + j), p);
         if (Cached && Kind == PASS_FUSED) {
             if (cnt < pc.cap) {
@@ -107,18 +108,19 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
             if (m != 0.f) atomicAdd(a.C + base + pc.j[k * pc.stride + tid], m * r);
         }
     } else {
-        walk<true>(g, a.tof, w, [&](int j, float m) {
+        walk<true>(g, a.tof, tail, w, [&](int j, float m) {
             if (m != 0.f) atomicAdd(a.C + base + j, m * r);
         });
     }
     return e.w;
 }
 
-template <int Kind, int Fmt, bool Persistent, bool Cached>
+template <int Kind, int Fmt, bool Persistent, bool Cached, bool Table>
 __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl, int chunk, int cap)
 {
     __shared__ SharedTable t;
     __shared__ float neff[kMaxRegions];
+    __shared__ float4 phi[kMaxTailTable];
     extern __shared__ unsigned char dyn_smem[];
     PieceCache pc;
     pc.cap = Cached ? cap : 0;
@@ -131,7 +133,18 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
         t.grid[k] = tbl.grid[k];
         neff[k] = 0.f;
     }
+    if (Table)
+        for (int k = threadIdx.x; k < a.tail_n; k += blockDim.x) phi[k] = a.tail_tab[k];
     __syncthreads();
+    using TailF = typename std::conditional<Table, TailTable, TailErfc>::type;
+    TailF tail;
+    if constexpr (Table) {
+        tail.tab = phi;
+        tail.inv_h_scale = a.tail_inv_h_scale;
+        tail.last = a.tail_n - 1;
+    } else {
+        tail.inv_sigma_sqrt2 = a.tof.inv_sigma_sqrt2;
+    }
     const bool bf16 = a.lam_bf16 != nullptr;
     const int lane = threadIdx.x & 31;
     if (Persistent) {
@@ -143,7 +156,7 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
             const long long end = min((long long)start + chunk, a.n);
             for (long long i = (long long)start + lane; i < end; i += 32) {
                 int r;
-                float w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, r);
+                float w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, tail, r);
                 if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
             }
         }
@@ -151,7 +164,7 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
         const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
         if (i < a.n) {
             int r;
-            float w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, r);
+            float w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, tail, r);
             if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
         }
     }
@@ -164,11 +177,11 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
 
 constexpr int kMaxCacheBytes = 200 * 1024;
 
-template <int Kind, int Fmt, bool Persistent, bool Cached>
+template <int Kind, int Fmt, bool Persistent, bool Cached, bool Table>
 cudaError_t launch_variant(int blocks, const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl,
                            cudaStream_t s)
 {
-    auto kern = k_event_pass<Kind, Fmt, Persistent, Cached>;
+    auto kern = k_event_pass<Kind, Fmt, Persistent, Cached, Table>;
     size_t smem = 0;
     if (Cached) {
         smem = (size_t)cfg.cache * cfg.threads * 8;
@@ -179,6 +192,20 @@ cudaError_t launch_variant(int blocks, const LaunchCfg& cfg, const PassArgs& a, 
     return cudaGetLastError();
 }
 
+template <int Kind, int Fmt, bool Table>
+cudaError_t launch_tail(int blocks, const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl, cudaStream_t s)
+{
+    const bool persistent = cfg.blocks_per_sm > 0;
+    if constexpr (Kind == PASS_FUSED) {
+        if (cfg.cache > 0) {
+            if (persistent) return launch_variant<Kind, Fmt, true, true, Table>(blocks, cfg, a, tbl, s);
+            return launch_variant<Kind, Fmt, false, true, Table>(blocks, cfg, a, tbl, s);
+        }
+    }
+    if (persistent) return launch_variant<Kind, Fmt, true, false, Table>(blocks, cfg, a, tbl, s);
+    return launch_variant<Kind, Fmt, false, false, Table>(blocks, cfg, a, tbl, s);
+}
+
 template <int Kind, int Fmt>
 cudaError_t launch_kind(const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl, int num_sms,
                         cudaStream_t s)
@@ -186,13 +213,10 @@ cudaError_t launch_kind(const LaunchCfg& cfg, const PassArgs& a, const RegionTab
     const int blocks = pass_blocks(cfg, a.n, num_sms);
     if (blocks == 0) return cudaSuccess;
     if ((size_t)cfg.cache * cfg.threads * 8 > (size_t)kMaxCacheBytes) return cudaErrorInvalidValue;
-    const bool cached = Kind == PASS_FUSED && cfg.cache > 0;
-    if (cfg.blocks_per_sm > 0) {
-        if (cached) return launch_variant<Kind, Fmt, true, true>(blocks, cfg, a, tbl, s);
-        return launch_variant<Kind, Fmt, true, false>(blocks, cfg, a, tbl, s);
-    }
-    if (cached) return launch_variant<Kind, Fmt, false, true>(blocks, cfg, a, tbl, s);
-    return launch_variant<Kind, Fmt, false, false>(blocks, cfg, a, tbl, s);
+    const bool table = cfg.tail == TAIL_TABLE;
+    if (table && (!a.tail_tab || a.tail_n < 2 || a.tail_n > kMaxTailTable)) return cudaErrorInvalidValue;
+    if (table) return launch_tail<Kind, Fmt, true>(blocks, cfg, a, tbl, s);
+    return launch_tail<Kind, Fmt, false>(blocks, cfg, a, tbl, s);
 }
 
 }  // namespace

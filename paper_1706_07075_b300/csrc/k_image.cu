@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(256) k_sensitivity(const float* __restrict__ l
     const float inf = __int_as_float(0x7f800000);
     Walk w = make_walk(g, c, u, -inf, inf);
     TofDev none{};
-    walk<false>(g, none, w, [&](int j, float len) {
+    TailErfc unused{0.f};
+    walk<false>(g, none, unused, w, [&](int j, float len) {
         if (len > 0.f) atomicAdd(s + j, (double)len);
     });
 }

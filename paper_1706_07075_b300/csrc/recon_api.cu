@@ -79,11 +79,16 @@ struct recon_ctx {
     // per-call scratch
     DevBuf pass_partial, upd_partial, work, iter, hist, reg_vox, red_partial, vec;
 
+    // erfc interpolation table for the TOF kernel (rebuilt when K changes)
+    DevBuf tail_tab;
+    int tail_n = 0;
+    float tail_inv_h_scale = 0.f;
+
     // options
     bool bf16 = false, timing = false, graphs = true, autotune = true;
     bool user_cfg = false;
-    LaunchCfg cfg{256, 0, 0, 0};
-    LaunchCfg last_cfg{256, 0, 0, 0};
+    LaunchCfg cfg{128, 0, 0, 0, TAIL_TABLE};
+    LaunchCfg last_cfg{128, 0, 0, 0, TAIL_TABLE};
     std::map<std::tuple<long long, int, long long, int>, LaunchCfg> tuned;
     recon_stats stats{};
 
@@ -278,7 +283,34 @@ recon_status finish_sensitivity(recon_ctx* ctx)
     return RECON_OK;
 }
 
-LaunchCfg default_cfg() { return LaunchCfg{256, 0, 0, 0}; }
+LaunchCfg default_cfg() { return LaunchCfg{128, 0, 0, 0, TAIL_TABLE}; }
+
+// Piecewise cubic Hermite table of erfc on [0, K/sqrt 2 + h], h = 1/64, from
+// libm's erfc and the derivative -2/sqrt(pi) exp(-x^2) (FP64, host).
+recon_status build_tail_table(recon_ctx* ctx)
+{
+    const double h = 1.0 / 64.0;
+    const double xmax = ctx->k_sigma / std::sqrt(2.0);
+    const int n = (int)std::ceil(xmax / h) + 1;
+    if (n > kMaxTailTable) return fail(ctx, RECON_EINVAL, "kernel window too wide for the erfc table");
+    std::vector<float> tab(4 * (size_t)n);
+    const double two_over_sqrt_pi = 2.0 / std::sqrt(std::acos(-1.0));
+    for (int k = 0; k < n; ++k) {
+        const double x0 = k * h, x1 = (k + 1) * h;
+        const double f0 = std::erfc(x0), f1 = std::erfc(x1);
+        const double d0 = -h * two_over_sqrt_pi * std::exp(-x0 * x0);
+        const double d1 = -h * two_over_sqrt_pi * std::exp(-x1 * x1);
+        tab[4 * k + 0] = (float)f0;
+        tab[4 * k + 1] = (float)d0;
+        tab[4 * k + 2] = (float)(3.0 * (f1 - f0) - 2.0 * d0 - d1);
+        tab[4 * k + 3] = (float)(2.0 * (f0 - f1) + d0 + d1);
+    }
+    CK(ensure(ctx->tail_tab, sizeof(float) * tab.size()));
+    CK(cudaMemcpy(ctx->tail_tab.p, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice));
+    ctx->tail_n = n;
+    ctx->tail_inv_h_scale = (float)(1.0 / (h * ctx->sigma_mm * std::sqrt(2.0)));
+    return RECON_OK;
+}
 
 bool valid_cfg(const recon_launch* c)
 {
@@ -289,6 +321,7 @@ bool valid_cfg(const recon_launch* c)
         return false;
     if (c->cached_pieces != 0 && (c->cached_pieces < 8 || c->cached_pieces > 256)) return false;
     if ((long long)c->cached_pieces * c->threads_per_block * 8 > 200 * 1024) return false;
+    if (c->tail_eval != TAIL_TABLE && c->tail_eval != TAIL_ERFC) return false;
     return true;
 }
 
@@ -311,6 +344,9 @@ PassArgs base_args(recon_ctx* ctx, const void* events, long long n)
     a.n = n;
     a.lattice = (float)ctx->lattice;
     a.tof = make_tof(ctx);
+    a.tail_tab = ctx->tail_tab.as<float4>();
+    a.tail_n = ctx->tail_n;
+    a.tail_inv_h_scale = ctx->tail_inv_h_scale;
     return a;
 }
 
@@ -320,8 +356,9 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
 {
     // flat and persistent grids, walking twice or replaying a shared-memory piece cache
     const std::vector<LaunchCfg> cands = {
-        {128, 0, 0, 0},  {256, 0, 0, 0},   {128, 8, 64, 0}, {256, 4, 64, 0}, {256, 8, 256, 0},
-        {64, 0, 0, 64},  {128, 0, 0, 48},  {128, 0, 0, 64}, {64, 6, 64, 64}, {128, 3, 64, 64},
+        {128, 0, 0, 0, TAIL_TABLE}, {256, 0, 0, 0, TAIL_TABLE}, {64, 0, 0, 0, TAIL_TABLE},
+        {128, 8, 64, 0, TAIL_TABLE}, {256, 4, 256, 0, TAIL_TABLE}, {64, 0, 0, 64, TAIL_TABLE},
+        {128, 0, 0, 48, TAIL_TABLE}, {128, 0, 0, 0, TAIL_ERFC},
     };
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -387,7 +424,7 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
 {
     char buf[512];
     snprintf(buf, sizeof buf, "%p %lld %d %d %d %d %d %p %p %p %p %p %d %d %d %p %p %d %p %lld %d %a %a %a",
-             p.a.events, p.a.n, ctx->fmt, p.cfg.threads, p.cfg.blocks_per_sm, p.cfg.chunk, p.cfg.cache, (void*)p.lam, (void*)p.C,
+             p.a.events, p.a.n, ctx->fmt, p.cfg.threads, p.cfg.blocks_per_sm, p.cfg.chunk, p.cfg.cache * 2 + p.cfg.tail, (void*)p.lam, (void*)p.C,
              (const void*)p.s32, (void*)p.bf16, (void*)p.reg_vox_dev, p.n_regions, p.upd_bpr, p.pass_blocks,
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
@@ -614,6 +651,11 @@ recon_status recon_create(const recon_geometry* geom, const recon_grid* grid, do
     if ((e = ensure(ctx->C, sizeof(float) * nv)) != cudaSuccess) return bail(e, "allocating C");
     if ((e = ensure(ctx->work, 64)) != cudaSuccess) return bail(e, "allocating work counter");
     if ((e = ensure(ctx->iter, 64)) != cudaSuccess) return bail(e, "allocating iteration counter");
+    if (build_tail_table(ctx) != RECON_OK) {
+        g_create_error = ctx->err;
+        recon_destroy(ctx);
+        return RECON_ECUDA;
+    }
     if ((e = cudaMemsetAsync(ctx->s64.p, 0, sizeof(double) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemsetAsync(ctx->s32.p, 0, sizeof(float) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemsetAsync(ctx->lam.p, 0, sizeof(float) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
@@ -666,7 +708,14 @@ recon_status recon_set_kernel_window(recon_ctx* ctx, double k_sigma)
 {
     CHECK_CTX();
     if (!(k_sigma >= 0.5 && k_sigma <= 8.0)) return fail(ctx, RECON_EINVAL, "k_sigma must be in [0.5, 8]");
+    const double old = ctx->k_sigma;
     ctx->k_sigma = k_sigma;
+    recon_status st = build_tail_table(ctx);
+    if (st != RECON_OK) {
+        ctx->k_sigma = old;
+        build_tail_table(ctx);
+        return st;
+    }
     invalidate_graph(ctx);
     return RECON_OK;
 }
@@ -690,7 +739,7 @@ recon_status recon_set_launch(recon_ctx* ctx, const recon_launch* cfg)
     if (!valid_cfg(cfg)) return fail(ctx, RECON_EINVAL, "invalid launch configuration");
     ctx->user_cfg = true;
     ctx->cfg = LaunchCfg{cfg->threads_per_block, cfg->blocks_per_sm, cfg->blocks_per_sm > 0 ? cfg->chunk_events : 0,
-                         cfg->cached_pieces};
+                         cfg->cached_pieces, cfg->tail_eval};
     return RECON_OK;
 }
 
@@ -701,6 +750,7 @@ recon_status recon_get_launch(const recon_ctx* ctx, recon_launch* out)
     out->blocks_per_sm = ctx->last_cfg.blocks_per_sm;
     out->chunk_events = ctx->last_cfg.chunk;
     out->cached_pieces = ctx->last_cfg.cache;
+    out->tail_eval = ctx->last_cfg.tail;
     return RECON_OK;
 }
 

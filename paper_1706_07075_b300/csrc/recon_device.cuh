@@ -63,27 +63,56 @@ __device__ __forceinline__ Event load_event_packed(const int4* __restrict__ ev, 
     return e;
 }
 
-// Signed tail of the Gaussian at tau: sign(tau) * erfc(|tau| / (sigma sqrt 2)).
+// Signed tail of the Gaussian at tau: g = sign(tau) * erfc(|tau| / (sigma sqrt 2)).
 struct Tail {
     float g, s;
 };
 
-__device__ __forceinline__ Tail tail_at(float tau, float inv_sigma_sqrt2)
-{
-    Tail t;
-    t.s = tau >= 0.f ? 1.f : -1.f;
-    t.g = t.s * erfcf(fabsf(tau) * inv_sigma_sqrt2);
-    return t;
-}
+// Tail from CUDA's erfcf.
+struct TailErfc {
+    float inv_sigma_sqrt2;
+    __device__ __forceinline__ Tail operator()(float tau) const
+    {
+        Tail t;
+        t.s = copysignf(1.f, tau);
+        t.g = copysignf(erfcf(fabsf(tau) * inv_sigma_sqrt2), tau);
+        return t;
+    }
+};
+
+// Tail from a piecewise cubic Hermite interpolant of erfc on a uniform grid
+// of step h over [0, K/sqrt 2]: on interval k, erfc(x) ~ c0 + t (c1 + t (c2 +
+// t c3)) with t = x/h - k.  The coefficients come from erfc and its
+// derivative -2/sqrt(pi) exp(-x^2) at the interval ends (host, FP64), so the
+// interpolation error is below h^4 max|erfc''''| / 384 (~1e-9 for h = 1/64).
+// The table sits in shared memory: one 16-byte load per evaluation.
+struct TailTable {
+    const float4* tab;  // shared memory, n entries
+    float inv_h_scale;  // 1 / (h sigma sqrt 2): tau -> table coordinate
+    int last;           // n - 1
+    __device__ __forceinline__ Tail operator()(float tau) const
+    {
+        const float u = fabsf(tau) * inv_h_scale;
+        const int k = min((int)u, last);
+        const float t = u - (float)k;
+        const float4 c = tab[k];
+        const float f = fmaf(fmaf(fmaf(c.w, t, c.z), t, c.y), t, c.x);
+        Tail r;
+        r.s = copysignf(1.f, tau);
+        r.g = copysignf(f, tau);
+        return r;
+    }
+};
 
 // Per-event walk state after clipping the line to the grid box and the TOF
-// window.  Everything the two walks (forward, back) need is here.
+// window.  Everything the two sweeps (forward, back) need is here.
 struct Walk {
     float tau_in, tau_out;    // clipped parameter range (relative to c)
-    int ix, iy, iz;           // voxel containing the start
-    int sx, sy, sz;           // +1 / -1 / 0 per axis
-    float t0x, t0y, t0z;      // tau of the first plane crossing per axis (inf if parallel)
+    int j0;                   // linear index of the start voxel
+    int sxl, syl, szl;        // linear-index step per axis (+-1, +-nx, +-nx*ny, or 0)
+    float t0x, t0y, t0z;      // tau of the first plane crossing per axis (inf if none inside the grid)
     float dtx, dty, dtz;      // tau between successive crossings per axis
+    float rx, ry, rz;         // crossings per axis that stay inside the grid
     bool valid;
 };
 
@@ -91,7 +120,9 @@ struct Walk {
 // unit direction `u` (tau measured from c).  Slab method for the box, then the
 // start voxel and the first crossing on each axis.  The first crossing is
 // expressed relative to c once, and later crossings as first + m * step, so
-// plane positions carry no accumulated rounding.
+// plane positions carry no accumulated rounding.  Each axis may be crossed
+// only as often as the grid has voxels left in that direction, so every index
+// the walk produces lies inside the grid whatever the rounding.
 __device__ __forceinline__ Walk make_walk(const GridDev& g, float3 c, float3 u, float tau_lo, float tau_hi)
 {
     Walk w;
@@ -101,15 +132,17 @@ __device__ __forceinline__ Walk make_walk(const GridDev& g, float3 c, float3 u, 
     const int n[3] = {g.nx, g.ny, g.nz};
     const float cc[3] = {c.x, c.y, c.z};
     const float uu[3] = {u.x, u.y, u.z};
+    float inv_u[3];
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+        inv_u[k] = 1.f / uu[k];
         float hi = lo[k] + (float)n[k] * v[k];
         if (uu[k] == 0.f) {
             ok = ok && (cc[k] >= lo[k]) && (cc[k] < hi);
         } else {
-            float t0 = (lo[k] - cc[k]) / uu[k];
-            float t1 = (hi - cc[k]) / uu[k];
+            float t0 = (lo[k] - cc[k]) * inv_u[k];
+            float t1 = (hi - cc[k]) * inv_u[k];
             a = fmaxf(a, fminf(t0, t1));
             b = fminf(b, fmaxf(t0, t1));
         }
@@ -117,35 +150,41 @@ __device__ __forceinline__ Walk make_walk(const GridDev& g, float3 c, float3 u, 
     w.valid = ok && (a < b);
     w.tau_in = a;
     w.tau_out = b;
-    int idx[3], st[3];
-    float t0[3], dt[3];
+    int idx[3], step[3];
+    float t0[3], dt[3], rem[3];
+    const float inf = __int_as_float(0x7f800000);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float x = fmaf(a, uu[k], cc[k]);
+        const float x = fmaf(a, uu[k], cc[k]);
         float fi = floorf((x - lo[k]) / v[k]);
         fi = fminf(fmaxf(fi, 0.f), (float)(n[k] - 1));   // also maps NaN of an invalid walk to 0
-        int i = (int)fi;
+        const int i = (int)fi;
         idx[k] = i;
         if (uu[k] > 0.f) {
-            st[k] = 1;
-            float plane = lo[k] + (float)(i + 1) * v[k];
-            t0[k] = (plane - cc[k]) / uu[k];
-            dt[k] = v[k] / uu[k];
+            step[k] = 1;
+            t0[k] = (lo[k] + (float)(i + 1) * v[k] - cc[k]) * inv_u[k];
+            dt[k] = v[k] * inv_u[k];
+            rem[k] = (float)(n[k] - 1 - i);
         } else if (uu[k] < 0.f) {
-            st[k] = -1;
-            float plane = lo[k] + (float)i * v[k];
-            t0[k] = (plane - cc[k]) / uu[k];
-            dt[k] = -v[k] / uu[k];
+            step[k] = -1;
+            t0[k] = (lo[k] + (float)i * v[k] - cc[k]) * inv_u[k];
+            dt[k] = -v[k] * inv_u[k];
+            rem[k] = (float)i;
         } else {
-            st[k] = 0;
-            t0[k] = __int_as_float(0x7f800000);  // +inf: never crossed
+            step[k] = 0;
+            t0[k] = inf;
             dt[k] = 0.f;
+            rem[k] = 0.f;
         }
+        if (rem[k] <= 0.f) t0[k] = inf;
     }
-    w.ix = idx[0]; w.iy = idx[1]; w.iz = idx[2];
-    w.sx = st[0]; w.sy = st[1]; w.sz = st[2];
+    w.j0 = idx[0] + g.nx * (idx[1] + g.ny * idx[2]);
+    w.sxl = step[0];
+    w.syl = step[1] * g.nx;
+    w.szl = step[2] * g.nx * g.ny;
     w.t0x = t0[0]; w.t0y = t0[1]; w.t0z = t0[2];
     w.dtx = dt[0]; w.dty = dt[1]; w.dtz = dt[2];
+    w.rx = rem[0]; w.ry = rem[1]; w.rz = rem[2];
     return w;
 }
 
@@ -163,32 +202,33 @@ __device__ __forceinline__ bool event_line(const Event& e, float3& c, float3& u)
 }
 
 // Siddon walk over the voxel pieces of a prepared Walk.  `visit(j, a)` gets
-// the linear voxel index (relative to the grid) and the TOF mass of the piece.
-// With Weighted = false the mass is the piece length in mm (sensitivity).
-// The loop ends at tau_out, after nx+ny+nz+2 pieces at most, or when rounding
-// would step outside the grid (the remaining sliver is dropped), so every
-// index handed to `visit` lies inside the grid.
-template <bool Weighted, class Visit>
-__device__ __forceinline__ void walk(const GridDev& g, const TofDev& tof, const Walk& w, Visit&& visit)
+// the linear voxel index (relative to the grid) and the TOF mass of the piece
+// (tails from `tail`); with Weighted = false the mass is the piece length in
+// mm (sensitivity).  Each step crosses the nearest plane; the axis update is
+// written without branches so that the lanes of a warp, which cross different
+// axes, stay converged.  The walk ends at tau_out (an axis with no crossing
+// left inside the grid has its next crossing at +inf), after at most
+// nx + ny + nz + 2 pieces.
+template <bool Weighted, class TailF, class Visit>
+__device__ __forceinline__ void walk(const GridDev& g, const TofDev& tof, const TailF& tail, const Walk& w,
+                                     Visit&& visit)
 {
     if (!w.valid) return;
-    int ix = w.ix, iy = w.iy, iz = w.iz;
-    const int sy_lin = w.sy * g.nx;
-    const int sz_lin = w.sz * g.nx * g.ny;
-    int j = ix + g.nx * (iy + g.ny * iz);
+    const float inf = __int_as_float(0x7f800000);
+    int j = w.j0;
     float mx = 0.f, my = 0.f, mz = 0.f;
     float tx = w.t0x, ty = w.t0y, tz = w.t0z;
     float tau = w.tau_in;
     Tail cur;
-    if (Weighted) cur = tail_at(tau, tof.inv_sigma_sqrt2);
+    if (Weighted) cur = tail(tau);
     const int max_steps = g.nx + g.ny + g.nz + 2;
     for (int step = 0; step < max_steps; ++step) {
-        float tn = fminf(fminf(tx, ty), tz);
-        bool last = tn >= w.tau_out;
-        tn = fmaxf(fminf(tn, w.tau_out), tau);
+        const float tmin = fminf(tx, fminf(ty, tz));
+        const bool last = tmin >= w.tau_out;
+        const float tn = fmaxf(fminf(tmin, w.tau_out), tau);
         float a;
         if (Weighted) {
-            Tail nxt = tail_at(tn, tof.inv_sigma_sqrt2);
+            const Tail nxt = tail(tn);
             a = tof.half_inv_norm * ((nxt.s - cur.s) + (cur.g - nxt.g));
             cur = nxt;
         } else {
@@ -197,16 +237,19 @@ __device__ __forceinline__ void walk(const GridDev& g, const TofDev& tof, const 
         visit(j, a);
         if (last) break;
         tau = tn;
-        if (tx <= ty && tx <= tz) {
-            ix += w.sx; j += w.sx; mx += 1.f; tx = fmaf(mx, w.dtx, w.t0x);
-            if ((unsigned)ix >= (unsigned)g.nx) break;
-        } else if (ty <= tz) {
-            iy += w.sy; j += sy_lin; my += 1.f; ty = fmaf(my, w.dty, w.t0y);
-            if ((unsigned)iy >= (unsigned)g.ny) break;
-        } else {
-            iz += w.sz; j += sz_lin; mz += 1.f; tz = fmaf(mz, w.dtz, w.t0z);
-            if ((unsigned)iz >= (unsigned)g.nz) break;
-        }
+        const bool bx = tx == tmin;
+        const bool by = !bx && ty == tmin;
+        const bool bz = !bx && !by;
+        j += bx ? w.sxl : (by ? w.syl : w.szl);
+        mx += bx ? 1.f : 0.f;
+        my += by ? 1.f : 0.f;
+        mz += bz ? 1.f : 0.f;
+        const float nx_ = mx < w.rx ? fmaf(mx, w.dtx, w.t0x) : inf;
+        const float ny_ = my < w.ry ? fmaf(my, w.dty, w.t0y) : inf;
+        const float nz_ = mz < w.rz ? fmaf(mz, w.dtz, w.t0z) : inf;
+        tx = bx ? nx_ : tx;
+        ty = by ? ny_ : ty;
+        tz = bz ? nz_ : tz;
     }
 }
 

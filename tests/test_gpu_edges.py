@@ -103,23 +103,24 @@ def test_one_voxel_grid_closed_form():
         assert img[0] == pytest.approx(n / 12.5, rel=1e-6)
 
 
-@pytest.mark.parametrize("cfg", [(64, 0, 0, 0), (128, 0, 0, 0), (256, 4, 32, 0), (128, 16, 256, 0),
-                                 (256, 1, 1024, 0), (128, 0, 0, 64), (64, 6, 64, 64), (128, 0, 0, 8),
-                                 (256, 2, 64, 96)])
+@pytest.mark.parametrize("cfg", [(64, 0, 0, 0, 0), (128, 0, 0, 0, 0), (256, 4, 32, 0, 0), (128, 16, 256, 0, 0),
+                                 (256, 1, 1024, 0, 0), (128, 0, 0, 64, 0), (64, 6, 64, 64, 0), (128, 0, 0, 8, 0),
+                                 (256, 2, 64, 96, 0), (128, 0, 0, 0, 1), (64, 4, 64, 32, 1)])
 def test_launch_configurations_agree(ctx_tiny, cfg):
-    # (128, 0, 0, 8) caches fewer pieces than most walks have: those events walk twice
+    # (128, 0, 0, 8) caches fewer pieces than most walks have: those events walk twice.
+    # The last field switches the Gaussian tails from the erfc table to CUDA's erfcf.
     ctx, g = ctx_tiny
     ev, _ = tiny_inputs()
     ctx.set_launch(None)
     ref = np.zeros(g.n_vox, np.float32)
-    ctx.set_launch(256, 0, 0, 0)
+    ctx.set_launch(256, 0, 0, 0, 0)
     ctx.mlem(B.make_events(ev), 2, None, ref, None)
     ctx.set_launch(*cfg)
     img = np.zeros(g.n_vox, np.float32)
     ctx.mlem(None, 2, None, img, None)
-    assert ctx.get_launch() == (cfg[0], cfg[1], cfg[2] if cfg[1] else 0, cfg[3])
+    assert ctx.get_launch() == (cfg[0], cfg[1], cfg[2] if cfg[1] else 0, cfg[3], cfg[4])
     ctx.set_launch(None)
-    assert rel_l2(img, ref) < 1e-6
+    assert rel_l2(img, ref) < (1e-6 if cfg[4] == 0 else 2e-6)
 
 
 def test_device_buffers_match_host_buffers(ctx_tiny):

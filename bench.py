@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=1708)
-    ap.add_argument("--cpu-sample", type=int, default=60_000, help="events in the oracle's timed sample")
+    ap.add_argument("--cpu-sample", type=int, default=300_000, help="events in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -114,6 +114,32 @@ def measured_peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def measure_probes(n_vox, stream, dev):
+    """Roofline denominators measured on this GPU (librecon_probe.so)."""
+    import ctypes as C
+    import torch
+    from paper_1706_07075_b300 import build as lib_build
+    lib = C.CDLL(lib_build.build_probe())
+    for name in ("recon_probe_l2_red", "recon_probe_gather", "recon_probe_erfc"):
+        getattr(lib, name).restype = C.c_int
+    img = torch.zeros(n_vox, dtype=torch.float32, device=dev)
+    sink = torch.zeros(148 * 64 * 256, dtype=torch.float32, device=dev)
+    out = {}
+    v = C.c_double()
+    h = C.c_void_p(stream.cuda_stream)
+    if lib.recon_probe_l2_red(C.c_void_p(img.data_ptr()), C.c_int64(n_vox), 1, h, C.byref(v)) == 0:
+        out["l2_red_gops"] = v.value / 1e9
+    if lib.recon_probe_l2_red(C.c_void_p(img.data_ptr()), C.c_int64(n_vox), 4, h, C.byref(v)) == 0:
+        out["l2_red_runs4_gops"] = v.value / 1e9
+    if lib.recon_probe_gather(C.c_void_p(img.data_ptr()), C.c_int64(n_vox), C.c_void_p(sink.data_ptr()), h,
+                              C.byref(v)) == 0:
+        out["gather_gops"] = v.value / 1e9
+    if lib.recon_probe_erfc(C.c_void_p(sink.data_ptr()), h, C.byref(v)) == 0:
+        out["erfc_gops"] = v.value / 1e9
+    torch.cuda.synchronize(dev)
+    return out
 
 
 def mean_visits(ev, n_sample=200_000):
@@ -281,13 +307,22 @@ def run_ours(args):
         vbar = mean_visits(ev)
         visits = vbar * n
         out["extra"]["mean_visits_per_event"] = vbar
-        # HBM term: resident event records (32 B) read once per pass
+        probes = measure_probes(ctx.n_vox, stream, dev)
+        out["extra"]["probes"] = probes
+        # The event pass issues one FP32 reduction into the L2-resident image per
+        # Siddon piece (visits per launch = mean pieces per event x events) and
+        # reads each 32-byte event record once from HBM.
+        red_rate = visits / (pass_ms / 1e3)
         hbm_gbs = 32.0 * n / (pass_ms / 1e3) / 1e9
-        # ALU term: see the design doc for the per-visit operation count
-        out["roofline"] = {"bound": "alu", "achieved": None, "peak": None, "unit": "Gvisit/s", "frac": None,
-                           "traffic": None, "visits_per_launch": visits,
-                           "visit_rate_g_per_s": visits / (pass_ms / 1e3) / 1e9,
-                           "hbm_gbs_achieved": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": src}
+        out["roofline"] = {
+            "bound": "l2_red", "achieved": red_rate / 1e9, "peak": probes["l2_red_gops"], "unit": "Gop/s",
+            "frac": red_rate / 1e9 / probes["l2_red_gops"], "traffic": None,
+            "per_launch": {"events": n, "reductions": visits, "gathers": visits, "hbm_bytes": 32.0 * n,
+                           "pass_ms": pass_ms},
+            "peak_source": "live probe: scattered red.global.add.f32 into an L2-resident image of the grid's size",
+            "secondary": {"hbm_gbs": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
+                          "hbm_peak_source": src,
+                          "gather_frac": red_rate / 1e9 / probes["gather_gops"]}}
         if not args.no_cpu_baseline:
             lsub = lors[:, :200_000]
             out["cpu_baseline"] = cpu_baseline(ev, lsub, args.iters, args.cpu_sample)

@@ -88,7 +88,7 @@ typedef struct {
 
 /* Launch configuration of the event pass (chosen by the autotuner unless set). */
 typedef struct {
-    int32_t threads_per_block; /* 64, 128 or 256 */
+    int32_t threads_per_block; /* multiple of 32 in [32, 256] */
     int32_t blocks_per_sm;     /* > 0 (<= 32): persistent grid of SMs x this with a per-warp work
                                   queue; 0: flat grid, one event per thread */
     int32_t chunk_events;      /* events a warp takes from the queue at a time (multiple of 32) */

@@ -87,8 +87,8 @@ struct recon_ctx {
     // options
     bool bf16 = false, timing = false, graphs = true, autotune = true;
     bool user_cfg = false;
-    LaunchCfg cfg{128, 0, 0, 0, TAIL_TABLE};
-    LaunchCfg last_cfg{128, 0, 0, 0, TAIL_TABLE};
+    LaunchCfg cfg{128, 0, 0, 0, TAIL_ERFC};
+    LaunchCfg last_cfg{128, 0, 0, 0, TAIL_ERFC};
     std::map<std::tuple<long long, int, long long, int>, LaunchCfg> tuned;
     recon_stats stats{};
 
@@ -283,7 +283,7 @@ recon_status finish_sensitivity(recon_ctx* ctx)
     return RECON_OK;
 }
 
-LaunchCfg default_cfg() { return LaunchCfg{128, 0, 0, 0, TAIL_TABLE}; }
+LaunchCfg default_cfg() { return LaunchCfg{128, 0, 0, 0, TAIL_ERFC}; }
 
 // Piecewise cubic Hermite table of erfc on [0, K/sqrt 2 + h], h = 1/64, from
 // libm's erfc and the derivative -2/sqrt(pi) exp(-x^2) (FP64, host).
@@ -315,7 +315,7 @@ recon_status build_tail_table(recon_ctx* ctx)
 bool valid_cfg(const recon_launch* c)
 {
     if (!c) return false;
-    if (c->threads_per_block != 64 && c->threads_per_block != 128 && c->threads_per_block != 256) return false;
+    if (c->threads_per_block < 32 || c->threads_per_block > 256 || c->threads_per_block % 32) return false;
     if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return false;
     if (c->blocks_per_sm > 0 && (c->chunk_events < 32 || c->chunk_events % 32 || c->chunk_events > (1 << 20)))
         return false;
@@ -356,9 +356,9 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
 {
     // flat and persistent grids, walking twice or replaying a shared-memory piece cache
     const std::vector<LaunchCfg> cands = {
-        {128, 0, 0, 0, TAIL_TABLE}, {256, 0, 0, 0, TAIL_TABLE}, {64, 0, 0, 0, TAIL_TABLE},
-        {128, 8, 64, 0, TAIL_TABLE}, {256, 4, 256, 0, TAIL_TABLE}, {64, 0, 0, 64, TAIL_TABLE},
-        {128, 0, 0, 48, TAIL_TABLE}, {128, 0, 0, 0, TAIL_ERFC},
+        {128, 0, 0, 0, TAIL_ERFC}, {256, 0, 0, 0, TAIL_ERFC}, {96, 0, 0, 0, TAIL_ERFC},
+        {192, 0, 0, 0, TAIL_ERFC}, {128, 8, 64, 0, TAIL_ERFC}, {64, 0, 0, 64, TAIL_ERFC},
+        {128, 0, 0, 0, TAIL_TABLE}, {256, 0, 0, 0, TAIL_TABLE},
     };
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));

@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=1708)
     ap.add_argument("--cpu-sample", type=int, default=300_000, help="events in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch", default=None,
+                    help="fix the event-pass launch: threads,blocks_per_sm,chunk,cached_pieces,tail_eval "
+                         "(default: the library's autotuner)")
+    ap.add_argument("--no-graphs", action="store_true", help="launch iterations directly instead of graph replay")
     return ap.parse_args()
 
 
@@ -239,6 +243,10 @@ def run_ours(args):
     ctx.load_events(B.make_events(pinned))
     t_load = time.perf_counter() - t
 
+    if args.launch:
+        ctx.set_launch(*[int(x) for x in args.launch.split(",")])
+    if args.no_graphs:
+        ctx.set_graphs(0)
     # warm-up (the first call also runs the launch autotuner)
     for _ in range(args.warmup):
         ctx.mlem(None, args.iters)
@@ -280,7 +288,7 @@ def run_ours(args):
         t = time.perf_counter()
         ctx.mlem(B.make_events(pinned), args.iters, None, img, cons)
         e2e_times.append(time.perf_counter() - t)
-    e2e_T = sum(e2e_times[1:]) / max(1, args.e2e_steps)
+    e2e_T = sum(e2e_times[1:]) / args.e2e_steps if args.e2e_steps > 0 else float("nan")
     h2d = ev.nbytes
     d2h = img.numel() * 4 + cons.nbytes
 

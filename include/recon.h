@@ -97,8 +97,8 @@ typedef struct {
                                   memory (8 bytes each, threads_per_block * cached_pieces * 8 <= 200 KB)
                                   and the backprojection replays them */
     int32_t tail_eval;         /* Gaussian tails erfc(|tau|/(sigma sqrt 2)) at the piece boundaries from
-                                  0: a shared-memory cubic Hermite table of erfc (step 1/64, error
-                                  below 1e-8), 1: CUDA's erfcf */
+                                  0: t exp(-x^2 + P(t)), t = 1/(1 + x/2), with a fitted degree-10 P
+                                  (relative error ~6e-7 at K = 3), 1: CUDA's erfcf */
 } recon_launch;
 
 typedef struct {

@@ -115,12 +115,11 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
     return e.w;
 }
 
-template <int Kind, int Fmt, bool Persistent, bool Cached, bool Table>
+template <int Kind, int Fmt, bool Persistent, bool Cached, bool Fit>
 __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl, int chunk, int cap)
 {
     __shared__ SharedTable t;
     __shared__ float neff[kMaxRegions];
-    __shared__ float4 phi[kMaxTailTable];
     extern __shared__ unsigned char dyn_smem[];
     PieceCache pc;
     pc.cap = Cached ? cap : 0;
@@ -133,18 +132,10 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
         t.grid[k] = tbl.grid[k];
         neff[k] = 0.f;
     }
-    if (Table)
-        for (int k = threadIdx.x; k < a.tail_n; k += blockDim.x) phi[k] = a.tail_tab[k];
     __syncthreads();
-    using TailF = typename std::conditional<Table, TailTable, TailErfc>::type;
+    using TailF = typename std::conditional<Fit, TailFit, TailErfc>::type;
     TailF tail;
-    if constexpr (Table) {
-        tail.tab = phi;
-        tail.inv_h_scale = a.tail_inv_h_scale;
-        tail.last = a.tail_n - 1;
-    } else {
-        tail.inv_sigma_sqrt2 = a.tof.inv_sigma_sqrt2;
-    }
+    tail.inv_sigma_sqrt2 = a.tof.inv_sigma_sqrt2;
     const bool bf16 = a.lam_bf16 != nullptr;
     const int lane = threadIdx.x & 31;
     if (Persistent) {
@@ -177,11 +168,11 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
 
 constexpr int kMaxCacheBytes = 200 * 1024;
 
-template <int Kind, int Fmt, bool Persistent, bool Cached, bool Table>
+template <int Kind, int Fmt, bool Persistent, bool Cached, bool Fit>
 cudaError_t launch_variant(int blocks, const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl,
                            cudaStream_t s)
 {
-    auto kern = k_event_pass<Kind, Fmt, Persistent, Cached, Table>;
+    auto kern = k_event_pass<Kind, Fmt, Persistent, Cached, Fit>;
     size_t smem = 0;
     if (Cached) {
         smem = (size_t)cfg.cache * cfg.threads * 8;
@@ -192,18 +183,18 @@ cudaError_t launch_variant(int blocks, const LaunchCfg& cfg, const PassArgs& a, 
     return cudaGetLastError();
 }
 
-template <int Kind, int Fmt, bool Table>
+template <int Kind, int Fmt, bool Fit>
 cudaError_t launch_tail(int blocks, const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl, cudaStream_t s)
 {
     const bool persistent = cfg.blocks_per_sm > 0;
     if constexpr (Kind == PASS_FUSED) {
         if (cfg.cache > 0) {
-            if (persistent) return launch_variant<Kind, Fmt, true, true, Table>(blocks, cfg, a, tbl, s);
-            return launch_variant<Kind, Fmt, false, true, Table>(blocks, cfg, a, tbl, s);
+            if (persistent) return launch_variant<Kind, Fmt, true, true, Fit>(blocks, cfg, a, tbl, s);
+            return launch_variant<Kind, Fmt, false, true, Fit>(blocks, cfg, a, tbl, s);
         }
     }
-    if (persistent) return launch_variant<Kind, Fmt, true, false, Table>(blocks, cfg, a, tbl, s);
-    return launch_variant<Kind, Fmt, false, false, Table>(blocks, cfg, a, tbl, s);
+    if (persistent) return launch_variant<Kind, Fmt, true, false, Fit>(blocks, cfg, a, tbl, s);
+    return launch_variant<Kind, Fmt, false, false, Fit>(blocks, cfg, a, tbl, s);
 }
 
 template <int Kind, int Fmt>
@@ -213,9 +204,7 @@ cudaError_t launch_kind(const LaunchCfg& cfg, const PassArgs& a, const RegionTab
     const int blocks = pass_blocks(cfg, a.n, num_sms);
     if (blocks == 0) return cudaSuccess;
     if ((size_t)cfg.cache * cfg.threads * 8 > (size_t)kMaxCacheBytes) return cudaErrorInvalidValue;
-    const bool table = cfg.tail == TAIL_TABLE;
-    if (table && (!a.tail_tab || a.tail_n < 2 || a.tail_n > kMaxTailTable)) return cudaErrorInvalidValue;
-    if (table) return launch_tail<Kind, Fmt, true>(blocks, cfg, a, tbl, s);
+    if (cfg.tail == TAIL_FIT) return launch_tail<Kind, Fmt, true>(blocks, cfg, a, tbl, s);
     return launch_tail<Kind, Fmt, false>(blocks, cfg, a, tbl, s);
 }
 

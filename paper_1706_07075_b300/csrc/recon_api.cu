@@ -80,15 +80,12 @@ struct recon_ctx {
     DevBuf pass_partial, upd_partial, work, iter, hist, reg_vox, red_partial, vec;
 
     // erfc interpolation table for the TOF kernel (rebuilt when K changes)
-    DevBuf tail_tab;
-    int tail_n = 0;
-    float tail_inv_h_scale = 0.f;
 
     // options
     bool bf16 = false, timing = false, graphs = true, autotune = true;
     bool user_cfg = false;
-    LaunchCfg cfg{128, 0, 0, 0, TAIL_ERFC};
-    LaunchCfg last_cfg{128, 0, 0, 0, TAIL_ERFC};
+    LaunchCfg cfg{128, 0, 0, 0, TAIL_FIT};
+    LaunchCfg last_cfg{128, 0, 0, 0, TAIL_FIT};
     std::map<std::tuple<long long, int, long long, int>, LaunchCfg> tuned;
     recon_stats stats{};
 
@@ -283,34 +280,7 @@ recon_status finish_sensitivity(recon_ctx* ctx)
     return RECON_OK;
 }
 
-LaunchCfg default_cfg() { return LaunchCfg{128, 0, 0, 0, TAIL_ERFC}; }
-
-// Piecewise cubic Hermite table of erfc on [0, K/sqrt 2 + h], h = 1/64, from
-// libm's erfc and the derivative -2/sqrt(pi) exp(-x^2) (FP64, host).
-recon_status build_tail_table(recon_ctx* ctx)
-{
-    const double h = 1.0 / 64.0;
-    const double xmax = ctx->k_sigma / std::sqrt(2.0);
-    const int n = (int)std::ceil(xmax / h) + 1;
-    if (n > kMaxTailTable) return fail(ctx, RECON_EINVAL, "kernel window too wide for the erfc table");
-    std::vector<float> tab(4 * (size_t)n);
-    const double two_over_sqrt_pi = 2.0 / std::sqrt(std::acos(-1.0));
-    for (int k = 0; k < n; ++k) {
-        const double x0 = k * h, x1 = (k + 1) * h;
-        const double f0 = std::erfc(x0), f1 = std::erfc(x1);
-        const double d0 = -h * two_over_sqrt_pi * std::exp(-x0 * x0);
-        const double d1 = -h * two_over_sqrt_pi * std::exp(-x1 * x1);
-        tab[4 * k + 0] = (float)f0;
-        tab[4 * k + 1] = (float)d0;
-        tab[4 * k + 2] = (float)(3.0 * (f1 - f0) - 2.0 * d0 - d1);
-        tab[4 * k + 3] = (float)(2.0 * (f0 - f1) + d0 + d1);
-    }
-    CK(ensure(ctx->tail_tab, sizeof(float) * tab.size()));
-    CK(cudaMemcpy(ctx->tail_tab.p, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice));
-    ctx->tail_n = n;
-    ctx->tail_inv_h_scale = (float)(1.0 / (h * ctx->sigma_mm * std::sqrt(2.0)));
-    return RECON_OK;
-}
+LaunchCfg default_cfg() { return LaunchCfg{128, 0, 0, 0, TAIL_FIT}; }
 
 bool valid_cfg(const recon_launch* c)
 {
@@ -321,7 +291,7 @@ bool valid_cfg(const recon_launch* c)
         return false;
     if (c->cached_pieces != 0 && (c->cached_pieces < 8 || c->cached_pieces > 256)) return false;
     if ((long long)c->cached_pieces * c->threads_per_block * 8 > 200 * 1024) return false;
-    if (c->tail_eval != TAIL_TABLE && c->tail_eval != TAIL_ERFC) return false;
+    if (c->tail_eval != TAIL_FIT && c->tail_eval != TAIL_ERFC) return false;
     return true;
 }
 
@@ -344,9 +314,6 @@ PassArgs base_args(recon_ctx* ctx, const void* events, long long n)
     a.n = n;
     a.lattice = (float)ctx->lattice;
     a.tof = make_tof(ctx);
-    a.tail_tab = ctx->tail_tab.as<float4>();
-    a.tail_n = ctx->tail_n;
-    a.tail_inv_h_scale = ctx->tail_inv_h_scale;
     return a;
 }
 
@@ -356,9 +323,9 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
 {
     // flat and persistent grids, walking twice or replaying a shared-memory piece cache
     const std::vector<LaunchCfg> cands = {
-        {128, 0, 0, 0, TAIL_ERFC}, {256, 0, 0, 0, TAIL_ERFC}, {96, 0, 0, 0, TAIL_ERFC},
-        {192, 0, 0, 0, TAIL_ERFC}, {128, 8, 64, 0, TAIL_ERFC}, {64, 0, 0, 64, TAIL_ERFC},
-        {128, 0, 0, 0, TAIL_TABLE}, {256, 0, 0, 0, TAIL_TABLE},
+        {128, 0, 0, 0, TAIL_FIT}, {256, 0, 0, 0, TAIL_FIT}, {96, 0, 0, 0, TAIL_FIT},
+        {192, 0, 0, 0, TAIL_FIT}, {128, 8, 64, 0, TAIL_FIT}, {64, 0, 0, 64, TAIL_FIT},
+        {128, 0, 0, 0, TAIL_ERFC}, {256, 0, 0, 0, TAIL_ERFC},
     };
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -651,11 +618,6 @@ recon_status recon_create(const recon_geometry* geom, const recon_grid* grid, do
     if ((e = ensure(ctx->C, sizeof(float) * nv)) != cudaSuccess) return bail(e, "allocating C");
     if ((e = ensure(ctx->work, 64)) != cudaSuccess) return bail(e, "allocating work counter");
     if ((e = ensure(ctx->iter, 64)) != cudaSuccess) return bail(e, "allocating iteration counter");
-    if (build_tail_table(ctx) != RECON_OK) {
-        g_create_error = ctx->err;
-        recon_destroy(ctx);
-        return RECON_ECUDA;
-    }
     if ((e = cudaMemsetAsync(ctx->s64.p, 0, sizeof(double) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemsetAsync(ctx->s32.p, 0, sizeof(float) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemsetAsync(ctx->lam.p, 0, sizeof(float) * nv, ctx->stream)) != cudaSuccess) return bail(e, "memset");
@@ -708,14 +670,7 @@ recon_status recon_set_kernel_window(recon_ctx* ctx, double k_sigma)
 {
     CHECK_CTX();
     if (!(k_sigma >= 0.5 && k_sigma <= 8.0)) return fail(ctx, RECON_EINVAL, "k_sigma must be in [0.5, 8]");
-    const double old = ctx->k_sigma;
     ctx->k_sigma = k_sigma;
-    recon_status st = build_tail_table(ctx);
-    if (st != RECON_OK) {
-        ctx->k_sigma = old;
-        build_tail_table(ctx);
-        return st;
-    }
     invalidate_graph(ctx);
     return RECON_OK;
 }

@@ -7,7 +7,6 @@
 namespace recon {
 
 constexpr int kMaxRegions = 64;
-constexpr int kMaxTailTable = 512;  // entries of the erfc interpolation table (h = 1/64 covers K <= 8)
 
 // Grid of one image (or region slab): nx*ny*nz voxels of (vx,vy,vz) mm from
 // the low corner (ox,oy,oz); vox_offset places it in a shared image buffer.
@@ -33,7 +32,7 @@ struct RegionTable {
 
 enum EventFmt { FMT_F32 = 0, FMT_PACKED = 1 };
 enum PassKind { PASS_FUSED = 0, PASS_FORWARD = 1, PASS_BACK = 2 };
-enum TailEval { TAIL_TABLE = 0, TAIL_ERFC = 1 };
+enum TailEval { TAIL_FIT = 0, TAIL_ERFC = 1 };
 
 struct LaunchCfg {
     int threads;       // threads per block (64, 128, 256)
@@ -55,9 +54,6 @@ struct PassArgs {
     double* partial;             // PASS_FUSED: per block and region, sum of w_i over events with p_i > 0
     unsigned long long* work;    // work-queue counter (persistent launches; zero before the launch)
     TofH tof;
-    const float4* tail_tab;      // TAIL_TABLE: per-interval cubic coefficients of erfc (device)
-    int tail_n;                  // entries of tail_tab
-    float tail_inv_h_scale;      // 1 / (h sigma sqrt 2)
 };
 
 // Number of blocks a pass launch uses (its partial array has blocks * regions doubles).

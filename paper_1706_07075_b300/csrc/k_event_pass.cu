@@ -160,9 +160,11 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
         }
     }
     if (Kind == PASS_FUSED) {
+        // fold the block's N_eff into one of kNeffSlots slots per region; the
+        // weights are 1 or 1/2, so the FP64 sums are exact in any order
         __syncthreads();
         for (int k = threadIdx.x; k < t.n; k += blockDim.x)
-            a.partial[(long long)blockIdx.x * t.n + k] = (double)neff[k];
+            if (neff[k] != 0.f) atomicAdd(a.partial + (blockIdx.x % kNeffSlots) * t.n + k, (double)neff[k]);
     }
 }
 

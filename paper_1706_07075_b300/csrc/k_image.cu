@@ -84,14 +84,19 @@ __global__ void __launch_bounds__(kImgThreads) k_update(float* __restrict__ lam,
 
 // hist[(k * R + r) * 2 + {0,1}] = {N_eff, sum_j s_j lambda_j} of region r after
 // iteration k = *iter; then ++*iter.  One block; fixed summation order.
-__global__ void k_finalize(const double* __restrict__ pass_part, int pass_blocks, const double* __restrict__ upd_part,
+// The pass slots (pass_slots x R) are cleared after reading, ready for the
+// next iteration's pass.
+__global__ void k_finalize(double* __restrict__ pass_part, int pass_slots, const double* __restrict__ upd_part,
                            int bpr, int R, double* __restrict__ hist, int* __restrict__ iter, int max_iter)
 {
     __shared__ double sh[32];
     const int k = *iter;
     for (int r = 0; r < R; ++r) {
         double a = 0.0, b = 0.0;
-        for (int i = threadIdx.x; i < pass_blocks; i += blockDim.x) a += pass_part[(long long)i * R + r];
+        for (int i = threadIdx.x; i < pass_slots; i += blockDim.x) {
+            a += pass_part[(long long)i * R + r];
+            pass_part[(long long)i * R + r] = 0.0;
+        }
         for (int i = threadIdx.x; i < bpr; i += blockDim.x) b += upd_part[(long long)r * bpr + i];
         a = block_sum(a, sh);
         b = block_sum(b, sh);
@@ -217,11 +222,11 @@ cudaError_t launch_update(float* lam, float* C, const float* s32, uint16_t* lam_
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double* pass_partial, int pass_blocks, const double* upd_partial,
+cudaError_t launch_finalize(double* pass_partial, int pass_slots, const double* upd_partial,
                             int upd_blocks_per_region, int n_regions, double* hist, int* iter_counter,
                             int max_iter, cudaStream_t st)
 {
-    k_finalize<<<1, 256, 0, st>>>(pass_partial, pass_blocks, upd_partial, upd_blocks_per_region, n_regions, hist,
+    k_finalize<<<1, 256, 0, st>>>(pass_partial, pass_slots, upd_partial, upd_blocks_per_region, n_regions, hist,
                                   iter_counter, max_iter);
     return cudaGetLastError();
 }

@@ -79,8 +79,6 @@ struct recon_ctx {
     // per-call scratch
     DevBuf pass_partial, upd_partial, work, iter, hist, reg_vox, red_partial, vec;
 
-    // erfc interpolation table for the TOF kernel (rebuilt when K changes)
-
     // options
     bool bf16 = false, timing = false, graphs = true, autotune = true;
     bool user_cfg = false;
@@ -332,10 +330,9 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
     *best = default_cfg();
+    CK(ensure(ctx->pass_partial, sizeof(double) * kNeffSlots * tbl.n));
+    a.partial = ctx->pass_partial.as<double>();
     for (const LaunchCfg& c : cands) {
-        const int blocks = pass_blocks(c, a.n, ctx->num_sms);
-        CK(ensure(ctx->pass_partial, sizeof(double) * (size_t)std::max(1, blocks) * tbl.n));
-        a.partial = ctx->pass_partial.as<double>();
         float ms_min = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
@@ -382,7 +379,7 @@ recon_status enqueue_iteration(recon_ctx* ctx, const IterPlan& p)
     CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, p.a, p.tbl, ctx->num_sms, ctx->stream));
     CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(), p.upd_bpr,
                      ctx->stream));
-    CK(launch_finalize(p.a.partial, p.pass_blocks, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions, p.hist,
+    CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions, p.hist,
                        p.iter, p.hist_cap, ctx->stream));
     return RECON_OK;
 }
@@ -424,7 +421,7 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter)
             CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(),
                              p.upd_bpr, ctx->stream));
             if (ctx->timing) CK(cudaEventRecord(evs[3 * k + 2], ctx->stream));
-            CK(launch_finalize(p.a.partial, p.pass_blocks, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions,
+            CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions,
                                p.hist, p.iter, p.hist_cap, ctx->stream));
             ctx->stats.kernel_launches += p.pass_blocks > 0 ? 3 : 2;
         }
@@ -904,14 +901,13 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     p.a.work = ctx->work.as<unsigned long long>();
     p.tbl = single_table(ctx);
     recon_status st;
-    CK(ensure(ctx->pass_partial, sizeof(double) * 16));
+    CK(ensure(ctx->pass_partial, sizeof(double) * kNeffSlots));
     p.a.partial = ctx->pass_partial.as<double>();
     p.cfg = choose_cfg(ctx, p.a, p.tbl, &st);
     if (st != RECON_OK) return st;
     CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
+    CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots, ctx->stream));
     p.pass_blocks = pass_blocks(p.cfg, ctx->n_ev, ctx->num_sms);
-    CK(ensure(ctx->pass_partial, sizeof(double) * (size_t)std::max(1, p.pass_blocks)));
-    p.a.partial = ctx->pass_partial.as<double>();
     p.upd_bpr = update_blocks(nv);
     CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)p.upd_bpr));
     CK(ensure(ctx->reg_vox, sizeof(long long) * 2));
@@ -927,11 +923,6 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     p.bf16 = ctx->bf16 ? ctx->lam_bf16.as<uint16_t>() : nullptr;
     p.reg_vox_dev = ctx->reg_vox.as<long long>();
     p.n_regions = 1;
-    if (p.pass_blocks == 0) {
-        // no events: the pass is empty, its partial sum is zero
-        CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double), ctx->stream));
-        p.pass_blocks = 1;
-    }
     ctx->last_cfg = p.cfg;
     recon_status s = run_iterations(ctx, p, n_iter);
     if (s != RECON_OK) return s;
@@ -1065,18 +1056,13 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
     p.tbl.n = R;
     for (int r = 0; r <= R; ++r) p.tbl.ev_begin[r] = off[r];
     for (int r = 0; r < R; ++r) p.tbl.grid[r] = grid_h(ctx->grid, lo[r], hi[r], rv[r]);
-    CK(ensure(ctx->pass_partial, sizeof(double) * 16 * R));
+    CK(ensure(ctx->pass_partial, sizeof(double) * kNeffSlots * R));
     p.a.partial = ctx->pass_partial.as<double>();
     p.cfg = choose_cfg(ctx, p.a, p.tbl, &s);
     if (s != RECON_OK) return s;
     CK(cudaMemsetAsync(ctx->C_reg.p, 0, sizeof(float) * nvt, ctx->stream));
+    CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots * R, ctx->stream));
     p.pass_blocks = pass_blocks(p.cfg, total, ctx->num_sms);
-    CK(ensure(ctx->pass_partial, sizeof(double) * (size_t)std::max(1, p.pass_blocks) * R));
-    p.a.partial = ctx->pass_partial.as<double>();
-    if (p.pass_blocks == 0) {
-        CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * R, ctx->stream));
-        p.pass_blocks = 1;
-    }
     p.upd_bpr = std::max(1, update_blocks(nvt) / R);
     CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)p.upd_bpr * R));
     p.hist_cap = std::max(n_iter, 64);

@@ -7,6 +7,7 @@
 namespace recon {
 
 constexpr int kMaxRegions = 64;
+constexpr int kNeffSlots = 32;  // FP64 slots per region that event-pass blocks fold N_eff into
 
 // Grid of one image (or region slab): nx*ny*nz voxels of (vx,vy,vz) mm from
 // the low corner (ox,oy,oz); vox_offset places it in a shared image buffer.
@@ -51,12 +52,13 @@ struct PassArgs {
     float* C;                    // backprojection accumulator
     float* p_out;                // PASS_FORWARD: p_i
     const float* r_in;           // PASS_BACK: r_i
-    double* partial;             // PASS_FUSED: per block and region, sum of w_i over events with p_i > 0
+    double* partial;             // PASS_FUSED: kNeffSlots x regions accumulators of sum w_i over events with
+                                 // p_i > 0 (zero before the pass; the finalize reads and clears them)
     unsigned long long* work;    // work-queue counter (persistent launches; zero before the launch)
     TofH tof;
 };
 
-// Number of blocks a pass launch uses (its partial array has blocks * regions doubles).
+// Number of blocks a pass launch uses.
 int pass_blocks(const LaunchCfg& cfg, long long n, int num_sms);
 cudaError_t launch_pass(PassKind kind, EventFmt fmt, const LaunchCfg& cfg, const PassArgs& a,
                         const RegionTable& tbl, int num_sms, cudaStream_t s);
@@ -76,7 +78,7 @@ int update_blocks(long long n_vox);
 cudaError_t launch_update(float* lam, float* C, const float* s32, uint16_t* lam_bf16, const long long* reg_vox,
                           int n_regions, double* partial, int blocks_per_region, cudaStream_t st);
 // hist[(k * R + r) * 2 + {0,1}] = {N_eff, sum s lambda} of region r after iteration k = *iter; ++*iter.
-cudaError_t launch_finalize(const double* pass_partial, int pass_blocks, const double* upd_partial,
+cudaError_t launch_finalize(double* pass_partial, int pass_slots, const double* upd_partial,
                             int upd_blocks_per_region, int n_regions, double* hist, int* iter_counter,
                             int max_iter, cudaStream_t st);
 cudaError_t launch_to_bf16(const float* src, uint16_t* dst, long long n, cudaStream_t st);

@@ -44,15 +44,6 @@ __device__ __forceinline__ Event load_event(const PassArgs& a, long long i)
     return load_event_packed(static_cast<const int4*>(a.events), i, a.lattice);
 }
 
-__device__ __forceinline__ float gather(const PassArgs& a, bool bf16, long long j)
-{
-    if (bf16) {
-        unsigned short h = __ldg(reinterpret_cast<const unsigned short*>(a.lam_bf16) + j);
-        return __uint_as_float(((unsigned)h) << 16);
-    }
-    return __ldg(a.lam + j);
-}
-
 // Per-thread cache of one walk's pieces in shared memory, laid out
 // [piece][thread] so that a warp's accesses fall in distinct banks.
 struct PieceCache {
@@ -74,20 +65,23 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
     Walk w;
     w.valid = false;
     if (event_line(e, c, u)) w = make_walk(g, c, u, -a.tof.half_window, a.tof.half_window);
-    const long long base = g.vox_offset;
+    // the walk hands over 2 [Phi(b) - Phi(a)] per piece; half_inv_norm turns it
+    // into the TOF mass, applied once to p_i and once to r_i
+    const float hin = a.tof.half_inv_norm;
+    float* const Cb = a.C + g.vox_offset;
     if (Kind == PASS_BACK) {
-        const float r = a.r_in[i];
-        if (r != 0.f)
-            walk<true>(g, a.tof, tail, w, [&](int j, float m) {
-                if (m != 0.f) atomicAdd(a.C + base + j, m * r);
-            });
+        const float r = a.r_in[i] * hin;
+        if (r != 0.f) walk<true>(g, a.tof, tail, w, [&](int j, float m) { atomicAdd(Cb + j, m * r); });
         return 0.f;
     }
     float p = 0.f;
     int cnt = 0;
     const int tid = threadIdx.x;
+    const float* const lb = a.lam + g.vox_offset;
+    const unsigned short* const hb = reinterpret_cast<const unsigned short*>(a.lam_bf16) + g.vox_offset;
     walk<true>(g, a.tof, tail, w, [&](int j, float m) {
-        p = fmaf(m, gather(a, bf16, base + j), p);
+        const float lam_j = bf16 ? __uint_as_float(((unsigned)__ldg(hb + j)) << 16) : __ldg(lb + j);
+        p = fmaf(m, lam_j, p);
         if (Cached && Kind == PASS_FUSED) {
             if (cnt < pc.cap) {
                 pc.j[cnt * pc.stride + tid] = j;
@@ -96,21 +90,17 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
             ++cnt;
         }
     });
+    p *= hin;
     if (Kind == PASS_FORWARD) {
         a.p_out[i] = p;
         return 0.f;
     }
     if (!(p > 0.f)) return 0.f;
-    const float r = e.w / p;
+    const float r = e.w / p * hin;
     if (Cached && cnt <= pc.cap) {
-        for (int k = 0; k < cnt; ++k) {
-            const float m = pc.a[k * pc.stride + tid];
-            if (m != 0.f) atomicAdd(a.C + base + pc.j[k * pc.stride + tid], m * r);
-        }
+        for (int k = 0; k < cnt; ++k) atomicAdd(Cb + pc.j[k * pc.stride + tid], pc.a[k * pc.stride + tid] * r);
     } else {
-        walk<true>(g, a.tof, tail, w, [&](int j, float m) {
-            if (m != 0.f) atomicAdd(a.C + base + j, m * r);
-        });
+        walk<true>(g, a.tof, tail, w, [&](int j, float m) { atomicAdd(Cb + j, m * r); });
     }
     return e.w;
 }

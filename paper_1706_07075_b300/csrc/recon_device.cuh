@@ -203,9 +203,12 @@ __device__ __forceinline__ bool event_line(const Event& e, float3& c, float3& u)
 }
 
 // Siddon walk over the voxel pieces of a prepared Walk.  `visit(j, a)` gets
-// the linear voxel index (relative to the grid) and the TOF mass of the piece
-// (tails from `tail`); with Weighted = false the mass is the piece length in
-// mm (sensitivity).  Each step crosses the nearest plane; the axis update is
+// the linear voxel index (relative to the grid) and, with Weighted = true, the
+// piece's tail difference a = (s_b - s_a) + (g_a - g_b) = 2 [Phi(b) - Phi(a)]
+// (tails from `tail`): the TOF mass is tof.half_inv_norm * a, a factor the
+// callers apply once per event instead of once per piece.  With Weighted =
+// false, a is the piece length in mm (sensitivity).  Each step crosses the
+// nearest plane; the axis update is
 // written without branches so that the lanes of a warp, which cross different
 // axes, stay converged.  The walk ends at tau_out (an axis with no crossing
 // left inside the grid has its next crossing at +inf), after at most
@@ -230,7 +233,7 @@ __device__ __forceinline__ void walk(const GridDev& g, const TofDev& tof, const 
         float a;
         if (Weighted) {
             const Tail nxt = tail(tn);
-            a = tof.half_inv_norm * ((nxt.s - cur.s) + (cur.g - nxt.g));
+            a = (nxt.s - cur.s) + (cur.g - nxt.g);
             cur = nxt;
         } else {
             a = tn - tau;

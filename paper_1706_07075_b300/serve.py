@@ -1,0 +1,235 @@
+"""Continuous-batching reconstruction server over the librecon C-ABI.
+
+Jobs (list-mode events + scanner + grid + iteration count) arrive at any
+time.  The scheduler admits queued jobs, oldest first, whenever a slot is
+free and the job's device-memory footprint fits the remaining HBM budget; a
+later, smaller job may pass an older one that does not fit yet (first fit in
+arrival order).  Each slot owns a CUDA stream and a reconstruction context
+per image grid, so the upload, the MLEM iterations and the read-back of
+concurrent jobs overlap on the GPU.  Sensitivity images are computed once
+per (scanner, grid) and stay resident on the device; contexts are kept and
+reused by later jobs on the same grid.
+
+Timing per job: queue wait, service time and latency (completion - arrival).
+The scheduling logic is independent of the GPU: `Server` takes an executor
+object, and `LibreconExecutor` is the one that runs jobs through librecon.
+"""
+import heapq
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+EVENT_BYTES = 32          # resident F32 event record
+IMAGE_BYTES_PER_VOXEL = 20  # lambda, C, s32 (4 B each) + s64 (8 B)
+STAGING_BYTES = (1 << 23) * 32
+
+
+@dataclass
+class Job:
+    job_id: int
+    arrival: float                # seconds on the server clock
+    events: object                # (7, n) float32 array/tensor (pinned host memory for full overlap)
+    geometry: tuple               # (radius, axial length, max axial angle)
+    grid: tuple                   # (nx, ny, nz, vx, vy, vz, ox, oy, oz)
+    n_iter: int
+    sens_key: object = None       # key of the resident sensitivity image
+    kind: str = ""
+    result: object = None         # host float32 image after completion
+    conservation: object = None
+    admitted: float = None
+    finished: float = None
+    slot: int = None
+
+    @property
+    def n_events(self):
+        return int(self.events.shape[1])
+
+    def footprint(self):
+        nx, ny, nz = self.grid[:3]
+        return self.n_events * EVENT_BYTES + nx * ny * nz * IMAGE_BYTES_PER_VOXEL + STAGING_BYTES
+
+    @property
+    def latency(self):
+        return None if self.finished is None else self.finished - self.arrival
+
+
+@dataclass(order=True)
+class _Queued:
+    arrival: float
+    seq: int
+    job: Job = field(compare=False)
+
+
+class Server:
+    """Admission, slots and the HBM budget; `executor.run(job, slot)` does the work."""
+
+    def __init__(self, executor, slots=3, hbm_budget_bytes=200 << 30, clock=time.perf_counter):
+        if slots < 1:
+            raise ValueError("slots must be >= 1")
+        self.executor = executor
+        self.slots = slots
+        self.budget = int(hbm_budget_bytes)
+        self.clock = clock
+        self._queue = []
+        self._seq = 0
+        self._free_slots = list(range(slots))
+        self._in_use = 0
+        self._lock = threading.Condition()
+        self._threads = []
+        self._errors = []
+        self.done = []
+        self.t0 = None
+        self.max_concurrent = 0
+        self._running = 0
+
+    def now(self):
+        return self.clock() - self.t0
+
+    def start(self):
+        self.t0 = self.clock()
+
+    def submit(self, job):
+        if job.footprint() > self.budget:
+            raise ValueError(f"job {job.job_id} needs {job.footprint()} bytes, more than the whole budget")
+        with self._lock:
+            heapq.heappush(self._queue, _Queued(job.arrival, self._seq, job))
+            self._seq += 1
+            self._admit_locked()
+
+    def _admit_locked(self):
+        """First fit in arrival order while slots and budget allow."""
+        kept = []
+        while self._queue and self._free_slots:
+            q = heapq.heappop(self._queue)
+            fp = q.job.footprint()
+            if self._in_use + fp <= self.budget:
+                slot = self._free_slots.pop(0)
+                self._in_use += fp
+                q.job.admitted = self.now()
+                q.job.slot = slot
+                self._running += 1
+                self.max_concurrent = max(self.max_concurrent, self._running)
+                t = threading.Thread(target=self._work, args=(q.job, slot, fp), daemon=True)
+                self._threads.append(t)
+                t.start()
+            else:
+                kept.append(q)
+        for q in kept:
+            heapq.heappush(self._queue, q)
+
+    def _work(self, job, slot, fp):
+        try:
+            self.executor.run(job, slot)
+        except Exception as e:  # reported by drain(); the slot and memory are released
+            self._errors.append((job.job_id, repr(e)))
+        finally:
+            with self._lock:
+                job.finished = self.now()
+                self.done.append(job)
+                self._in_use -= fp
+                self._free_slots.append(slot)
+                self._free_slots.sort()
+                self._running -= 1
+                self._admit_locked()
+                self._lock.notify_all()
+
+    def drain(self, timeout=None):
+        """Wait until every submitted job has finished."""
+        deadline = None if timeout is None else time.monotonic() + timeout
+        with self._lock:
+            while self._queue or self._running:
+                left = None if deadline is None else deadline - time.monotonic()
+                if left is not None and left <= 0:
+                    raise TimeoutError("jobs still running")
+                self._lock.wait(left)
+        for t in self._threads:
+            t.join()
+        if self._errors:
+            raise RuntimeError(f"jobs failed: {self._errors}")
+
+    def replay(self, jobs):
+        """Submit jobs at their arrival times (seconds after start) and drain."""
+        self.start()
+        for job in sorted(jobs, key=lambda j: j.arrival):
+            delay = job.arrival - self.now()
+            if delay > 0:
+                time.sleep(delay)
+            self.submit(job)
+        self.drain()
+        return self.stats()
+
+    def stats(self):
+        lat = np.array([j.latency for j in self.done])
+        ev_it = sum(j.n_events * j.n_iter for j in self.done)
+        span = max(j.finished for j in self.done) - min(j.arrival for j in self.done) if self.done else 0.0
+        return {"jobs": len(self.done), "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+                "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+                "events_iters_per_s": ev_it / span if span > 0 else None, "span_s": span,
+                "max_concurrent": self.max_concurrent}
+
+
+class LibreconExecutor:
+    """Runs jobs through librecon: one CUDA stream per slot, contexts reused per
+    grid, sensitivity images resident per key."""
+
+    def __init__(self, slots, device=0, sensitivities=None, keep_results=True):
+        import torch
+        from . import binding as B
+        self.B = B
+        self.torch = torch
+        self.device = device
+        torch.cuda.set_device(device)
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        self.contexts = [dict() for _ in range(slots)]   # per slot: grid -> Context
+        self.sens = dict(sensitivities or {})            # key -> device float64 tensor
+        self.keep_results = keep_results
+        self._sens_lock = threading.Lock()
+
+    def register_sensitivity(self, key, geometry, grid, lors):
+        """Compute a sensitivity image once and keep it on the device."""
+        torch = self.torch
+        with self._sens_lock:
+            if key in self.sens:
+                return self.sens[key]
+            nvox = grid[0] * grid[1] * grid[2]
+            s = torch.zeros(nvox, dtype=torch.float64, device=f"cuda:{self.device}")
+            with self.B.Context(geometry, grid) as ctx:
+                ctx.sensitivity(lors, s)
+            torch.cuda.synchronize(self.device)
+            self.sens[key] = s
+            return s
+
+    def _context(self, slot, job):
+        key = (tuple(job.grid), tuple(job.geometry))
+        ctx = self.contexts[slot].get(key)
+        if ctx is None:
+            ctx = self.B.Context(job.geometry, job.grid)
+            ctx.set_stream(self.streams[slot].cuda_stream)
+            self.contexts[slot][key] = ctx
+        return ctx
+
+    def run(self, job, slot):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        ctx = self._context(slot, job)
+        ctx.set_sensitivity(self.sens[job.sens_key])
+        nvox = job.grid[0] * job.grid[1] * job.grid[2]
+        img = torch.empty(nvox, dtype=torch.float32).pin_memory() if self.keep_results else None
+        cons = np.zeros((job.n_iter, 2))
+        ctx.mlem(self.B.make_events(job.events), job.n_iter, None, img, cons)
+        job.result = img.numpy() if img is not None else None
+        job.conservation = cons
+
+    def close(self):
+        for per_slot in self.contexts:
+            for ctx in per_slot.values():
+                ctx.close()
+            per_slot.clear()
+
+
+def poisson_arrivals(n, rate_per_s, seed):
+    """Arrival times of a Poisson stream (exponential gaps)."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, n))

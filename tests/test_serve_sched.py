@@ -1,0 +1,104 @@
+"""Host-side logic of the continuous-batching server (no GPU): admission by
+slots and HBM footprint, first fit in arrival order, release on completion
+and on failure, latency bookkeeping."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1706_07075_b300.serve import Job, Server, poisson_arrivals
+
+
+class FakeExecutor:
+    """Sleeps for a job-dependent time and records concurrency and memory use."""
+
+    def __init__(self, server_ref, fail_ids=()):
+        self.server_ref = server_ref
+        self.fail_ids = set(fail_ids)
+        self.lock = threading.Lock()
+        self.running = 0
+        self.peak_running = 0
+        self.peak_bytes = 0
+        self.order = []
+
+    def run(self, job, slot):
+        srv = self.server_ref[0]
+        with self.lock:
+            self.running += 1
+            self.peak_running = max(self.peak_running, self.running)
+            self.peak_bytes = max(self.peak_bytes, srv._in_use)
+            self.order.append(job.job_id)
+        time.sleep(0.002 * job.n_iter)
+        with self.lock:
+            self.running -= 1
+        if job.job_id in self.fail_ids:
+            raise RuntimeError("injected failure")
+        job.result = job.job_id
+
+
+def make_job(i, n_events, arrival=0.0, grid=(10, 10, 10, 1, 1, 1, 0, 0, 0), n_iter=3):
+    return Job(i, arrival, np.zeros((7, n_events), np.float32), (100.0, 100.0, 90.0), grid, n_iter)
+
+
+def test_slots_and_budget_are_never_exceeded():
+    ref = [None]
+    ex = FakeExecutor(ref)
+    budget = 3 * make_job(0, 1_000_000).footprint()
+    srv = Server(ex, slots=4, hbm_budget_bytes=budget)
+    ref[0] = srv
+    jobs = [make_job(i, 1_000_000 if i % 3 else 200_000, arrival=0.001 * i) for i in range(30)]
+    stats = srv.replay(jobs)
+    assert stats["jobs"] == 30 and all(j.result == j.job_id for j in jobs)
+    assert ex.peak_running <= 4
+    assert ex.peak_bytes <= budget
+    assert stats["max_concurrent"] >= 2                      # work overlapped
+    assert all(j.latency >= 0 and j.admitted >= j.arrival - 1e-9 for j in jobs)
+
+
+def test_first_fit_lets_a_small_job_pass_a_large_one():
+    ref = [None]
+    ex = FakeExecutor(ref)
+    small = make_job(0, 10).footprint()
+    big = make_job(1, 10, grid=(1000, 1000, 100, 1, 1, 1, 0, 0, 0))     # 2 GB of images
+    srv = Server(ex, slots=3, hbm_budget_bytes=big.footprint() + small)
+    ref[0] = srv
+    srv.start()
+    with srv._lock:
+        # occupy part of the budget so that the big job cannot start yet
+        srv._in_use = 2 * small
+    first = make_job(2, 10, arrival=0.0)
+    srv.submit(big)                       # does not fit next to the reserved bytes
+    srv.submit(first)                     # fits: admitted although it came later
+    time.sleep(0.05)
+    assert first.admitted is not None and big.admitted is None
+    with srv._lock:
+        srv._in_use -= 2 * small
+        srv._admit_locked()
+    srv.drain(timeout=5)
+    assert big.result == 1
+
+
+def test_failed_job_releases_its_slot_and_memory():
+    ref = [None]
+    ex = FakeExecutor(ref, fail_ids={3})
+    srv = Server(ex, slots=2, hbm_budget_bytes=make_job(0, 1000).footprint() * 2)
+    ref[0] = srv
+    jobs = [make_job(i, 1000, arrival=0.0) for i in range(6)]
+    srv.start()
+    for j in jobs:
+        srv.submit(j)
+    with pytest.raises(RuntimeError, match="injected failure"):
+        srv.drain(timeout=5)
+    assert srv._in_use == 0 and sorted(srv._free_slots) == [0, 1]
+    assert sum(1 for j in jobs if j.result is not None) == 5
+
+
+def test_oversized_job_is_rejected_and_stats():
+    ref = [None]
+    srv = Server(FakeExecutor(ref), slots=1, hbm_budget_bytes=1000)
+    ref[0] = srv
+    with pytest.raises(ValueError):
+        srv.submit(make_job(0, 10))
+    t = poisson_arrivals(1000, 50.0, 3)
+    assert np.all(np.diff(t) > 0) and abs(1000 / t[-1] - 50.0) < 10.0

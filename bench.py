@@ -45,6 +45,11 @@ def parse():
                     help="fix the event-pass launch: threads,blocks_per_sm,chunk,cached_pieces,tail_eval "
                          "(default: the library's autotuner)")
     ap.add_argument("--no-graphs", action="store_true", help="launch iterations directly instead of graph replay")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the region-divided and packed/BF16 legs that follow the main measurement")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the served-reconstruction workload (Poisson stream of mixed jobs) instead")
+    ap.add_argument("--serve-jobs", type=int, default=200)
     return ap.parse_args()
 
 
@@ -213,6 +218,153 @@ def run_reference(args):
     return 0
 
 
+FULLBODY_REGIONS = [(0, 67), (67, 134), (134, 200), (200, 267), (267, 334), (334, 400), (400, 467),
+                    (467, 534), (534, 600)]
+
+
+def _timed_steps(stream, k, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(k):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def time_regions_leg(ctx, B, n, args, stream):
+    """Region-divided form (Sec. 2.5): split by TOF z into nine regions, all
+    regions' events in one event-pass launch per iteration, stitch.  Counts the
+    original events (not their duplicates) per iteration."""
+    import numpy as np
+    sigma = ctx.get_info()["sigma_mm"]
+    margin = 3.0 * sigma + 6.0
+    cons = np.zeros((args.iters, 9, 2))
+    ctx.mlem_regions(None, FULLBODY_REGIONS, margin, 6.0, args.iters, None, None, cons)   # warm-up (+ autotune)
+    st0 = ctx.get_stats()
+    ms = _timed_steps(stream, args.steps, lambda: ctx.mlem_regions(None, FULLBODY_REGIONS, margin, 6.0, args.iters,
+                                                                     None, None, cons))
+    st1 = ctx.get_stats()
+    return {"workload": "fullbody 9 TOF regions, shell 6 mm, margin 3 sigma + shell", "value": n * args.iters *
+            args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+            "launch": list(ctx.get_launch()), "n_eff_per_region_last": [float(x) for x in cons[-1, :, 0]],
+            "steps": args.steps}
+
+
+def time_packed_leg(ctx, B, synth, ev, n, args, stream):
+    """Precision-packed form: int16 endpoints on a 0.05 mm lattice + FP16 d
+    (16 B per event) and the forward gather from a BF16 image copy."""
+    import numpy as np
+    rec = synth.pack_events(ev)
+    ctx.load_events(B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM))
+    del rec
+    ctx.set_gather_bf16(1)
+    cons = np.zeros((args.iters, 2))
+    ctx.mlem(None, args.iters, None, None, cons)     # warm-up (+ autotune for the packed format)
+    st0 = ctx.get_stats()
+    ms = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons))
+    st1 = ctx.get_stats()
+    ctx.set_gather_bf16(0)
+    return {"workload": "fullbody packed int16/FP16 events, BF16 gather", "value": n * args.iters * args.steps /
+            (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]), "launch": list(ctx.get_launch()),
+            "conservation_last": [float(x) for x in cons[-1]], "steps": args.steps}
+
+
+def run_serve(args):
+    """Served reconstruction: a Poisson stream of jobs mixing single-region slabs
+    (150x150x80 voxels, events whose TOF point lies in the slab), full bodies
+    (150x150x600) and small fields of view (128^3 voxels of 0.5 mm), 3 iterations
+    each, 60/10/30%, at 0.8x the serial capacity measured on one job of each kind."""
+    import numpy as np
+    import torch
+    from paper_1706_07075_b300 import synth
+    from paper_1706_07075_b300.serve import Job, LibreconExecutor, Server, poisson_arrivals
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    n_fb = args.events
+    fb = synth.events("fullbody", n_fb, args.seed)
+    p1, p2, d = fb[0:3], fb[3:6], fb[6]
+    dz = p1[2] - p2[2]
+    D = np.sqrt((p1[0] - p2[0]) ** 2 + (p1[1] - p2[1]) ** 2 + dz ** 2)
+    z = 0.5 * (p1[2] + p2[2]) + d * dz / D
+    del p1, p2, d, dz, D
+    geo_fb = (400.0, 2400.0, 45.0)
+    kinds = {"fullbody": (geo_fb, synth.grid_of("fullbody"), [torch.from_numpy(fb).pin_memory()])}
+    slabs = []
+    for z0 in np.arange(-1040.0, 900.0, 240.0):
+        keep = (z >= z0) & (z < z0 + 320.0)
+        if keep.sum() >= 1_000_000:
+            slabs.append((z0, torch.from_numpy(np.ascontiguousarray(fb[:, keep])).pin_memory()))
+    del z
+    for z0, evs in slabs:
+        kinds[f"region{int(z0)}"] = (geo_fb, (150, 150, 80, 4.0, 4.0, 4.0, -300.0, -300.0, float(z0)), [evs])
+    kinds["smallfov"] = ((60.0, 100.0, 90.0), synth.grid_of("smallfov"),
+                         [torch.from_numpy(synth.events("smallfov", 5_000_000, args.seed + k)).pin_memory()
+                          for k in range(2)])
+    ex = LibreconExecutor(slots=3)
+    lors_fb = synth.sensitivity_lors("fullbody", 20_000_000, args.seed)
+    for k, (geo, grid, _) in kinds.items():
+        lors = lors_fb if geo == geo_fb else synth.sensitivity_lors("smallfov", 10_000_000, args.seed)
+        ex.register_sensitivity(k, geo, grid, lors)
+    # serial service time of one job of each kind (warm)
+    service = {}
+    for k, (geo, grid, evs) in kinds.items():
+        for rep in range(2):
+            j = Job(0, 0.0, evs[0], geo, grid, args.iters, sens_key=k, kind=k)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ex.run(j, 0)
+            torch.cuda.synchronize()
+            service[k] = time.perf_counter() - t
+    region_kinds = [k for k in kinds if k.startswith("region")]
+    mix = [("region", 0.6), ("fullbody", 0.1), ("smallfov", 0.3)]
+    mean_service = (0.6 * np.mean([service[k] for k in region_kinds]) + 0.1 * service["fullbody"] +
+                    0.3 * service["smallfov"])
+    rate = 0.8 / mean_service
+    rng = np.random.default_rng(args.seed)
+    arrivals = poisson_arrivals(args.serve_jobs, rate, args.seed)
+    jobs = []
+    for i, t in enumerate(arrivals):
+        u = rng.uniform()
+        kind = "region" if u < 0.6 else ("fullbody" if u < 0.7 else "smallfov")
+        if kind == "region":
+            kind = region_kinds[int(rng.integers(0, len(region_kinds)))]
+        geo, grid, evs = kinds[kind]
+        ev = evs[int(rng.integers(0, len(evs)))]
+        jobs.append(Job(i, float(t), ev, geo, grid, args.iters, sens_key=kind, kind=kind))
+    ex.keep_results = False
+    srv = Server(ex, slots=3, hbm_budget_bytes=200 << 30)
+    sampler = ClockSampler(local)
+    sampler.start()
+    stats = srv.replay(jobs)
+    clocks = sampler.stop()
+    ex.close()
+    by_kind = {}
+    for j in srv.done:
+        key = "region" if j.kind.startswith("region") else j.kind
+        by_kind.setdefault(key, []).append(j.latency)
+    line = {"metric": "served TOF-MLEM reconstruction: p50/p99 job latency and aggregate events x iterations / s",
+            "value": stats["p50_s"], "unit": "s", "p50_s": stats["p50_s"], "p99_s": stats["p99_s"],
+            "events_iters_per_s": stats["events_iters_per_s"], "jobs": stats["jobs"],
+            "max_concurrent": stats["max_concurrent"], "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "dtype": "f32", "config": {"workload": "served mix: region slabs 150x150x80 / full body 150x150x600 / "
+                                                   "small FOV 128^3 @ 0.5 mm, 60/10/30%, 3 iterations",
+                                       "arrival_rate_jobs_per_s": rate, "slots": 3, "hbm_budget_gb": 200,
+                                       "region_events": {k: int(kinds[k][2][0].shape[1]) for k in region_kinds},
+                                       "fullbody_events": n_fb, "smallfov_events": 5_000_000},
+            "serial_service_s": service,
+            "latency_p50_by_kind_s": {k: float(np.percentile(v, 50)) for k, v in by_kind.items()},
+            "latency_p99_by_kind_s": {k: float(np.percentile(v, 99)) for k, v in by_kind.items()},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -292,6 +444,11 @@ def run_ours(args):
     h2d = ev.nbytes
     d2h = img.numel() * 4 + cons.nbytes
 
+    legs = {}
+    if not args.no_legs:
+        legs["regions"] = time_regions_leg(ctx, B, n, args, stream)
+        legs["packed_bf16"] = time_packed_leg(ctx, B, synth, ev, n, args, stream)
+
     # roofline of the dominant kernel (the fused event pass)
     passes = max(1, stats["pass_launches"])
     pass_ms = stats["pass_ms"] / passes
@@ -308,6 +465,7 @@ def run_ours(args):
                    "d2h_bytes_per_step": int(d2h)},
            "gpu_launches": int(stats["kernel_launches"]),
            "clocks": clocks,
+           "legs": legs,
            "extra": {"t_generate_s": t_gen, "t_sensitivity_s": t_sens, "t_load_s": t_load,
                      "pass_ms": pass_ms, "update_ms": upd_ms, "conservation_last": list(cons[-1])}}
     if rank == 0:
@@ -345,6 +503,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -47,17 +47,17 @@ __global__ void k_gather(const float* img, uint32_t n_words, int per_thread, flo
     if (acc == 1234.5f) sink[t] = acc;
 }
 
-// One scattered gather and one scattered reduction per step, the L2 access
-// pattern of a Siddon piece in the fused MLEM pass.
-__global__ void k_mixed(float* img, uint32_t n_words, int per_thread, float* sink)
+// One scattered gather from `lam` and one scattered reduction into `C` (two
+// separate images, as in the fused MLEM pass) per step.
+__global__ void k_mixed(const float* lam, float* C, uint32_t n_words, int per_thread, float* sink)
 {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t h = hash32(t * 0xc2b2ae35u + 11u);
     float acc = 0.f;
     for (int k = 0; k < per_thread; ++k) {
         h = hash32(h + (uint32_t)k);
-        acc += __ldg(img + h % n_words);
-        atomicAdd(img + (h >> 7) % n_words, 1e-7f);
+        acc += __ldg(lam + h % n_words);
+        atomicAdd(C + (h >> 7) % n_words, 1e-7f);
     }
     if (acc == 1234.5f) sink[t] = acc;
 }
@@ -114,12 +114,13 @@ extern "C" int recon_probe_gather(const float* img, int64_t n_words, float* sink
                    (double)blocks * threads * per_thread, ops_per_s);
 }
 
-extern "C" int recon_probe_mixed(float* img, int64_t n_words, float* sink, void* stream, double* steps_per_s)
+extern "C" int recon_probe_mixed(const float* lam, float* C, int64_t n_words, float* sink, void* stream,
+                                 double* steps_per_s)
 {
-    if (!img || !sink || n_words <= 0 || n_words >= (1LL << 32) || !steps_per_s) return 1;
+    if (!lam || !C || !sink || n_words <= 0 || n_words >= (1LL << 32) || !steps_per_s) return 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int threads = 256, blocks = 148 * 64, per_thread = 256;
-    return time_it(s, [&] { k_mixed<<<blocks, threads, 0, s>>>(img, (uint32_t)n_words, per_thread, sink); },
+    return time_it(s, [&] { k_mixed<<<blocks, threads, 0, s>>>(lam, C, (uint32_t)n_words, per_thread, sink); },
                    (double)blocks * threads * per_thread, steps_per_s);
 }
 

@@ -25,9 +25,10 @@ int recon_probe_l2_red(float* img, int64_t n_words, int32_t runs, void* stream, 
 /* Scattered 4-byte read-only gathers from img[0..n_words); sink: 148*64*256 floats. */
 int recon_probe_gather(const float* img, int64_t n_words, float* sink, void* stream, double* ops_per_s);
 
-/* Steps per second of one scattered gather plus one scattered reduction each (the L2
- * access pattern of one Siddon piece of the fused pass); img is modified. */
-int recon_probe_mixed(float* img, int64_t n_words, float* sink, void* stream, double* steps_per_s);
+/* Steps per second of one scattered gather from lam plus one scattered reduction into C
+ * (two images of n_words each: the L2 access pattern of one Siddon piece of the fused
+ * pass); C is modified. */
+int recon_probe_mixed(const float* lam, float* C, int64_t n_words, float* sink, void* stream, double* steps_per_s);
 
 /* erfcf evaluations per second (FP32 ALU); sink: 148*64*256 floats. */
 int recon_probe_erfc(float* sink, void* stream, double* ops_per_s);

@@ -51,6 +51,21 @@ void release(DevBuf& b)
     b.bytes = 0;
 }
 
+// Region division prepared for the batched reconstruction: the split, the
+// slab layout and each region's start value, valid for one (events,
+// sensitivity, division) combination.
+struct RegionPrep {
+    bool valid = false;
+    long long ev_gen = -1, sens_gen = -1;
+    std::vector<recon_region> regions;
+    double margin = 0, shell = 0;
+    int fmt = -1;
+    std::vector<long long> off;   // region event offsets (R + 2 entries from the split)
+    std::vector<int> lo, hi;      // slab slice ranges
+    std::vector<long long> rv;    // slab voxel offsets (R + 1)
+    std::vector<float> start;     // uniform start value per region
+};
+
 }  // namespace
 
 struct recon_ctx {
@@ -93,6 +108,8 @@ struct recon_ctx {
 
     // region division
     DevBuf codes, counts, offsets, base, idx, ev_reg, lam_reg, C_reg, s_reg, bf16_reg, reg_vox_reg;
+    RegionPrep region_prep;
+    long long sens_generation = 0;
 };
 
 namespace {
@@ -274,6 +291,7 @@ recon_status finish_sensitivity(recon_ctx* ctx)
     recon_status s = host_sum(ctx, ctx->red_partial.as<double>(), b, &ctx->sens_total);
     if (s != RECON_OK) return s;
     ctx->have_sens = true;
+    ctx->sens_generation++;
     invalidate_graph(ctx);
     return RECON_OK;
 }
@@ -990,55 +1008,86 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
     if (!ctx->have_sens) return fail(ctx, RECON_ESTATE, "no sensitivity image (call recon_sensitivity first)");
     if (!ctx->have_ev) return fail(ctx, RECON_ESTATE, "no events loaded");
     const int R = n_regions;
-    std::vector<long long> off;
-    s = split_internal(ctx, R, regions, shell_mm, off);
-    if (s != RECON_OK) return s;
-    const long long total = off[R];
     const bool packed = ctx->fmt == FMT_PACKED;
-    const size_t rec = packed ? 16 : 32;
-    CK(ensure(ctx->ev_reg, rec * (size_t)std::max(1LL, total)));
-    CK(launch_region_gather(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr,
-                            ctx->codes.as<uint8_t>(), ctx->idx.as<int>(), total,
-                            packed ? nullptr : ctx->ev_reg.as<float4>(), packed ? ctx->ev_reg.as<int4>() : nullptr,
-                            ctx->stream));
-    if (total > 0) ctx->stats.kernel_launches += 1;
-
-    std::vector<int> lo, hi;
-    slab_ranges(ctx, R, regions, margin_mm, lo, hi);
-    const long long plane = (long long)ctx->grid.nx * ctx->grid.ny;
-    std::vector<long long> rv(R + 1, 0);
-    for (int r = 0; r < R; ++r) rv[r + 1] = rv[r] + plane * (hi[r] - lo[r]);
-    const long long nvt = rv[R];
-    CK(ensure(ctx->lam_reg, sizeof(float) * nvt));
-    CK(ensure(ctx->C_reg, sizeof(float) * nvt));
-    CK(ensure(ctx->s_reg, sizeof(float) * nvt));
-    CK(ensure(ctx->reg_vox_reg, sizeof(long long) * (R + 1)));
-    CK(cudaMemcpyAsync(ctx->reg_vox_reg.p, rv.data(), sizeof(long long) * (R + 1), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CK(ensure(ctx->red_partial, sizeof(double) * 1024));
-    // per-region slab sensitivity (FP32 copy of the global s) and start image
-    for (int r = 0; r < R; ++r) {
-        const long long nr = rv[r + 1] - rv[r];
-        const int b = reduce_blocks(nr);
-        CK(launch_sens_finish(ctx->s64.as<double>() + lo[r] * plane, nr, ctx->s_reg.as<float>() + rv[r],
-                              ctx->red_partial.as<double>(), b, ctx->stream));
-        double S = 0, W = 0;
-        s = host_sum(ctx, ctx->red_partial.as<double>(), b, &S);
+    RegionPrep& rp = ctx->region_prep;
+    const bool reuse = rp.valid && rp.ev_gen == ctx->ev_generation && rp.sens_gen == ctx->sens_generation &&
+                       rp.margin == margin_mm && rp.shell == shell_mm && rp.fmt == ctx->fmt &&
+                       (int)rp.regions.size() == R &&
+                       std::equal(rp.regions.begin(), rp.regions.end(), regions, [](const recon_region& a,
+                                                                                     const recon_region& b) {
+                           return a.z_lo == b.z_lo && a.z_hi == b.z_hi;
+                       });
+    if (!reuse) {
+        // split, region-ordered event copy, slab sensitivities and start values:
+        // kept until the events, the sensitivity or the division change
+        rp.valid = false;
+        s = split_internal(ctx, R, regions, shell_mm, rp.off);
         if (s != RECON_OK) return s;
-        const long long ne = off[r + 1] - off[r];
-        if (ne > 0) {
-            const int bw = reduce_blocks(ne);
-            CK(launch_reduce_weights(packed ? nullptr : ctx->ev_reg.as<float4>() + 2 * off[r],
-                                     packed ? ctx->ev_reg.as<int4>() + off[r] : nullptr, ne,
-                                     ctx->red_partial.as<double>(), bw, ctx->stream));
-            s = host_sum(ctx, ctx->red_partial.as<double>(), bw, &W);
-            if (s != RECON_OK) return s;
-            ctx->stats.kernel_launches += 1;
+        const long long total = rp.off[R];
+        const size_t rec = packed ? 16 : 32;
+        CK(ensure(ctx->ev_reg, rec * (size_t)std::max(1LL, total)));
+        CK(launch_region_gather(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr,
+                                ctx->codes.as<uint8_t>(), ctx->idx.as<int>(), total,
+                                packed ? nullptr : ctx->ev_reg.as<float4>(), packed ? ctx->ev_reg.as<int4>() : nullptr,
+                                ctx->stream));
+        if (total > 0) ctx->stats.kernel_launches += 1;
+        slab_ranges(ctx, R, regions, margin_mm, rp.lo, rp.hi);
+        const long long plane = (long long)ctx->grid.nx * ctx->grid.ny;
+        rp.rv.assign(R + 1, 0);
+        for (int r = 0; r < R; ++r) rp.rv[r + 1] = rp.rv[r] + plane * (rp.hi[r] - rp.lo[r]);
+        const long long nvt = rp.rv[R];
+        CK(ensure(ctx->lam_reg, sizeof(float) * nvt));
+        CK(ensure(ctx->C_reg, sizeof(float) * nvt));
+        CK(ensure(ctx->s_reg, sizeof(float) * nvt));
+        CK(ensure(ctx->reg_vox_reg, sizeof(long long) * (R + 1)));
+        CK(cudaMemcpyAsync(ctx->reg_vox_reg.p, rp.rv.data(), sizeof(long long) * (R + 1), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(ensure(ctx->red_partial, sizeof(double) * 1024 * 2 * R));
+        // per-region slab sensitivity (FP32 copy of the global s), sum of s and sum of w
+        std::vector<int> bs(R), bw(R);
+        double* part = ctx->red_partial.as<double>();
+        for (int r = 0; r < R; ++r) {
+            const long long nr = rp.rv[r + 1] - rp.rv[r];
+            bs[r] = reduce_blocks(nr);
+            CK(launch_sens_finish(ctx->s64.as<double>() + rp.lo[r] * plane, nr, ctx->s_reg.as<float>() + rp.rv[r],
+                                  part + (size_t)2048 * r, bs[r], ctx->stream));
+            const long long ne = rp.off[r + 1] - rp.off[r];
+            bw[r] = ne > 0 ? reduce_blocks(ne) : 0;
+            if (ne > 0)
+                CK(launch_reduce_weights(packed ? nullptr : ctx->ev_reg.as<float4>() + 2 * rp.off[r],
+                                         packed ? ctx->ev_reg.as<int4>() + rp.off[r] : nullptr, ne,
+                                         part + (size_t)2048 * r + 1024, bw[r], ctx->stream));
+            ctx->stats.kernel_launches += ne > 0 ? 2 : 1;
         }
-        CK(launch_fill_masked(ctx->lam_reg.as<float>() + rv[r], ctx->s_reg.as<float>() + rv[r], nr,
-                              (float)(S > 0 ? W / S : 0.0), ctx->stream));
-        ctx->stats.kernel_launches += 2;
+        std::vector<double> h((size_t)2048 * R);
+        CK(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        rp.start.assign(R, 0.f);
+        for (int r = 0; r < R; ++r) {
+            double S = 0, W = 0;
+            for (int k = 0; k < bs[r]; ++k) S += h[(size_t)2048 * r + k];
+            for (int k = 0; k < bw[r]; ++k) W += h[(size_t)2048 * r + 1024 + k];
+            rp.start[r] = (float)(S > 0 ? W / S : 0.0);
+        }
+        rp.regions.assign(regions, regions + R);
+        rp.margin = margin_mm;
+        rp.shell = shell_mm;
+        rp.fmt = ctx->fmt;
+        rp.ev_gen = ctx->ev_generation;
+        rp.sens_gen = ctx->sens_generation;
+        rp.valid = true;
     }
+    const std::vector<long long>& off = rp.off;
+    const std::vector<int>& lo = rp.lo;
+    const std::vector<int>& hi = rp.hi;
+    const std::vector<long long>& rv = rp.rv;
+    const long long total = off[R];
+    const long long nvt = rv[R];
+    // start image: uniform on each slab's mask with sum s lambda = sum w of its events
+    for (int r = 0; r < R; ++r)
+        CK(launch_fill_masked(ctx->lam_reg.as<float>() + rv[r], ctx->s_reg.as<float>() + rv[r], rv[r + 1] - rv[r],
+                              rp.start[r], ctx->stream));
+    ctx->stats.kernel_launches += R;
     CK(cudaMemsetAsync(ctx->C_reg.p, 0, sizeof(float) * nvt, ctx->stream));
     if (ctx->bf16) {
         CK(ensure(ctx->bf16_reg, sizeof(uint16_t) * nvt));

@@ -174,7 +174,7 @@ class LibreconExecutor:
     """Runs jobs through librecon: one CUDA stream per slot, contexts reused per
     grid, sensitivity images resident per key."""
 
-    def __init__(self, slots, device=0, sensitivities=None, keep_results=True):
+    def __init__(self, slots, device=0, sensitivities=None, keep_results=True, launch=(192, 0, 0, 0, 1)):
         import torch
         from . import binding as B
         self.B = B
@@ -183,8 +183,10 @@ class LibreconExecutor:
         torch.cuda.set_device(device)
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.contexts = [dict() for _ in range(slots)]   # per slot: grid -> Context
+        self.loaded = [dict() for _ in range(slots)]     # per slot: grid -> sensitivity key resident in it
         self.sens = dict(sensitivities or {})            # key -> device float64 tensor
         self.keep_results = keep_results
+        self.launch = launch                              # fixed event-pass launch (None: autotune per job size)
         self._sens_lock = threading.Lock()
 
     def register_sensitivity(self, key, geometry, grid, lors):
@@ -207,14 +209,35 @@ class LibreconExecutor:
         if ctx is None:
             ctx = self.B.Context(job.geometry, job.grid)
             ctx.set_stream(self.streams[slot].cuda_stream)
+            if self.launch is not None:
+                ctx.set_launch(*self.launch)
             self.contexts[slot][key] = ctx
+        if self.loaded[slot].get(key) != job.sens_key:
+            ctx.set_sensitivity(self.sens[job.sens_key])
+            self.loaded[slot][key] = job.sens_key
         return ctx
+
+    def warm(self, jobs):
+        """Create every (slot, grid) context the jobs need and run one of each kind
+        per slot, so that first-use costs stay out of the measured latencies."""
+        seen = set()
+        for job in jobs:
+            for slot in range(len(self.streams)):
+                key = (slot, tuple(job.grid), job.sens_key)
+                if key in seen:
+                    continue
+                seen.add(key)
+                keep = self.keep_results
+                self.keep_results = False
+                try:
+                    self.run(job, slot)
+                finally:
+                    self.keep_results = keep
 
     def run(self, job, slot):
         torch = self.torch
         torch.cuda.set_device(self.device)
         ctx = self._context(slot, job)
-        ctx.set_sensitivity(self.sens[job.sens_key])
         nvox = job.grid[0] * job.grid[1] * job.grid[2]
         img = torch.empty(nvox, dtype=torch.float32).pin_memory() if self.keep_results else None
         cons = np.zeros((job.n_iter, 2))

@@ -212,10 +212,13 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "fullbody-146M-150x150x600-4mm (oracle: bounded sample)", "events_per_step": n_sample,
-                   "iters_per_step": 1},
+        "config": {"workload": "fullbody-146M-150x150x600-4mm", "events": 146_000_000, "iters_per_step": args.iters,
+                   "sensitivity_lors": args.lors, "tof_fwhm_ps": 300.0,
+                   "l2": "inputs larger than L2 (events 32 B x 146M = 4.7 GB resident)", "parallelism": "single"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
-                         "sample": f"1 FP64 MLEM iteration over {n_sample} full-body events per step"},
+                         "sample": f"each step: 1 FP64 MLEM iteration over a bounded sample of {n_sample} full-body "
+                                   f"events (the 150x150x600 grid, sensitivity from 200000 LORs); the metric counts "
+                                   f"those sampled events x iterations per second"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -60,6 +60,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x):
+    """Largest value over the ranks of the process group (x itself without one).
+    Ranks run independent reconstructions (replicas, no data-path collective);
+    the job's time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, ms):
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle samples during the timed region."""
 
@@ -434,11 +453,8 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     stats = ctx.get_stats()
     ctx.set_timing(0)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = n * args.iters * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(ms)
+    value = aggregate_rate(n * args.iters * args.steps, world, ms)
 
     # end to end through the public call: pinned host events in, host image out
     img = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()

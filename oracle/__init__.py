@@ -22,12 +22,21 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   region_slabs ........ pinned (the paper's 176-slice extended regions)
   mlem_regions ........ pinned through mlem and region_codes; the stitched
                         image's count total is a closed form (N events)
+  lut_samples ......... pinned (unit sum, symmetry, spacing; second moment
+                        converges to the truncated-normal variance)
+  forward_lut /
+  backproject_lut ..... pinned (brute-force sample positions on axis lines;
+                        unit mass inside the grid; adjointness; convergence
+                        to the exact Siddon x Phi projector as N grows)
 """
 from .core import (  # noqa: F401
     Grid,
     backproject,
+    backproject_lut,
     count_visits,
     forward,
+    forward_lut,
+    lut_samples,
     region_codes,
     region_members,
     sensitivity,

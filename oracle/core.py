@@ -85,6 +85,13 @@ def _load():
             lib.oracle_region_codes.argtypes = [planes, C.c_int64, C.c_int64, C.c_int32, dp, C.c_double,
                                                 C.POINTER(C.c_uint8), dp]
             lib.oracle_region_codes.restype = C.c_int64
+            fp = C.POINTER(C.c_float)
+            lib.oracle_lut_samples.argtypes = [C.c_int32, C.c_double, C.c_double, dp, dp]
+            lib.oracle_lut_samples.restype = None
+            lib.oracle_forward_lut.argtypes = [gp, planes, C.c_int64, C.c_int64, C.c_int32, dp, fp, dp, dp]
+            lib.oracle_forward_lut.restype = C.c_int
+            lib.oracle_backproject_lut.argtypes = [gp, planes, C.c_int64, C.c_int64, C.c_int32, dp, fp, dp, dp]
+            lib.oracle_backproject_lut.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -262,6 +269,63 @@ def sensitivity(grid, lors, threads=None):
     rcs = _run_threads(part, [(a, b, k) for k, (a, b) in enumerate(ranges)])
     if any(rc != 0 for rc in rcs):
         raise RuntimeError(f"oracle_sensitivity failed {rcs}")
+    total = np.zeros(grid.n_vox)
+    for acc in accs:
+        total += acc
+    return total
+
+
+# --------------------------------------------------- sampled TOF kernel
+
+def lut_samples(n_samples, sigma, K=3.0):
+    """Offsets t_k (mm) and unit-sum Gaussian weights w_k of the sampled kernel."""
+    t = np.zeros(n_samples)
+    w = np.zeros(n_samples)
+    _load().oracle_lut_samples(int(n_samples), float(sigma), float(K), _dptr(t), _dptr(w))
+    return t, w
+
+
+def _lut_args(n_samples, sigma, K):
+    t, w = lut_samples(n_samples, sigma, K)
+    t32 = np.ascontiguousarray(t.astype(np.float32))
+    return w, t32, t32.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def forward_lut(grid, events, lam, n_samples, sigma, K=3.0, threads=None):
+    """p_i with the sampled kernel: sum_k w_k lambda(voxel of sample k)."""
+    lib = _load()
+    keep, ptrs = _event_planes(events)
+    n = keep[0].shape[0]
+    lam = np.ascontiguousarray(lam, np.float64).reshape(-1)
+    p = np.zeros(n)
+    if n == 0:
+        return p
+    w, t32, tp = _lut_args(n_samples, sigma, K)
+    g = grid.c()
+
+    def part(i0, i1):
+        return lib.oracle_forward_lut(C.byref(g), ptrs, i0, i1, int(n_samples), _dptr(w), tp, _dptr(lam), _dptr(p))
+
+    _run_threads(part, _ranges(n, threads or threads_used(n)))
+    return p
+
+
+def backproject_lut(grid, events, r, n_samples, sigma, K=3.0, threads=None):
+    """C_j = sum over samples in voxel j of w_k r_i (sampled kernel)."""
+    lib = _load()
+    keep, ptrs = _event_planes(events)
+    n = keep[0].shape[0]
+    r = np.ascontiguousarray(r, np.float64).reshape(-1)
+    w, t32, tp = _lut_args(n_samples, sigma, K)
+    g = grid.c()
+    ranges = _ranges(n, threads or threads_used(n)) if n else []
+    accs = [np.zeros(grid.n_vox) for _ in ranges]
+
+    def part(i0, i1, k):
+        return lib.oracle_backproject_lut(C.byref(g), ptrs, i0, i1, int(n_samples), _dptr(w), tp, _dptr(r),
+                                          _dptr(accs[k]))
+
+    _run_threads(part, [(a, b, k) for k, (a, b) in enumerate(ranges)])
     total = np.zeros(grid.n_vox)
     for acc in accs:
         total += acc

@@ -23,7 +23,7 @@ import math
 
 import numpy as np
 
-from .core import Grid, backproject, forward, region_codes, region_members
+from .core import Grid, backproject, backproject_lut, forward, forward_lut, region_codes, region_members
 
 
 def uniform_start(sens, weights_total):
@@ -35,12 +35,14 @@ def uniform_start(sens, weights_total):
     return lam
 
 
-def mlem(grid, events, sens, n_iter, sigma, K=3.0, weights=None, init=None, threads=None, return_p=False):
+def mlem(grid, events, sens, n_iter, sigma, K=3.0, weights=None, init=None, threads=None, return_p=False,
+         lut_samples=None):
     """Run n_iter MLEM iterations.
 
     Returns (lambda, history) where history[k] = (N_eff, sum_j s_j lambda_j,
     log-likelihood at the image the iteration started from).  N_eff is the
-    weight of the events with p_i > 0 in iteration k.
+    weight of the events with p_i > 0 in iteration k.  lut_samples=N swaps the
+    exact projector for the sampled TOF kernel of Sec. 2.3 (N samples).
     """
     s = np.asarray(sens, np.float64).reshape(-1)
     assert s.size == grid.n_vox
@@ -51,12 +53,18 @@ def mlem(grid, events, sens, n_iter, sigma, K=3.0, weights=None, init=None, thre
     history = []
     p = None
     for _ in range(n_iter):
-        p = forward(grid, events, lam, sigma, K, threads)
+        if lut_samples:
+            p = forward_lut(grid, events, lam, lut_samples, sigma, K, threads)
+        else:
+            p = forward(grid, events, lam, sigma, K, threads)
         valid = p > 0
         r = np.zeros(n)
         r[valid] = w[valid] / p[valid]
         loglik = float(np.sum(w[valid] * np.log(p[valid])) - np.sum(s * lam))
-        Cimg = backproject(grid, events, r, sigma, K, threads)
+        if lut_samples:
+            Cimg = backproject_lut(grid, events, r, lut_samples, sigma, K, threads)
+        else:
+            Cimg = backproject(grid, events, r, sigma, K, threads)
         new = np.zeros_like(lam)
         new[mask] = lam[mask] * Cimg[mask] / s[mask]
         lam = new

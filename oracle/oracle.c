@@ -328,6 +328,95 @@ int oracle_sensitivity(const og_grid *g, const double *const lor[6], int64_t l0,
     return rc;
 }
 
+/* --------------------------------------- sampled TOF kernel (Sec. 2.3) */
+
+/*
+ * The paper's own projector: N samples equally spaced across the TOF kernel,
+ * centred on the TOF point, each carrying its Gaussian weight, the weights
+ * summing to one; each sample deposits its weight in the voxel that contains
+ * it ("direct technique for voxel filling").  Reading: the samples sit at the
+ * centres of N equal cells covering [-K sigma, K sigma]:
+ *     t_k = -K sigma + (k + 1/2) 2 K sigma / N,   w_k = phi(t_k/sigma) / sum_m phi(t_m/sigma).
+ */
+void oracle_lut_samples(int32_t N, double sigma, double K, double *t, double *w)
+{
+    double sum = 0.0;
+    for (int32_t k = 0; k < N; ++k) {
+        t[k] = -K * sigma + (k + 0.5) * (2.0 * K * sigma / N);
+        w[k] = exp(-0.5 * (t[k] / sigma) * (t[k] / sigma));
+        sum += w[k];
+    }
+    for (int32_t k = 0; k < N; ++k) w[k] /= sum;
+}
+
+/*
+ * Voxel of sample k of event i, or -1 outside the grid.  A voxel index is an
+ * integer decided by floating point, so it is decided here in FP32 with the
+ * operation sequence the GPU kernel uses (one rounding per operation; fmaf is
+ * the correctly rounded fused multiply-add), from the FP32 event values and
+ * the FP32 sample offset t32.  Everything else of the projector is FP64.
+ */
+static int64_t lut_voxel(const og_grid *g, const float e[7], float t32)
+{
+    const float dx = e[0] - e[3], dy = e[1] - e[4], dz = e[2] - e[5];
+    const float D = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+    if (!(D > 0.0f)) return -1;
+    const float inv = 1.0f / D;
+    const float u[3] = {dx * inv, dy * inv, dz * inv};
+    const float m[3] = {0.5f * (e[0] + e[3]), 0.5f * (e[1] + e[4]), 0.5f * (e[2] + e[5])};
+    const float o[3] = {(float)g->ox, (float)g->oy, (float)g->oz};
+    const float v[3] = {(float)g->vx, (float)g->vy, (float)g->vz};
+    const int32_t n[3] = {g->nx, g->ny, g->nz};
+    int64_t idx[3];
+    for (int k = 0; k < 3; ++k) {
+        const float c = fmaf(e[6], u[k], m[k]);   /* TOF point */
+        const float x = fmaf(t32, u[k], c);       /* sample position */
+        const float f = floorf((x - o[k]) / v[k]);
+        if (!(f >= 0.0f) || !(f < (float)n[k])) return -1;
+        idx[k] = (int64_t)f;
+    }
+    return idx[0] + (int64_t)g->nx * (idx[1] + (int64_t)g->ny * idx[2]);
+}
+
+static void event_f32(const double *const ev[7], int64_t i, float e[7])
+{
+    for (int k = 0; k < 7; ++k) e[k] = (float)ev[k][i];
+}
+
+/* p_i = sum_k w_k lambda(voxel of sample k), events [i0, i1). t32: the FP32
+ * sample offsets the GPU uses (the same values rounded once from t_k). */
+int oracle_forward_lut(const og_grid *g, const double *const ev[7], int64_t i0, int64_t i1, int32_t N,
+                       const double *w, const float *t32, const double *lambda, double *p_out)
+{
+    for (int64_t i = i0; i < i1; ++i) {
+        float e[7];
+        event_f32(ev, i, e);
+        double p = 0.0;
+        for (int32_t k = 0; k < N; ++k) {
+            int64_t j = lut_voxel(g, e, t32[k]);
+            if (j >= 0) p += w[k] * lambda[j];
+        }
+        p_out[i] = p;
+    }
+    return 0;
+}
+
+/* C_j += sum_k w_k r_i over the samples of events [i0, i1) falling in voxel j. */
+int oracle_backproject_lut(const og_grid *g, const double *const ev[7], int64_t i0, int64_t i1, int32_t N,
+                           const double *w, const float *t32, const double *r, double *C_acc)
+{
+    for (int64_t i = i0; i < i1; ++i) {
+        if (r[i] == 0.0) continue;
+        float e[7];
+        event_f32(ev, i, e);
+        for (int32_t k = 0; k < N; ++k) {
+            int64_t j = lut_voxel(g, e, t32[k]);
+            if (j >= 0) C_acc[j] += w[k] * r[i];
+        }
+    }
+    return 0;
+}
+
 /* ------------------------------------------------ TOF-assisted division */
 
 /*

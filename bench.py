@@ -45,6 +45,9 @@ def parse():
                     help="fix the event-pass launch: threads,blocks_per_sm,chunk,cached_pieces,tail_eval "
                          "(default: the library's autotuner)")
     ap.add_argument("--no-graphs", action="store_true", help="launch iterations directly instead of graph replay")
+    ap.add_argument("--samples", type=int, default=0,
+                    help="time the sampled TOF kernel with this many samples in the main measurement "
+                         "(default 0: the exact Siddon x Phi projector)")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the region-divided and packed/BF16 legs that follow the main measurement")
     ap.add_argument("--serve", action="store_true",
@@ -233,6 +236,8 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "fullbody-146M-150x150x600-4mm", "events": 146_000_000, "iters_per_step": args.iters,
                    "sensitivity_lors": args.lors, "tof_fwhm_ps": 300.0,
+                      "projector": f"sampled TOF kernel, {args.samples} samples" if args.samples else
+                      "exact Siddon pieces x Gaussian mass",
                    "l2": "inputs larger than L2 (events 32 B x 146M = 4.7 GB resident)", "parallelism": "single"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
                          "sample": f"each step: 1 FP64 MLEM iteration over a bounded sample of {n_sample} full-body "
@@ -299,6 +304,40 @@ def time_packed_leg(ctx, B, synth, ev, n, args, stream):
             (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]), "launch": list(ctx.get_launch()),
             "conservation_last": [float(x) for x in cons[-1]], "steps": args.steps}
+
+
+def time_lut_leg(ctx, B, n, args, stream, img_exact):
+    """The paper's own projector (Sec. 2.3): 32 equally spaced Gaussian samples
+    per event, each deposited in its voxel, against the exact Siddon x Phi
+    projector on the same resident events.  Accuracy: relative L2 distance of
+    the sampled projector's image to the exact one after the same iterations
+    from the same start, and of the two forward projections of that image."""
+    import numpy as np
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx.set_projector(B.PROJ_SAMPLED, 32)
+    cons = np.zeros((args.iters, 2))
+    ctx.mlem(None, args.iters, None, None, cons)     # warm-up
+    st0 = ctx.get_stats()
+    ms = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons))
+    st1 = ctx.get_stats()
+    img_lut = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
+    ctx.mlem(None, args.iters, None, img_lut, cons)
+    p_lut = torch.empty(n, dtype=torch.float32, device=dev)
+    p_ex = torch.empty(n, dtype=torch.float32, device=dev)
+    lam = img_exact.to(dev)
+    ctx.forward(None, lam, p_lut)
+    ctx.set_projector(B.PROJ_EXACT)
+    ctx.forward(None, lam, p_ex)
+    torch.cuda.synchronize(dev)
+    a, b = img_lut.double(), img_exact.double()
+    fwd_rel = float(torch.linalg.vector_norm(p_lut.double() - p_ex.double()) / torch.linalg.vector_norm(p_ex.double()))
+    return {"workload": "fullbody, sampled TOF kernel, 32 samples (Sec. 2.3)", "value": n * args.iters * args.steps /
+            (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+            "image_rel_l2_vs_exact": float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)),
+            "forward_rel_l2_vs_exact": fwd_rel, "conservation_last": [float(x) for x in cons[-1]],
+            "steps": args.steps}
 
 
 def run_serve(args):
@@ -426,6 +465,8 @@ def run_ours(args):
         ctx.set_launch(*[int(x) for x in args.launch.split(",")])
     if args.no_graphs:
         ctx.set_graphs(0)
+    if args.samples:
+        ctx.set_projector(B.PROJ_SAMPLED, args.samples)
     # warm-up (the first call also runs the launch autotuner)
     for _ in range(args.warmup):
         ctx.mlem(None, args.iters)
@@ -469,7 +510,8 @@ def run_ours(args):
     d2h = img.numel() * 4 + cons.nbytes
 
     legs = {}
-    if not args.no_legs:
+    if not args.no_legs and not args.samples:
+        legs["sampled_lut32"] = time_lut_leg(ctx, B, n, args, stream, img)
         legs["regions"] = time_regions_leg(ctx, B, n, args, stream)
         legs["packed_bf16"] = time_packed_leg(ctx, B, synth, ev, n, args, stream)
 
@@ -508,14 +550,17 @@ def run_ours(args):
         # FP32 reduction into C, both in L2-resident images: the bound is the
         # GPU's rate of such (gather + reduction) steps, measured live by the
         # mixed probe on an image of the same size.
-        mixed = probes.get("mixed_gsteps")
+        R, G = probes.get("l2_red_gops"), probes.get("gather_gops")
+        peak = 1.0 / (1.0 / R + 1.0 / G) if R and G else None
         out["roofline"] = {
-            "bound": "l2_random_access", "achieved": red_rate / 1e9, "peak": mixed, "unit": "Gpiece/s",
-            "frac": (red_rate / 1e9 / mixed) if mixed else None, "traffic": None,
+            "bound": "l2_random_access", "achieved": red_rate / 1e9, "peak": peak, "unit": "Gpiece/s",
+            "frac": (red_rate / 1e9 / peak) if peak else None, "traffic": None,
             "per_launch": {"events": n, "pieces": visits, "gathers": visits, "reductions": visits,
                            "hbm_bytes": 32.0 * n, "pass_ms": pass_ms},
-            "peak_source": "live probe: one scattered gather + one scattered red.global.add.f32 per step over an "
-                           "L2-resident image of the grid's size",
+            "peak_source": "live probes on an L2-resident image of the grid's size: R = scattered "
+                           "red.global.add.f32 per s, G = scattered 4-byte gathers per s; a piece costs one of each "
+                           "through the same L1/L2 path, so peak = 1 / (1/R + 1/G)",
+            "mixed_probe_gsteps": probes.get("mixed_gsteps"),
             "secondary": {"hbm_gbs": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
                           "hbm_peak_source": src,
                           "red_frac": red_rate / 1e9 / probes["l2_red_gops"],

@@ -144,6 +144,35 @@ recon_status recon_set_stream(recon_ctx* ctx, void* cuda_stream);
 /* Kernel truncation in sigmas, 0.5 <= k <= 8 (default 3). */
 recon_status recon_set_kernel_window(recon_ctx* ctx, double k_sigma);
 
+/* Projector of every later forward, backproject, mlem and mlem_regions call on ctx.
+ *
+ * RECON_PROJ_EXACT (default; n_samples ignored): the Siddon pieces of the line with
+ *   the exact TOF mass [Phi(tau_b/sigma) - Phi(tau_a/sigma)] / (2 Phi(K) - 1) of each
+ *   piece (Sec. 2.3, Gaussian kernel truncated at +-K sigma).
+ * RECON_PROJ_SAMPLED: the paper's own GPU projector (Sec. 2.3, Fig. 3): n_samples
+ *   points equally spaced over [-K sigma, K sigma] around the TOF point (the midpoints
+ *   of n_samples equal intervals), weights proportional to the Gaussian and summing to
+ *   one, each point deposited in the one voxel that contains it.  Sample k of event i
+ *   sits at c + t_k u, c = M + d u; its voxel is decided per axis in FP32 as
+ *   floor(fma(t_k, u/v, (c - o)/v)) with the operation order the kernel documents.
+ *   Points outside the grid are dropped.  The paper uses 32 samples on its GPU and 15
+ *   on its CPU.  The sample table travels in the kernel's constant parameter bank.
+ *
+ * Errors: EINVAL for an unknown projector or n_samples outside
+ * [1, RECON_MAX_TOF_SAMPLES].  The sampled projector runs a flat one-event-per-thread
+ * grid with the launch's threads_per_block; the other launch fields do not apply. */
+#define RECON_PROJ_EXACT 0
+#define RECON_PROJ_SAMPLED 1
+#define RECON_MAX_TOF_SAMPLES 64
+recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_samples);
+
+/* The sampled projector's table as the kernel uses it: *n_out = sample count (0 for
+ * the exact projector); offsets_mm[k] (signed distance from the TOF point along u) and
+ * weights[k] for k < *n_out, each nullable, caller-owned host arrays of `capacity`
+ * floats.  EINVAL (with *n_out set) when capacity is too small. */
+recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float* offsets_mm, float* weights,
+                                   int32_t* n_out);
+
 /* Forward gather from a BF16 copy of the image (1) or the FP32 image (0, default).
  * Backprojection always accumulates in FP32. */
 recon_status recon_set_gather_bf16(recon_ctx* ctx, int32_t on);
@@ -192,7 +221,9 @@ recon_status recon_load_events(recon_ctx* ctx, const recon_events* events);
 
 /* Forward projection p_i = sum_j a_ij lambda_j (Sec. 2.3/2.4) with
  * a_ij = [Phi(tau_b/sigma) - Phi(tau_a/sigma)] / (2 Phi(K) - 1) over the piece
- * [tau_a, tau_b] of the LOR inside voxel j and inside +-K sigma of the TOF point.
+ * [tau_a, tau_b] of the LOR inside voxel j and inside +-K sigma of the TOF point
+ * (RECON_PROJ_EXACT), or the summed weights of the samples in voxel j
+ * (RECON_PROJ_SAMPLED; see recon_set_projector).
  * events: NULL = the resident events, else loaded first (and kept resident).
  * image: nx*ny*nz floats (host or device); NULL = the context's current image.
  * p_out: n floats (host or device).  Errors: EINVAL, ESTATE (no events). */

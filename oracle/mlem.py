@@ -101,7 +101,8 @@ def stitch(grid, slabs, images):
     return out.reshape(-1)
 
 
-def mlem_regions(grid, events, sens, regions, shell_mm, margin_mm, n_iter, sigma, K=3.0, threads=None):
+def mlem_regions(grid, events, sens, regions, shell_mm, margin_mm, n_iter, sigma, K=3.0, threads=None,
+                 lut_samples=None):
     """Divide events by TOF-estimated z, reconstruct each slab, sum the slabs.
 
     Returns (image, per-region images, per-region histories, codes, offsets, idx).
@@ -119,7 +120,7 @@ def mlem_regions(grid, events, sens, regions, shell_mm, margin_mm, n_iter, sigma
         ev_r = [e[members] for e in events]
         g_r = slab_grid(grid, lo, hi)
         lam_r, h_r = mlem(g_r, ev_r, s3[lo:hi].reshape(-1), n_iter, sigma, K, weights=w_all[members],
-                          threads=threads)
+                          threads=threads, lut_samples=lut_samples)
         images.append(lam_r)
         hists.append(h_r)
     return stitch(grid, slabs, images), images, hists, codes, offsets, idx

@@ -369,9 +369,11 @@ static int64_t lut_voxel(const og_grid *g, const float e[7], float t32)
     const int32_t n[3] = {g->nx, g->ny, g->nz};
     int64_t idx[3];
     for (int k = 0; k < 3; ++k) {
+        const float iv = 1.0f / v[k];
         const float c = fmaf(e[6], u[k], m[k]);   /* TOF point */
-        const float x = fmaf(t32, u[k], c);       /* sample position */
-        const float f = floorf((x - o[k]) / v[k]);
+        const float A = (c - o[k]) * iv;          /* TOF point in voxel units */
+        const float B = u[k] * iv;                /* direction in voxel units */
+        const float f = floorf(fmaf(t32, B, A));  /* voxel of the sample at c + t u */
         if (!(f >= 0.0f) || !(f < (float)n[k])) return -1;
         idx[k] = (int64_t)f;
     }

@@ -72,6 +72,8 @@ SIGNATURES = {
     "recon_set_stream": (C.c_int, [_CTX, _VP]),
     "recon_set_kernel_window": (C.c_int, [_CTX, C.c_double]),
     "recon_set_gather_bf16": (C.c_int, [_CTX, C.c_int32]),
+    "recon_set_projector": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
+    "recon_get_tof_samples": (C.c_int, [_CTX, C.c_int32, _VP, _VP, C.POINTER(C.c_int32)]),
     "recon_set_launch": (C.c_int, [_CTX, C.POINTER(recon_launch)]),
     "recon_get_launch": (C.c_int, [_CTX, C.POINTER(recon_launch)]),
     "recon_set_timing": (C.c_int, [_CTX, C.c_int32]),
@@ -217,6 +219,24 @@ def recon_set_kernel_window(ctx, k_sigma):
 
 def recon_set_gather_bf16(ctx, on):
     return check(ctx, load().recon_set_gather_bf16(ctx, int(bool(on))))
+
+
+PROJ_EXACT = 0
+PROJ_SAMPLED = 1
+MAX_TOF_SAMPLES = 64
+
+
+def recon_set_projector(ctx, projector, n_samples=0):
+    return check(ctx, load().recon_set_projector(ctx, int(projector), int(n_samples)))
+
+
+def recon_get_tof_samples(ctx):
+    """(offsets_mm, weights) float32 arrays of the sampled projector (empty when exact)."""
+    t = np.zeros(MAX_TOF_SAMPLES, np.float32)
+    w = np.zeros(MAX_TOF_SAMPLES, np.float32)
+    n = C.c_int32(0)
+    check(ctx, load().recon_get_tof_samples(ctx, MAX_TOF_SAMPLES, t.ctypes.data, w.ctypes.data, C.byref(n)))
+    return t[:n.value].copy(), w[:n.value].copy()
 
 
 def recon_set_launch(ctx, threads_per_block=None, blocks_per_sm=0, chunk_events=0, cached_pieces=0, tail_eval=0):

@@ -158,6 +158,135 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
     }
 }
 
+// ------------------------------------------------------------------------
+// Sampled TOF kernel (Sec. 2.3, the paper's own projector): sample k of event
+// i sits at c + t_k u on the line, c = M + d u the TOF point, and adds its
+// weight w_k (unit sum over k) to the one voxel that contains it.  The voxel
+// decision is made per axis in voxel units, one IEEE rounding per operation:
+//     A = (c - o) * (1/v),  B = u * (1/v),  voxel = floor(fma(t_k, B, A)),
+// with u = (P1 - P2) * (1/|P1 - P2|) and |P1 - P2| from an fma chain.
+// Samples outside the grid are dropped.  Consecutive samples in the same
+// voxel are merged, so a voxel costs one gather and one reduction however
+// many samples it holds.
+
+struct LutLine {
+    float ax, ay, az, bx, by, bz;
+    bool valid;
+};
+
+__device__ __forceinline__ LutLine lut_line(const GridDev& g, const Event& e)
+{
+    LutLine l;
+    const float dx = __fsub_rn(e.p1.x, e.p2.x), dy = __fsub_rn(e.p1.y, e.p2.y), dz = __fsub_rn(e.p1.z, e.p2.z);
+    const float D = __fsqrt_rn(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))));
+    l.valid = D > 0.f;
+    const float inv = __frcp_rn(D);
+    const float ux = __fmul_rn(dx, inv), uy = __fmul_rn(dy, inv), uz = __fmul_rn(dz, inv);
+    const float mx = __fmul_rn(0.5f, __fadd_rn(e.p1.x, e.p2.x));
+    const float my = __fmul_rn(0.5f, __fadd_rn(e.p1.y, e.p2.y));
+    const float mz = __fmul_rn(0.5f, __fadd_rn(e.p1.z, e.p2.z));
+    const float ivx = __frcp_rn(g.vx), ivy = __frcp_rn(g.vy), ivz = __frcp_rn(g.vz);
+    l.ax = __fmul_rn(__fsub_rn(__fmaf_rn(e.d, ux, mx), g.ox), ivx);
+    l.ay = __fmul_rn(__fsub_rn(__fmaf_rn(e.d, uy, my), g.oy), ivy);
+    l.az = __fmul_rn(__fsub_rn(__fmaf_rn(e.d, uz, mz), g.oz), ivz);
+    l.bx = __fmul_rn(ux, ivx);
+    l.by = __fmul_rn(uy, ivy);
+    l.bz = __fmul_rn(uz, ivz);
+    return l;
+}
+
+// Visit (voxel, summed weight) of every run of consecutive samples that share
+// a voxel inside the grid.
+template <class Visit>
+__device__ __forceinline__ void lut_walk(const GridDev& g, const LutH& lut, const LutLine& l, Visit&& visit)
+{
+    if (!l.valid) return;
+    const float fnx = (float)g.nx, fny = (float)g.ny, fnz = (float)g.nz;
+    int prev = -1;
+    float acc = 0.f;
+    for (int k = 0; k < lut.n; ++k) {
+        const float2 s = lut.s[k];
+        const float fx = floorf(__fmaf_rn(s.x, l.bx, l.ax));
+        const float fy = floorf(__fmaf_rn(s.x, l.by, l.ay));
+        const float fz = floorf(__fmaf_rn(s.x, l.bz, l.az));
+        const bool in = fx >= 0.f && fx < fnx && fy >= 0.f && fy < fny && fz >= 0.f && fz < fnz;
+        const int j = in ? (int)fx + g.nx * ((int)fy + g.ny * (int)fz) : -1;
+        if (j != prev) {
+            if (prev >= 0) visit(prev, acc);
+            prev = j;
+            acc = 0.f;
+        }
+        acc += s.y;
+    }
+    if (prev >= 0) visit(prev, acc);
+}
+
+template <int Kind, int Fmt>
+__device__ __forceinline__ float do_event_lut(const PassArgs& a, const SharedTable& t, long long i, bool bf16,
+                                              int& region)
+{
+    region = find_region(t, i);
+    const GridDev& g = t.grid[region];
+    const Event e = load_event<Fmt>(a, i);
+    const LutLine l = lut_line(g, e);
+    float* const Cb = a.C + g.vox_offset;
+    if (Kind == PASS_BACK) {
+        const float r = a.r_in[i];
+        if (r != 0.f) lut_walk(g, a.lut, l, [&](int j, float w) { atomicAdd(Cb + j, w * r); });
+        return 0.f;
+    }
+    const float* const lb = a.lam + g.vox_offset;
+    const unsigned short* const hb = reinterpret_cast<const unsigned short*>(a.lam_bf16) + g.vox_offset;
+    float p = 0.f;
+    lut_walk(g, a.lut, l, [&](int j, float w) {
+        const float lam_j = bf16 ? __uint_as_float(((unsigned)__ldg(hb + j)) << 16) : __ldg(lb + j);
+        p = fmaf(w, lam_j, p);
+    });
+    if (Kind == PASS_FORWARD) {
+        a.p_out[i] = p;
+        return 0.f;
+    }
+    if (!(p > 0.f)) return 0.f;
+    const float r = e.w / p;
+    lut_walk(g, a.lut, l, [&](int j, float w) { atomicAdd(Cb + j, w * r); });
+    return e.w;
+}
+
+template <int Kind, int Fmt>
+__global__ void __launch_bounds__(256) k_lut_pass(PassArgs a, RegionTable tbl)
+{
+    __shared__ SharedTable t;
+    __shared__ float neff[kMaxRegions];
+    if (threadIdx.x == 0) t.n = tbl.n;
+    for (int k = threadIdx.x; k <= tbl.n; k += blockDim.x) t.ev_begin[k] = tbl.ev_begin[k];
+    for (int k = threadIdx.x; k < tbl.n; k += blockDim.x) {
+        t.grid[k] = tbl.grid[k];
+        neff[k] = 0.f;
+    }
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) {
+        int r;
+        const float w = do_event_lut<Kind, Fmt>(a, t, i, a.lam_bf16 != nullptr, r);
+        if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
+    }
+    if (Kind == PASS_FUSED) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < t.n; k += blockDim.x)
+            if (neff[k] != 0.f) atomicAdd(a.partial + (blockIdx.x % kNeffSlots) * t.n + k, (double)neff[k]);
+    }
+}
+
+template <int Kind, int Fmt>
+cudaError_t launch_lut(const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl, cudaStream_t s)
+{
+    if (a.lut.n < 1 || a.lut.n > kMaxLutSamples) return cudaErrorInvalidValue;
+    const long long blocks = (a.n + cfg.threads - 1) / cfg.threads;
+    if (blocks == 0) return cudaSuccess;
+    k_lut_pass<Kind, Fmt><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
+    return cudaGetLastError();
+}
+
 constexpr int kMaxCacheBytes = 200 * 1024;
 
 template <int Kind, int Fmt, bool Persistent, bool Cached, bool Fit>
@@ -193,6 +322,7 @@ template <int Kind, int Fmt>
 cudaError_t launch_kind(const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl, int num_sms,
                         cudaStream_t s)
 {
+    if (a.lut.n > 0) return launch_lut<Kind, Fmt>(cfg, a, tbl, s);
     const int blocks = pass_blocks(cfg, a.n, num_sms);
     if (blocks == 0) return cudaSuccess;
     if ((size_t)cfg.cache * cfg.threads * 8 > (size_t)kMaxCacheBytes) return cudaErrorInvalidValue;

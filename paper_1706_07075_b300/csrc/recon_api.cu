@@ -72,6 +72,7 @@ struct recon_ctx {
     recon_geometry geom{};
     recon_grid grid{};
     double fwhm_ps = 0, sigma_mm = 0, k_sigma = 3.0;
+    int lut_n = 0;   // samples of the sampled TOF kernel; 0: exact projector
     int device = 0, num_sms = 148;
     cudaStream_t own_stream = nullptr, stream = nullptr;
     std::string err;
@@ -151,6 +152,28 @@ TofH make_tof(const recon_ctx* c)
     t.inv_sigma_sqrt2 = (float)(1.0 / (c->sigma_mm * std::sqrt(2.0)));
     t.half_inv_norm = (float)(0.5 / std::erf(c->k_sigma / std::sqrt(2.0)));
     return t;
+}
+
+// Sampled TOF kernel (Sec. 2.3): offsets at the midpoints of lut_n equal
+// intervals of [-K sigma, K sigma], weights exp(-t^2 / (2 sigma^2)) scaled to
+// sum to one; offsets and weights computed in FP64, rounded once to FP32.
+LutH make_lut(const recon_ctx* c)
+{
+    LutH l;
+    memset(&l, 0, sizeof l);
+    l.n = c->lut_n;
+    if (l.n <= 0) return l;
+    const double half = c->k_sigma * c->sigma_mm;
+    const double step = 2.0 * half / l.n;
+    double t[kMaxLutSamples], w[kMaxLutSamples], total = 0.0;
+    for (int k = 0; k < l.n; ++k) {
+        t[k] = -half + (k + 0.5) * step;
+        const double z = t[k] / c->sigma_mm;
+        w[k] = std::exp(-0.5 * z * z);
+        total += w[k];
+    }
+    for (int k = 0; k < l.n; ++k) l.s[k] = make_float2((float)t[k], (float)(w[k] / total));
+    return l;
 }
 
 GridH grid_h(const recon_grid& g, int z_lo = 0, int z_hi = -1, long long vox_offset = 0)
@@ -330,6 +353,7 @@ PassArgs base_args(recon_ctx* ctx, const void* events, long long n)
     a.n = n;
     a.lattice = (float)ctx->lattice;
     a.tof = make_tof(ctx);
+    a.lut = make_lut(ctx);
     return a;
 }
 
@@ -411,6 +435,8 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
     std::string k(buf);
+    snprintf(buf, sizeof buf, " lut %d", p.a.lut.n);
+    k += buf;
     for (int r = 0; r < p.tbl.n; ++r) {
         snprintf(buf, sizeof buf, "|%lld %d %a %lld", p.tbl.ev_begin[r + 1], p.tbl.grid[r].nz,
                  (double)p.tbl.grid[r].oz, p.tbl.grid[r].vox_offset);
@@ -488,7 +514,7 @@ LaunchCfg choose_cfg(recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl, 
 {
     *st = RECON_OK;
     if (ctx->user_cfg) return ctx->cfg;
-    if (!ctx->autotune || a.n < (1LL << 20)) return default_cfg();
+    if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg();
     auto key = std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
@@ -687,6 +713,36 @@ recon_status recon_set_kernel_window(recon_ctx* ctx, double k_sigma)
     if (!(k_sigma >= 0.5 && k_sigma <= 8.0)) return fail(ctx, RECON_EINVAL, "k_sigma must be in [0.5, 8]");
     ctx->k_sigma = k_sigma;
     invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_samples)
+{
+    CHECK_CTX();
+    if (projector == RECON_PROJ_EXACT) {
+        ctx->lut_n = 0;
+    } else if (projector == RECON_PROJ_SAMPLED) {
+        if (n_samples < 1 || n_samples > RECON_MAX_TOF_SAMPLES)
+            return fail(ctx, RECON_EINVAL, "n_samples must be in [1, RECON_MAX_TOF_SAMPLES]");
+        ctx->lut_n = n_samples;
+    } else {
+        return fail(ctx, RECON_EINVAL, "unknown projector");
+    }
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float* offsets_mm, float* weights,
+                                   int32_t* n_out)
+{
+    if (!ctx || !n_out) return RECON_EINVAL;
+    const LutH l = make_lut(ctx);
+    *n_out = l.n;
+    if (l.n > capacity) return RECON_EINVAL;
+    for (int k = 0; k < l.n; ++k) {
+        if (offsets_mm) offsets_mm[k] = l.s[k].x;
+        if (weights) weights[k] = l.s[k].y;
+    }
     return RECON_OK;
 }
 

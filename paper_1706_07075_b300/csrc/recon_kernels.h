@@ -31,6 +31,17 @@ struct RegionTable {
     GridH grid[kMaxRegions];
 };
 
+// Sampled TOF kernel (Sec. 2.3): n offsets along the line from the TOF point
+// (mm) with unit-sum Gaussian weights, an array of (offset, weight) structs.
+// n = 0 selects the exact projector.  Passed by value, so the table sits in
+// the kernel's constant parameter bank, where a warp reading sample k
+// together gets it as one broadcast.
+constexpr int kMaxLutSamples = 64;
+struct LutH {
+    int n;
+    float2 s[kMaxLutSamples];  // (offset mm, weight)
+};
+
 enum EventFmt { FMT_F32 = 0, FMT_PACKED = 1 };
 enum PassKind { PASS_FUSED = 0, PASS_FORWARD = 1, PASS_BACK = 2 };
 enum TailEval { TAIL_FIT = 0, TAIL_ERFC = 1 };
@@ -56,6 +67,7 @@ struct PassArgs {
                                  // p_i > 0 (zero before the pass; the finalize reads and clears them)
     unsigned long long* work;    // work-queue counter (persistent launches; zero before the launch)
     TofH tof;
+    LutH lut;                    // sampled TOF kernel (lut.n > 0) instead of the exact one
 };
 
 // Number of blocks a pass launch uses.

@@ -28,6 +28,9 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   backproject_lut ..... pinned (brute-force sample positions on axis lines;
                         unit mass inside the grid; adjointness; convergence
                         to the exact Siddon x Phi projector as N grows)
+  median3 / sieve ..... pinned (scipy.ndimage.median_filter; closed forms on
+                        constant images at faces, edges and corners;
+                        impulse removal; ramps preserved)
 """
 from .core import (  # noqa: F401
     Grid,
@@ -46,4 +49,5 @@ from .core import (  # noqa: F401
     tof_weight,
     trace,
 )
+from .filters import median3, sieve  # noqa: F401
 from .mlem import mlem, mlem_regions, region_bounds, region_slabs, slab_grid, stitch  # noqa: F401

@@ -24,6 +24,7 @@ import math
 import numpy as np
 
 from .core import Grid, backproject, backproject_lut, forward, forward_lut, region_codes, region_members
+from .filters import sieve
 
 
 def uniform_start(sens, weights_total):
@@ -36,13 +37,16 @@ def uniform_start(sens, weights_total):
 
 
 def mlem(grid, events, sens, n_iter, sigma, K=3.0, weights=None, init=None, threads=None, return_p=False,
-         lut_samples=None):
+         lut_samples=None, median=False):
     """Run n_iter MLEM iterations.
 
     Returns (lambda, history) where history[k] = (N_eff, sum_j s_j lambda_j,
     log-likelihood at the image the iteration started from).  N_eff is the
     weight of the events with p_i > 0 in iteration k.  lut_samples=N swaps the
     exact projector for the sampled TOF kernel of Sec. 2.3 (N samples).
+    median=True applies the median-filter sieve of Sec. 2.4 (oracle.filters)
+    after each update; the history then holds sum_j s_j lambda_j of the
+    update, before the filter.
     """
     s = np.asarray(sens, np.float64).reshape(-1)
     assert s.size == grid.n_vox
@@ -69,6 +73,8 @@ def mlem(grid, events, sens, n_iter, sigma, K=3.0, weights=None, init=None, thre
         new[mask] = lam[mask] * Cimg[mask] / s[mask]
         lam = new
         history.append((float(w[valid].sum()), float(np.sum(s * lam)), loglik))
+        if median:
+            lam = sieve(lam, s, grid.shape_zyx)
     if return_p:
         return lam, history, p
     return lam, history
@@ -102,7 +108,7 @@ def stitch(grid, slabs, images):
 
 
 def mlem_regions(grid, events, sens, regions, shell_mm, margin_mm, n_iter, sigma, K=3.0, threads=None,
-                 lut_samples=None):
+                 lut_samples=None, median=False):
     """Divide events by TOF-estimated z, reconstruct each slab, sum the slabs.
 
     Returns (image, per-region images, per-region histories, codes, offsets, idx).
@@ -120,7 +126,7 @@ def mlem_regions(grid, events, sens, regions, shell_mm, margin_mm, n_iter, sigma
         ev_r = [e[members] for e in events]
         g_r = slab_grid(grid, lo, hi)
         lam_r, h_r = mlem(g_r, ev_r, s3[lo:hi].reshape(-1), n_iter, sigma, K, weights=w_all[members],
-                          threads=threads, lut_samples=lut_samples)
+                          threads=threads, lut_samples=lut_samples, median=median)
         images.append(lam_r)
         hists.append(h_r)
     return stitch(grid, slabs, images), images, hists, codes, offsets, idx

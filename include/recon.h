@@ -173,6 +173,20 @@ recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_sa
 recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float* offsets_mm, float* weights,
                                    int32_t* n_out);
 
+/* Median-filter sieve between iterations (Sec. 2.4; Sec. 4 on its effect at the
+ * borders of divided images).  on = 1: after every iteration's update of recon_mlem
+ * and recon_mlem_regions, lambda is replaced by its 3 x 3 x 3 median (the 14th
+ * smallest of the 27 values, neighbours outside the grid or the region's slab
+ * counting as 0) and voxels with s_j = 0 are set to 0.  The conservation history
+ * keeps N_eff and sum_j s_j lambda_j of the update, before the filter (the filter does
+ * not conserve counts).  Off by default. */
+recon_status recon_set_median_filter(recon_ctx* ctx, int32_t on);
+
+/* One 3 x 3 x 3 median filter of image_in into image_out over the context's grid,
+ * zero outside the grid, no mask (nx*ny*nz floats each, host or device; they may
+ * alias).  Values must not be NaN.  Errors: EINVAL (NULL pointer), ENOMEM, ECUDA. */
+recon_status recon_median_filter(recon_ctx* ctx, const float* image_in, float* image_out);
+
 /* Forward gather from a BF16 copy of the image (1) or the FP32 image (0, default).
  * Backprojection always accumulates in FP32. */
 recon_status recon_set_gather_bf16(recon_ctx* ctx, int32_t on);

@@ -49,5 +49,5 @@ from .core import (  # noqa: F401
     tof_weight,
     trace,
 )
-from .filters import median3, sieve  # noqa: F401
+from .filters import median3, median3_at, sieve  # noqa: F401
 from .mlem import mlem, mlem_regions, region_bounds, region_slabs, slab_grid, stitch  # noqa: F401

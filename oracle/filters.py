@@ -37,3 +37,22 @@ def sieve(lam, sens, shape_zyx):
     out = median3(lam, shape_zyx)
     out[np.asarray(sens).reshape(-1) <= 0] = 0.0
     return out
+
+
+def median3_at(img, shape_zyx, vox):
+    """median3 at the flat voxel indices vox only (for grids too large for median3)."""
+    a = np.asarray(img, np.float64).reshape(shape_zyx)
+    nz, ny, nx = shape_zyx
+    vox = np.asarray(vox, np.int64)
+    z, rem = np.divmod(vox, nx * ny)
+    y, x = np.divmod(rem, nx)
+    vals = np.zeros((27, vox.size))
+    k = 0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                zz, yy, xx = z + dz, y + dy, x + dx
+                inside = (zz >= 0) & (zz < nz) & (yy >= 0) & (yy < ny) & (xx >= 0) & (xx < nx)
+                vals[k, inside] = a[zz[inside], yy[inside], xx[inside]]
+                k += 1
+    return np.median(vals, axis=0)

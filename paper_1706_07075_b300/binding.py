@@ -73,6 +73,8 @@ SIGNATURES = {
     "recon_set_kernel_window": (C.c_int, [_CTX, C.c_double]),
     "recon_set_gather_bf16": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_projector": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
+    "recon_set_median_filter": (C.c_int, [_CTX, C.c_int32]),
+    "recon_median_filter": (C.c_int, [_CTX, _VP, _VP]),
     "recon_get_tof_samples": (C.c_int, [_CTX, C.c_int32, _VP, _VP, C.POINTER(C.c_int32)]),
     "recon_set_launch": (C.c_int, [_CTX, C.POINTER(recon_launch)]),
     "recon_get_launch": (C.c_int, [_CTX, C.POINTER(recon_launch)]),
@@ -228,6 +230,14 @@ MAX_TOF_SAMPLES = 64
 
 def recon_set_projector(ctx, projector, n_samples=0):
     return check(ctx, load().recon_set_projector(ctx, int(projector), int(n_samples)))
+
+
+def recon_set_median_filter(ctx, on):
+    return check(ctx, load().recon_set_median_filter(ctx, int(bool(on))))
+
+
+def recon_median_filter(ctx, image_in, image_out):
+    return check(ctx, load().recon_median_filter(ctx, ptr(image_in), ptr(image_out)))
 
 
 def recon_get_tof_samples(ctx):

@@ -73,6 +73,7 @@ struct recon_ctx {
     recon_grid grid{};
     double fwhm_ps = 0, sigma_mm = 0, k_sigma = 3.0;
     int lut_n = 0;   // samples of the sampled TOF kernel; 0: exact projector
+    bool median = false;  // median-filter sieve after every iteration
     int device = 0, num_sms = 148;
     cudaStream_t own_stream = nullptr, stream = nullptr;
     std::string err;
@@ -93,7 +94,7 @@ struct recon_ctx {
     long long ev_generation = 0;
 
     // per-call scratch
-    DevBuf pass_partial, upd_partial, work, iter, hist, reg_vox, red_partial, vec;
+    DevBuf pass_partial, upd_partial, work, iter, hist, reg_vox, red_partial, vec, med;
 
     // options
     bool bf16 = false, timing = false, graphs = true, autotune = true;
@@ -413,7 +414,20 @@ struct IterPlan {
     double* hist;
     int* iter;
     int hist_cap;
+    float* med;      // median-filter output (nullptr: no sieve); copied back into lam
+    long long med_vox;
+    int max_nz;
 };
+
+// Sieve (Sec. 2.4): lam -> median -> lam, after the update.
+recon_status enqueue_sieve(recon_ctx* ctx, const IterPlan& p)
+{
+    if (!p.med) return RECON_OK;
+    CK(launch_median3(p.lam, p.med, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->grid.nx, ctx->grid.ny, p.max_nz,
+                      ctx->stream));
+    CK(cudaMemcpyAsync(p.lam, p.med, sizeof(float) * (size_t)p.med_vox, cudaMemcpyDeviceToDevice, ctx->stream));
+    return RECON_OK;
+}
 
 recon_status enqueue_iteration(recon_ctx* ctx, const IterPlan& p)
 {
@@ -421,6 +435,8 @@ recon_status enqueue_iteration(recon_ctx* ctx, const IterPlan& p)
     CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, p.a, p.tbl, ctx->num_sms, ctx->stream));
     CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(), p.upd_bpr,
                      ctx->stream));
+    recon_status sv = enqueue_sieve(ctx, p);
+    if (sv != RECON_OK) return sv;
     CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions, p.hist,
                        p.iter, p.hist_cap, ctx->stream));
     return RECON_OK;
@@ -435,7 +451,7 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
     std::string k(buf);
-    snprintf(buf, sizeof buf, " lut %d", p.a.lut.n);
+    snprintf(buf, sizeof buf, " lut %d med %p %lld %d", p.a.lut.n, (void*)p.med, p.med_vox, p.max_nz);
     k += buf;
     for (int r = 0; r < p.tbl.n; ++r) {
         snprintf(buf, sizeof buf, "|%lld %d %a %lld", p.tbl.ev_begin[r + 1], p.tbl.grid[r].nz,
@@ -464,10 +480,12 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter)
             if (ctx->timing) CK(cudaEventRecord(evs[3 * k + 1], ctx->stream));
             CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(),
                              p.upd_bpr, ctx->stream));
+            recon_status sv = enqueue_sieve(ctx, p);
+            if (sv != RECON_OK) return sv;
             if (ctx->timing) CK(cudaEventRecord(evs[3 * k + 2], ctx->stream));
             CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions,
                                p.hist, p.iter, p.hist_cap, ctx->stream));
-            ctx->stats.kernel_launches += p.pass_blocks > 0 ? 3 : 2;
+            ctx->stats.kernel_launches += (p.pass_blocks > 0 ? 3 : 2) + (p.med ? 1 : 0);
         }
         if (ctx->timing) {
             CK(cudaStreamSynchronize(ctx->stream));
@@ -505,7 +523,7 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter)
     }
     for (int k = 0; k < n_iter; ++k) {
         CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-        ctx->stats.kernel_launches += p.pass_blocks > 0 ? 3 : 2;
+        ctx->stats.kernel_launches += (p.pass_blocks > 0 ? 3 : 2) + (p.med ? 1 : 0);
     }
     return RECON_OK;
 }
@@ -676,7 +694,7 @@ void recon_destroy(recon_ctx* ctx)
     invalidate_graph(ctx);
     DevBuf* bufs[] = {&ctx->s64, &ctx->s32, &ctx->lam, &ctx->C, &ctx->lam_bf16, &ctx->ev, &ctx->staging,
                       &ctx->pass_partial, &ctx->upd_partial, &ctx->work, &ctx->iter, &ctx->hist, &ctx->reg_vox,
-                      &ctx->red_partial, &ctx->vec, &ctx->codes, &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
+                      &ctx->red_partial, &ctx->vec, &ctx->med, &ctx->codes, &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
                       &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg};
     for (DevBuf* b : bufs) release(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
@@ -729,6 +747,34 @@ recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_sa
         return fail(ctx, RECON_EINVAL, "unknown projector");
     }
     invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_set_median_filter(recon_ctx* ctx, int32_t on)
+{
+    CHECK_CTX();
+    ctx->median = on != 0;
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_median_filter(recon_ctx* ctx, const float* image_in, float* image_out)
+{
+    CHECK_CTX();
+    if (!image_in || !image_out) return fail(ctx, RECON_EINVAL, "image_in and image_out are required");
+    const size_t bytes = sizeof(float) * (size_t)ctx->n_vox;
+    // staged through context scratch (vec: input, med: output), so in and out may alias
+    CK(ensure(ctx->med, bytes));
+    CK(ensure(ctx->vec, bytes));
+    CK(cudaMemcpyAsync(ctx->vec.p, image_in, bytes, cudaMemcpyDefault, ctx->stream));
+    const long long rv[2] = {0, ctx->n_vox};
+    CK(ensure(ctx->reg_vox, sizeof rv));
+    CK(cudaMemcpyAsync(ctx->reg_vox.p, rv, sizeof rv, cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_median3(ctx->vec.as<float>(), ctx->med.as<float>(), nullptr, nullptr, ctx->reg_vox.as<long long>(), 1,
+                      ctx->grid.nx, ctx->grid.ny, ctx->grid.nz, ctx->stream));
+    CK(cudaMemcpyAsync(image_out, ctx->med.p, bytes, cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->stats.kernel_launches += 1;
     return RECON_OK;
 }
 
@@ -997,6 +1043,13 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     p.bf16 = ctx->bf16 ? ctx->lam_bf16.as<uint16_t>() : nullptr;
     p.reg_vox_dev = ctx->reg_vox.as<long long>();
     p.n_regions = 1;
+    p.med = nullptr;
+    p.med_vox = nv;
+    p.max_nz = ctx->grid.nz;
+    if (ctx->median) {
+        CK(ensure(ctx->med, sizeof(float) * (size_t)nv));
+        p.med = ctx->med.as<float>();
+    }
     ctx->last_cfg = p.cfg;
     recon_status s = run_iterations(ctx, p, n_iter);
     if (s != RECON_OK) return s;
@@ -1180,6 +1233,14 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
     p.bf16 = ctx->bf16 ? ctx->bf16_reg.as<uint16_t>() : nullptr;
     p.reg_vox_dev = ctx->reg_vox_reg.as<long long>();
     p.n_regions = R;
+    p.med = nullptr;
+    p.med_vox = nvt;
+    p.max_nz = 0;
+    for (int r = 0; r < R; ++r) p.max_nz = std::max(p.max_nz, hi[r] - lo[r]);
+    if (ctx->median) {
+        CK(ensure(ctx->med, sizeof(float) * (size_t)nvt));
+        p.med = ctx->med.as<float>();
+    }
     ctx->last_cfg = p.cfg;
     s = run_iterations(ctx, p, n_iter);
     if (s != RECON_OK) return s;

@@ -94,6 +94,12 @@ cudaError_t launch_finalize(double* pass_partial, int pass_slots, const double* 
                             int upd_blocks_per_region, int n_regions, double* hist, int* iter_counter,
                             int max_iter, cudaStream_t st);
 cudaError_t launch_to_bf16(const float* src, uint16_t* dst, long long n, cudaStream_t st);
+// 3x3x3 median (zero outside each region's slab) of in into out per region
+// (reg_vox: device array of n_regions + 1 voxel offsets; slabs nx x ny x nz_r,
+// max_nz >= every nz_r); s32 (nullable): zero where s <= 0; bf16 (nullable):
+// BF16 copy of out.  in and out must not overlap.
+cudaError_t launch_median3(const float* in, float* out, const float* s32, uint16_t* bf16, const long long* reg_vox,
+                           int n_regions, int nx, int ny, int max_nz, cudaStream_t st);
 // Caller SoA planes (device) -> resident float4 pairs; weight nullable.
 cudaError_t launch_ingest_f32(const float* const* planes, const float* weight, long long n, float4* out,
                               cudaStream_t st);

@@ -67,3 +67,12 @@ def test_mlem_with_sieve_runs_filter_after_each_update():
     lam2, h2 = oracle.mlem(g, ev, s, 1, sigma, median=True)
     assert np.array_equal(lam2, oracle.sieve(lam1, s, g.shape_zyx))
     assert h1 == h2
+
+
+def test_median3_at_equals_median3():
+    shape = (6, 5, 7)
+    rng = np.random.default_rng(12)
+    img = rng.uniform(0, 1, shape).ravel()
+    full = oracle.median3(img, shape)
+    vox = rng.choice(img.size, 60, replace=False)
+    assert np.array_equal(oracle.median3_at(img, shape, vox), full[vox])

@@ -570,6 +570,11 @@ def run_ours(args):
                           "hbm_peak_source": src,
                           "red_frac": red_rate / 1e9 / probes["l2_red_gops"],
                           "gather_frac": red_rate / 1e9 / probes["gather_gops"]}}
+        if args.samples:
+            # the roofline above counts Siddon pieces: it describes the exact projector only
+            out["roofline"] = {"bound": "l2_random_access", "achieved": None, "peak": peak, "unit": "Gpiece/s",
+                               "frac": None, "traffic": None,
+                               "note": "sampled projector timed; see profiles/k_lut_pass_fullbody_8M.md"}
         if not args.no_cpu_baseline:
             lsub = lors[:, :200_000]
             out["cpu_baseline"] = cpu_baseline(ev, lsub, args.iters, args.cpu_sample)

@@ -231,6 +231,29 @@ recon_status recon_set_sensitivity(recon_ctx* ctx, const double* sens, int32_t o
  * ENOMEM. */
 recon_status recon_load_events(recon_ctx* ctx, const recon_events* events);
 
+/* Event pre-processing (Sec. 2.2, 2.4), one pass over the events on the GPU.
+ *
+ * Attenuation correction (Sec. 2.4): w_i = exp(sum_j mu_j L_ij), the integral of the
+ *   attenuation map along the event's whole LOR inside the grid (L_ij: Siddon chord
+ *   of the LOR in voxel j), i.e. inversely proportional to the probability that the
+ *   photon pair escapes attenuation.
+ * TOF scatter rejection (Sec. 2.2, Fig. 2): with z_reject > 0 an event is kept iff
+ *   the stretch of its LOR within z_reject * sigma of the TOF point meets a body voxel
+ *   (mu_j > 0) over a positive length; z_reject = 1.96 is the paper's 95% confidence.
+ *   Rejected events get w_i = 0.  z_reject = 0 keeps every event.
+ *
+ * events: NULL = the resident events, else loaded first (and kept resident).
+ * mu_map: nx*ny*nz floats (1/mm, >= 0, host or device).
+ * apply = 1: multiply the resident events' weights by w_i in place (rejected events
+ *   then weigh 0; the packed format stores the product in FP16, relative rounding
+ *   ~5e-4), so later recon_mlem / recon_mlem_regions calls with events = NULL use
+ *   them; apply = 0 leaves the events unchanged.
+ * weight_out (n floats), keep_out (n bytes, 1 = kept), n_kept: nullable outputs, host
+ * or device.  Errors: EINVAL (NULL mu_map, z_reject outside [0, 10]), ESTATE (no
+ * events), ENOMEM, ECUDA. */
+recon_status recon_preprocess(recon_ctx* ctx, const recon_events* events, const float* mu_map, double z_reject,
+                              int32_t apply, float* weight_out, uint8_t* keep_out, int64_t* n_kept);
+
 /* ---------------------------------------------------------------- projector */
 
 /* Forward projection p_i = sum_j a_ij lambda_j (Sec. 2.3/2.4) with

@@ -28,6 +28,9 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   backproject_lut ..... pinned (brute-force sample positions on axis lines;
                         unit mass inside the grid; adjointness; convergence
                         to the exact Siddon x Phi projector as N grows)
+  preprocess .......... pinned (closed-form line integrals through uniform
+                        boxes and a sphere; rejection decided by hand-built
+                        events inside, outside and at the 1.96 sigma edge)
   median3 / sieve ..... pinned (scipy.ndimage.median_filter; closed forms on
                         constant images at faces, edges and corners;
                         impulse removal; ramps preserved)
@@ -40,6 +43,7 @@ from .core import (  # noqa: F401
     forward,
     forward_lut,
     lut_samples,
+    preprocess,
     region_codes,
     region_members,
     sensitivity,

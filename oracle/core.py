@@ -85,6 +85,9 @@ def _load():
             lib.oracle_region_codes.argtypes = [planes, C.c_int64, C.c_int64, C.c_int32, dp, C.c_double,
                                                 C.POINTER(C.c_uint8), dp]
             lib.oracle_region_codes.restype = C.c_int64
+            lib.oracle_preprocess.argtypes = [gp, planes, C.c_int64, C.c_int64, dp, C.c_double, C.c_double, dp,
+                                              C.POINTER(C.c_uint8)]
+            lib.oracle_preprocess.restype = C.c_int64
             fp = C.POINTER(C.c_float)
             lib.oracle_lut_samples.argtypes = [C.c_int32, C.c_double, C.c_double, dp, dp]
             lib.oracle_lut_samples.restype = None
@@ -273,6 +276,37 @@ def sensitivity(grid, lors, threads=None):
     for acc in accs:
         total += acc
     return total
+
+
+# ------------------------------------------------------- pre-processing
+
+def preprocess(grid, events, mu, sigma, z=1.96, threads=None):
+    """Attenuation weights and TOF scatter rejection (Sec. 2.4, Sec. 2.2).
+
+    Returns (w, keep, kept): w_i = exp(sum_j mu_j L_ij) for kept events and 0
+    for rejected ones; keep_i = 1 iff [d - z sigma, d + z sigma] meets a voxel
+    with mu > 0 (z <= 0: keep all).
+    """
+    lib = _load()
+    keep_planes, ptrs = _event_planes(events)
+    n = keep_planes[0].shape[0]
+    mu = np.ascontiguousarray(mu, np.float64).reshape(-1)
+    assert mu.size == grid.n_vox
+    w = np.zeros(n)
+    keep = np.zeros(n, np.uint8)
+    if n == 0:
+        return w, keep, 0
+    g = grid.c()
+
+    def part(i0, i1):
+        r = lib.oracle_preprocess(C.byref(g), ptrs, i0, i1, _dptr(mu), float(sigma), float(z), _dptr(w),
+                                  keep.ctypes.data_as(C.POINTER(C.c_uint8)))
+        if r < 0:
+            raise MemoryError("oracle_preprocess buffer error")
+        return r
+
+    kept = int(sum(_run_threads(part, _ranges(n, threads or threads_used(n)))))
+    return w, keep, kept
 
 
 # --------------------------------------------------- sampled TOF kernel

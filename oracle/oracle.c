@@ -37,6 +37,10 @@
  *   Sec. 2.4 (Shepp & Vardi 1982 in list-mode form).  The update itself and the
  *   iteration loop live in oracle/mlem.py.
  *
+ *   Pre-processing (Sec. 2.2, 2.4): attenuation weights exp(sum mu L) along
+ *   each LOR and TOF scatter rejection against the body (mu > 0) at 95%
+ *   confidence; see oracle_preprocess.
+ *
  *   TOF-assisted division into body regions (Sec. 2.5, Fig. 4): the
  *   TOF-estimated annihilation z of each event decides the region(s) it feeds;
  *   each region also takes the events from a 6 mm outer shell on both axial
@@ -326,6 +330,58 @@ int oracle_sensitivity(const og_grid *g, const double *const lor[6], int64_t l0,
     }
     row_buf_free(&rb);
     return rc;
+}
+
+/* ------------------------- pre-processing: attenuation and TOF rejection */
+
+/*
+ * Attenuation correction (Sec. 2.4): each event carries a weight inversely
+ * proportional to the probability that its photon pair escapes the body,
+ *     w_i = exp( integral of mu along the LOR ) = exp( sum_j mu_j L_ij ),
+ * with L_ij the chord of the LOR in voxel j (mu in 1/mm, the mu-map on the
+ * image grid).  Reading: "the probability of being attenuated" is read as the
+ * survival probability exp(-integral mu), the usual attenuation correction
+ * factor; the weight multiplies the event's count in the update.
+ *
+ * TOF scatter rejection (Sec. 2.2, Fig. 2): an event is rejected when its
+ * TOF point lies outside the body at 95% confidence.  Reading: the body is
+ * the set of voxels with mu_j > 0; the event is kept iff the interval
+ * [d - z sigma, d + z sigma] of the line (z = 1.96 for 95%, two-sided) meets a
+ * body voxel over a piece of positive length.  z <= 0 keeps every event.
+ *
+ * Per event i in [i0, i1): w_out[i] = exp(sum mu L) if kept, else 0;
+ * keep_out[i] = 1 or 0.  Returns the number of kept events, or -1 on a
+ * buffer error.
+ */
+int64_t oracle_preprocess(const og_grid *g, const double *const ev[7], int64_t i0, int64_t i1, const double *mu,
+                          double sigma, double z, double *w_out, uint8_t *keep_out)
+{
+    row_buf rb;
+    if (!row_buf_init(&rb, g)) { row_buf_free(&rb); return -1; }
+    int64_t kept = 0;
+    for (int64_t i = i0; i < i1; ++i) {
+        double p1[3], p2[3], d;
+        event_at(ev, i, p1, p2, &d);
+        int64_t n = trace_line(g, p1, p2, -INFINITY, INFINITY, rb.cap, rb.vox, rb.ta, rb.tb, rb.scratch);
+        if (n < 0) { row_buf_free(&rb); return -1; }
+        double line_mu = 0.0;
+        for (int64_t m = 0; m < n; ++m) line_mu += mu[rb.vox[m]] * (rb.tb[m] - rb.ta[m]);
+        int keep = 1;
+        if (z > 0.0) {
+            keep = 0;
+            const double lo = d - z * sigma, hi = d + z * sigma;
+            for (int64_t m = 0; m < n && !keep; ++m) {
+                const double a = rb.ta[m] > lo ? rb.ta[m] : lo;
+                const double b = rb.tb[m] < hi ? rb.tb[m] : hi;
+                if (mu[rb.vox[m]] > 0.0 && b > a) keep = 1;
+            }
+        }
+        w_out[i] = keep ? exp(line_mu) : 0.0;
+        keep_out[i] = (uint8_t)keep;
+        kept += keep;
+    }
+    row_buf_free(&rb);
+    return kept;
 }
 
 /* --------------------------------------- sampled TOF kernel (Sec. 2.3) */

@@ -74,6 +74,8 @@ SIGNATURES = {
     "recon_set_gather_bf16": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_projector": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "recon_set_median_filter": (C.c_int, [_CTX, C.c_int32]),
+    "recon_preprocess": (C.c_int, [_CTX, C.POINTER(recon_events), _VP, C.c_double, C.c_int32, _VP, _VP,
+                                   C.POINTER(C.c_int64)]),
     "recon_median_filter": (C.c_int, [_CTX, _VP, _VP]),
     "recon_get_tof_samples": (C.c_int, [_CTX, C.c_int32, _VP, _VP, C.POINTER(C.c_int32)]),
     "recon_set_launch": (C.c_int, [_CTX, C.POINTER(recon_launch)]),
@@ -238,6 +240,14 @@ def recon_set_median_filter(ctx, on):
 
 def recon_median_filter(ctx, image_in, image_out):
     return check(ctx, load().recon_median_filter(ctx, ptr(image_in), ptr(image_out)))
+
+
+def recon_preprocess(ctx, events, mu_map, z_reject=1.96, apply=0, weight_out=None, keep_out=None):
+    """Attenuation weights and TOF scatter rejection; returns the number of kept events."""
+    kept = C.c_int64(0)
+    check(ctx, load().recon_preprocess(ctx, C.byref(events) if events is not None else None, ptr(mu_map),
+                                       float(z_reject), int(apply), ptr(weight_out), ptr(keep_out), C.byref(kept)))
+    return kept.value
 
 
 def recon_get_tof_samples(ctx):

@@ -94,7 +94,7 @@ struct recon_ctx {
     long long ev_generation = 0;
 
     // per-call scratch
-    DevBuf pass_partial, upd_partial, work, iter, hist, reg_vox, red_partial, vec, med;
+    DevBuf pass_partial, upd_partial, work, iter, hist, reg_vox, red_partial, vec, med, mu, keep, counter;
 
     // options
     bool bf16 = false, timing = false, graphs = true, autotune = true;
@@ -234,6 +234,28 @@ recon_status validate_events(recon_ctx* ctx, const recon_events* e)
     return RECON_OK;
 }
 
+// After the resident events (or their weights) change: new generation (drops
+// graphs and cached region copies) and the weight total sum_i w_i.
+recon_status events_changed(recon_ctx* ctx)
+{
+    ctx->ev_generation++;
+    invalidate_graph(ctx);
+    ctx->w_total = 0;
+    const long long n = ctx->n_ev;
+    if (n > 0) {
+        const bool packed = ctx->fmt == FMT_PACKED;
+        const int b = reduce_blocks(n);
+        CK(ensure(ctx->red_partial, sizeof(double) * 1024));
+        CK(launch_reduce_weights(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr, n,
+                                 ctx->red_partial.as<double>(), b, ctx->stream));
+        ctx->stats.kernel_launches += 1;
+        recon_status s = host_sum(ctx, ctx->red_partial.as<double>(), b, &ctx->w_total);
+        if (s != RECON_OK) return s;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
 // Copy events into the resident layout (chunked through a staging buffer when
 // they live on the host).
 recon_status load_events(recon_ctx* ctx, const recon_events* e)
@@ -289,20 +311,7 @@ recon_status load_events(recon_ctx* ctx, const recon_events* e)
     ctx->lattice = packed ? e->lattice_mm : 0.0;
     ctx->n_ev = n;
     ctx->have_ev = true;
-    ctx->ev_generation++;
-    invalidate_graph(ctx);
-    ctx->w_total = 0;
-    if (n > 0) {
-        const int b = reduce_blocks(n);
-        CK(ensure(ctx->red_partial, sizeof(double) * 1024));
-        CK(launch_reduce_weights(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr, n,
-                                 ctx->red_partial.as<double>(), b, ctx->stream));
-        ctx->stats.kernel_launches += 1;
-        s = host_sum(ctx, ctx->red_partial.as<double>(), b, &ctx->w_total);
-        if (s != RECON_OK) return s;
-    }
-    CK(cudaStreamSynchronize(ctx->stream));
-    return RECON_OK;
+    return events_changed(ctx);
 }
 
 recon_status finish_sensitivity(recon_ctx* ctx)
@@ -694,7 +703,7 @@ void recon_destroy(recon_ctx* ctx)
     invalidate_graph(ctx);
     DevBuf* bufs[] = {&ctx->s64, &ctx->s32, &ctx->lam, &ctx->C, &ctx->lam_bf16, &ctx->ev, &ctx->staging,
                       &ctx->pass_partial, &ctx->upd_partial, &ctx->work, &ctx->iter, &ctx->hist, &ctx->reg_vox,
-                      &ctx->red_partial, &ctx->vec, &ctx->med, &ctx->codes, &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
+                      &ctx->red_partial, &ctx->vec, &ctx->med, &ctx->mu, &ctx->keep, &ctx->counter, &ctx->codes, &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
                       &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg};
     for (DevBuf* b : bufs) release(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
@@ -922,6 +931,41 @@ recon_status recon_load_events(recon_ctx* ctx, const recon_events* events)
 {
     CHECK_CTX();
     return load_events(ctx, events);
+}
+
+recon_status recon_preprocess(recon_ctx* ctx, const recon_events* events, const float* mu_map, double z_reject,
+                              int32_t apply, float* weight_out, uint8_t* keep_out, int64_t* n_kept)
+{
+    CHECK_CTX();
+    if (!mu_map) return fail(ctx, RECON_EINVAL, "mu_map is NULL");
+    if (!(z_reject >= 0.0) || !(z_reject <= 10.0)) return fail(ctx, RECON_EINVAL, "z_reject must be in [0, 10]");
+    if (events) {
+        recon_status s = load_events(ctx, events);
+        if (s != RECON_OK) return s;
+    }
+    if (!ctx->have_ev) return fail(ctx, RECON_ESTATE, "no events loaded");
+    const long long n = ctx->n_ev;
+    CK(ensure(ctx->mu, sizeof(float) * (size_t)ctx->n_vox));
+    CK(cudaMemcpyAsync(ctx->mu.p, mu_map, sizeof(float) * (size_t)ctx->n_vox, cudaMemcpyDefault, ctx->stream));
+    CK(ensure(ctx->counter, sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(unsigned long long), ctx->stream));
+    if (weight_out && n > 0) CK(ensure(ctx->vec, sizeof(float) * (size_t)n));
+    if (keep_out && n > 0) CK(ensure(ctx->keep, (size_t)n));
+    const float half = (float)(z_reject * ctx->sigma_mm);
+    CK(launch_preprocess(ctx->ev.p, ctx->fmt, n, (float)ctx->lattice, grid_h(ctx->grid), ctx->mu.as<float>(), half,
+                         apply ? 1 : 0, weight_out ? ctx->vec.as<float>() : nullptr,
+                         keep_out ? ctx->keep.as<uint8_t>() : nullptr, ctx->counter.as<unsigned long long>(),
+                         ctx->stream));
+    ctx->stats.kernel_launches += n > 0 ? 1 : 0;
+    if (weight_out && n > 0)
+        CK(cudaMemcpyAsync(weight_out, ctx->vec.p, sizeof(float) * (size_t)n, cudaMemcpyDefault, ctx->stream));
+    if (keep_out && n > 0) CK(cudaMemcpyAsync(keep_out, ctx->keep.p, (size_t)n, cudaMemcpyDefault, ctx->stream));
+    unsigned long long kept = 0;
+    CK(cudaMemcpyAsync(&kept, ctx->counter.p, sizeof kept, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (n_kept) *n_kept = (int64_t)kept;
+    if (apply) return events_changed(ctx);
+    return RECON_OK;
 }
 
 recon_status recon_forward(recon_ctx* ctx, const recon_events* events, const float* image, float* p_out)

@@ -93,6 +93,12 @@ cudaError_t launch_update(float* lam, float* C, const float* s32, uint16_t* lam_
 cudaError_t launch_finalize(double* pass_partial, int pass_slots, const double* upd_partial,
                             int upd_blocks_per_region, int n_regions, double* hist, int* iter_counter,
                             int max_iter, cudaStream_t st);
+// Attenuation weights and TOF scatter rejection per resident event (events:
+// F32 float4 pairs or packed int4 records, written when apply != 0); w_out and
+// keep_out nullable; *kept += number of kept events.
+cudaError_t launch_preprocess(void* events, int fmt, long long n, float lattice, const GridH& g, const float* mu,
+                              float half_window, int apply, float* w_out, uint8_t* keep_out,
+                              unsigned long long* kept, cudaStream_t st);
 cudaError_t launch_to_bf16(const float* src, uint16_t* dst, long long n, cudaStream_t st);
 // 3x3x3 median (zero outside each region's slab) of in into out per region
 // (reg_vox: device array of n_regions + 1 voxel offsets; slabs nx x ny x nz_r,

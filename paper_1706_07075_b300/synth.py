@@ -41,6 +41,8 @@ import numpy as np
 C_MM_PER_PS = 0.299792458
 FWHM_PER_SIGMA = 2.0 * math.sqrt(2.0 * math.log(2.0))
 CHUNK = 1 << 20
+MU_WATER = 0.0096   # 1/mm at 511 keV: soft tissue
+MU_LUNG = 0.0029    # 1/mm: lung (density ~0.3)
 
 
 @dataclass(frozen=True)
@@ -50,6 +52,7 @@ class Shape:
     axes: tuple        # ellipsoid semi-axes; zcylinder (radius, radius, half length)
     activity: float
     body: bool = False  # part of the body outline (used for the scatter path)
+    mu: float = -1.0    # attenuation coefficient (1/mm) inside the shape; < 0: that of the enclosing body
 
     def volume(self):
         a, b, c = self.axes
@@ -104,8 +107,8 @@ def fullbody_workload():
         e((0, 0, 650), (80, 95, 110), 1.0, True),       # head
         e((90, 0, -600), (75, 75, 430), 1.0, True),     # left leg
         e((-90, 0, -600), (75, 75, 430), 1.0, True),    # right leg
-        e((85, 0, 300), (60, 70, 120), 0.3),            # lungs
-        e((-85, 0, 300), (60, 70, 120), 0.3),
+        Shape("ellipsoid", (85, 0, 300), (60, 70, 120), 0.3, False, MU_LUNG),    # lungs
+        Shape("ellipsoid", (-85, 0, 300), (60, 70, 120), 0.3, False, MU_LUNG),
         e((-70, 0, 140), (90, 70, 70), 2.0),            # liver
         e((30, -20, 260), (50, 45, 55), 3.0),           # heart
         e((0, -30, -140), (35, 30, 30), 8.0),           # bladder
@@ -455,3 +458,26 @@ def phantom_image(wname, grid=None, oversample=2):
                     act[s.contains(p)] = s.activity
                 img += act.reshape(nz, ny, nx)
     return img / oversample ** 3
+
+
+def mu_image(wname, grid=None):
+    """Attenuation map (1/mm) at the voxel centres, flat x-fastest: MU_WATER inside
+    the body outline, a shape's own mu where it sets one, 0 outside the body."""
+    w = WORKLOADS[wname]()
+    nx, ny, nz, v, _, _, ox, oy, oz = grid if grid is not None else grid_of(w)
+    out = np.zeros(nz * ny * nx, np.float32)
+    xs = ox + (np.arange(nx) + 0.5) * v
+    ys = oy + (np.arange(ny) + 0.5) * v
+    for z0 in range(0, nz, 16):
+        z1 = min(nz, z0 + 16)
+        zz, yy, xx = np.meshgrid(oz + (np.arange(z0, z1) + 0.5) * v, ys, xs, indexing="ij")
+        p = np.stack([xx.ravel(), yy.ravel(), zz.ravel()])
+        m = np.zeros(p.shape[1], np.float32)
+        for s in w.shapes:
+            if s.body:
+                m[s.contains(p)] = MU_WATER
+        for s in w.shapes:
+            if s.mu >= 0:
+                m[s.contains(p)] = s.mu
+        out[z0 * ny * nx:z1 * ny * nx] = m
+    return out

@@ -31,6 +31,9 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   preprocess .......... pinned (closed-form line integrals through uniform
                         boxes and a sphere; rejection decided by hand-built
                         events inside, outside and at the 1.96 sigma edge)
+  osem ................ pinned (dense textbook OSEM on an 8x8x8 grid built
+                        by brute force; sum s lambda = B N_eff per
+                        sub-iteration; B = 1 is MLEM)
   median3 / sieve ..... pinned (scipy.ndimage.median_filter; closed forms on
                         constant images at faces, edges and corners;
                         impulse removal; ramps preserved)
@@ -54,4 +57,5 @@ from .core import (  # noqa: F401
     trace,
 )
 from .filters import median3, median3_at, sieve  # noqa: F401
-from .mlem import mlem, mlem_regions, region_bounds, region_slabs, slab_grid, stitch  # noqa: F401
+from .mlem import (mlem, mlem_regions, osem, region_bounds, region_slabs, slab_grid, stitch,  # noqa: F401
+                   subset_ranges)

@@ -130,3 +130,40 @@ def mlem_regions(grid, events, sens, regions, shell_mm, margin_mm, n_iter, sigma
         images.append(lam_r)
         hists.append(h_r)
     return stitch(grid, slabs, images), images, hists, codes, offsets, idx
+
+
+def subset_ranges(n, n_subsets):
+    """Event ranges of the OSEM subsets: B consecutive blocks of the list."""
+    return [(b * n // n_subsets, (b + 1) * n // n_subsets) for b in range(n_subsets)]
+
+
+def osem(grid, events, sens, n_iter, n_subsets, sigma, K=3.0, weights=None, init=None, threads=None):
+    """List-mode OSEM (named in the title of Sec. 2.4; the paper reconstructs
+    with MLEM).  Reading: subset b holds the events of block b of the list
+    (subset_ranges; list-mode data arrive in random order, so blocks are random
+    partitions), and a sub-iteration is one MLEM update with that subset's
+    backprojection against the sensitivity scaled by 1/B:
+        lambda_j <- lambda_j C_j^b / (s_j / B)   where s_j > 0, else 0.
+    Returns (lambda, history) with one (N_eff of the subset, sum_j s_j lambda_j)
+    entry per sub-iteration; sum_j s_j lambda_j = B N_eff after each one.
+    """
+    s = np.asarray(sens, np.float64).reshape(-1)
+    n = np.asarray(events[0]).shape[0]
+    w = np.ones(n) if weights is None else np.asarray(weights, np.float64)
+    mask = s > 0
+    lam = uniform_start(s, w.sum()) if init is None else np.asarray(init, np.float64).reshape(-1).copy()
+    history = []
+    for _ in range(n_iter):
+        for lo, hi in subset_ranges(n, n_subsets):
+            ev_b = [np.asarray(e)[lo:hi] for e in events]
+            w_b = w[lo:hi]
+            p = forward(grid, ev_b, lam, sigma, K, threads)
+            valid = p > 0
+            r = np.zeros(hi - lo)
+            r[valid] = w_b[valid] / p[valid]
+            Cimg = backproject(grid, ev_b, r, sigma, K, threads)
+            new = np.zeros_like(lam)
+            new[mask] = lam[mask] * Cimg[mask] / (s[mask] / n_subsets)
+            lam = new
+            history.append((float(w_b[valid].sum()), float(np.sum(s * lam))))
+    return lam, history

@@ -173,6 +173,16 @@ recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_sa
 recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float* offsets_mm, float* weights,
                                    int32_t* n_out);
 
+/* List-mode OSEM for recon_mlem (OSEM is named in the title of Sec. 2.4; the paper
+ * itself reconstructs with MLEM).  n_subsets = B > 1: each iteration runs B
+ * sub-iterations; sub-iteration b uses the events of block b of the list,
+ * [b n / B, (b+1) n / B) (list-mode events arrive in random order, so the blocks are
+ * random partitions), and updates lambda_j <- lambda_j C_j^b / (s_j / B).  B = 1 (the
+ * default) is MLEM.  recon_mlem_regions always runs MLEM.  The median sieve, when on,
+ * runs once per iteration, after the last subset.  Errors: EINVAL (B outside
+ * [1, 1024]). */
+recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets);
+
 /* Median-filter sieve between iterations (Sec. 2.4; Sec. 4 on its effect at the
  * borders of divided images).  on = 1: after every iteration's update of recon_mlem
  * and recon_mlem_regions, lambda is replaced by its 3 x 3 x 3 median (the 14th
@@ -280,8 +290,11 @@ recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const
  * receiving the final image (the image also stays in the context).
  * conservation_out: NULL or n_iter x 2 doubles {N_eff, sum_j s_j lambda_j} after each
  * iteration, FP64 sums (N_eff = sum of w_i over events with p_i > 0); the two agree up
- * to FP32 rounding of the image (count conservation).
- * Errors: EINVAL (n_iter < 0), ESTATE (no sensitivity image or no events). */
+ * to FP32 rounding of the image (count conservation).  With B OSEM subsets
+ * (recon_set_subsets) there are n_iter x B rows, one per sub-iteration, and
+ * sum_j s_j lambda_j = B N_eff of that subset.
+ * Errors: EINVAL (n_iter < 0, n_iter x B > 2^24), ESTATE (no sensitivity image or no
+ * events). */
 recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_iter, const float* init,
                         float* image_out, double* conservation_out);
 

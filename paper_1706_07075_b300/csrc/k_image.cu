@@ -63,7 +63,7 @@ __global__ void k_fill_masked(float* __restrict__ lam, const float* __restrict__
 __global__ void __launch_bounds__(kImgThreads) k_update(float* __restrict__ lam, float* __restrict__ C,
                                                         const float* __restrict__ s, uint16_t* __restrict__ lam_bf16,
                                                         const long long* __restrict__ reg_vox, int bpr,
-                                                        double* __restrict__ part)
+                                                        double* __restrict__ part, float scale)
 {
     __shared__ double sh[32];
     const int r = blockIdx.x / bpr, b = blockIdx.x % bpr;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kImgThreads) k_update(float* __restrict__ lam,
     for (long long j = lo + (long long)b * blockDim.x + threadIdx.x; j < hi; j += (long long)bpr * blockDim.x) {
         float sj = s[j];
         float v = 0.f;
-        if (sj > 0.f) v = lam[j] * C[j] / sj;
+        if (sj > 0.f) v = lam[j] * C[j] * scale / sj;   // scale = 1 (MLEM) or B (OSEM: s / B)
         lam[j] = v;
         C[j] = 0.f;
         if (lam_bf16) lam_bf16[j] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
@@ -215,10 +215,10 @@ int update_blocks(long long n_vox)
 }
 
 cudaError_t launch_update(float* lam, float* C, const float* s32, uint16_t* lam_bf16, const long long* reg_vox,
-                          int n_regions, double* partial, int blocks_per_region, cudaStream_t st)
+                          int n_regions, double* partial, int blocks_per_region, cudaStream_t st, float scale)
 {
     k_update<<<n_regions * blocks_per_region, kImgThreads, 0, st>>>(lam, C, s32, lam_bf16, reg_vox,
-                                                                   blocks_per_region, partial);
+                                                                   blocks_per_region, partial, scale);
     return cudaGetLastError();
 }
 

@@ -74,6 +74,7 @@ struct recon_ctx {
     double fwhm_ps = 0, sigma_mm = 0, k_sigma = 3.0;
     int lut_n = 0;   // samples of the sampled TOF kernel; 0: exact projector
     bool median = false;  // median-filter sieve after every iteration
+    int subsets = 1;      // OSEM subsets of recon_mlem (1: MLEM)
     int device = 0, num_sms = 148;
     cudaStream_t own_stream = nullptr, stream = nullptr;
     std::string err;
@@ -426,7 +427,21 @@ struct IterPlan {
     float* med;      // median-filter output (nullptr: no sieve); copied back into lam
     long long med_vox;
     int max_nz;
+    int subsets;     // OSEM subsets (1: MLEM); single-region plans only
+    size_t rec_bytes;
 };
+
+// Pass arguments of sub-iteration b: events of block b of the list.
+void subset_args(const IterPlan& p, int b, PassArgs& a, RegionTable& t)
+{
+    a = p.a;
+    t = p.tbl;
+    if (p.subsets <= 1) return;
+    const long long n = p.a.n, lo = b * n / p.subsets, hi = (b + 1) * n / p.subsets;
+    a.events = static_cast<const char*>(p.a.events) + (size_t)lo * p.rec_bytes;
+    a.n = hi - lo;
+    t.ev_begin[1] = hi - lo;
+}
 
 // Sieve (Sec. 2.4): lam -> median -> lam, after the update.
 recon_status enqueue_sieve(recon_ctx* ctx, const IterPlan& p)
@@ -440,14 +455,21 @@ recon_status enqueue_sieve(recon_ctx* ctx, const IterPlan& p)
 
 recon_status enqueue_iteration(recon_ctx* ctx, const IterPlan& p)
 {
-    if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
-    CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, p.a, p.tbl, ctx->num_sms, ctx->stream));
-    CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(), p.upd_bpr,
-                     ctx->stream));
-    recon_status sv = enqueue_sieve(ctx, p);
-    if (sv != RECON_OK) return sv;
-    CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions, p.hist,
-                       p.iter, p.hist_cap, ctx->stream));
+    for (int b = 0; b < p.subsets; ++b) {
+        PassArgs a;
+        RegionTable t;
+        subset_args(p, b, a, t);
+        if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+        CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, a, t, ctx->num_sms, ctx->stream));
+        CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(),
+                         p.upd_bpr, ctx->stream, (float)p.subsets));
+        if (b == p.subsets - 1) {
+            recon_status sv = enqueue_sieve(ctx, p);
+            if (sv != RECON_OK) return sv;
+        }
+        CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions, p.hist,
+                           p.iter, p.hist_cap, ctx->stream));
+    }
     return RECON_OK;
 }
 
@@ -460,7 +482,8 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
     std::string k(buf);
-    snprintf(buf, sizeof buf, " lut %d med %p %lld %d", p.a.lut.n, (void*)p.med, p.med_vox, p.max_nz);
+    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d", p.a.lut.n, (void*)p.med, p.med_vox, p.max_nz,
+             p.subsets);
     k += buf;
     for (int r = 0; r < p.tbl.n; ++r) {
         snprintf(buf, sizeof buf, "|%lld %d %a %lld", p.tbl.ev_begin[r + 1], p.tbl.grid[r].nz,
@@ -478,30 +501,39 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter)
     const bool legacy = ctx->stream == nullptr || ctx->stream == cudaStreamLegacy || ctx->stream == cudaStreamPerThread;
     if (ctx->timing || !ctx->graphs || legacy) {
         std::vector<cudaEvent_t> evs;
+        const int B = p.subsets;
         if (ctx->timing) {
-            evs.resize(3 * (size_t)n_iter);
+            evs.resize(3 * (size_t)n_iter * B);
             for (auto& e : evs) CK(cudaEventCreate(&e));
         }
         for (int k = 0; k < n_iter; ++k) {
-            if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
-            if (ctx->timing) CK(cudaEventRecord(evs[3 * k], ctx->stream));
-            CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, p.a, p.tbl, ctx->num_sms, ctx->stream));
-            if (ctx->timing) CK(cudaEventRecord(evs[3 * k + 1], ctx->stream));
-            CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(),
-                             p.upd_bpr, ctx->stream));
-            recon_status sv = enqueue_sieve(ctx, p);
-            if (sv != RECON_OK) return sv;
-            if (ctx->timing) CK(cudaEventRecord(evs[3 * k + 2], ctx->stream));
-            CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions,
-                               p.hist, p.iter, p.hist_cap, ctx->stream));
-            ctx->stats.kernel_launches += (p.pass_blocks > 0 ? 3 : 2) + (p.med ? 1 : 0);
+            for (int b = 0; b < B; ++b) {
+                const size_t e = (size_t)k * B + b;
+                PassArgs a;
+                RegionTable t;
+                subset_args(p, b, a, t);
+                if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+                if (ctx->timing) CK(cudaEventRecord(evs[3 * e], ctx->stream));
+                CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, a, t, ctx->num_sms, ctx->stream));
+                if (ctx->timing) CK(cudaEventRecord(evs[3 * e + 1], ctx->stream));
+                CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions,
+                                 ctx->upd_partial.as<double>(), p.upd_bpr, ctx->stream, (float)B));
+                if (b == B - 1) {
+                    recon_status sv = enqueue_sieve(ctx, p);
+                    if (sv != RECON_OK) return sv;
+                }
+                if (ctx->timing) CK(cudaEventRecord(evs[3 * e + 2], ctx->stream));
+                CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions,
+                                   p.hist, p.iter, p.hist_cap, ctx->stream));
+                ctx->stats.kernel_launches += (a.n > 0 ? 3 : 2) + (p.med && b == B - 1 ? 1 : 0);
+            }
         }
         if (ctx->timing) {
             CK(cudaStreamSynchronize(ctx->stream));
-            for (int k = 0; k < n_iter; ++k) {
+            for (size_t e = 0; e < (size_t)n_iter * B; ++e) {
                 float a = 0, b = 0;
-                CK(cudaEventElapsedTime(&a, evs[3 * k], evs[3 * k + 1]));
-                CK(cudaEventElapsedTime(&b, evs[3 * k + 1], evs[3 * k + 2]));
+                CK(cudaEventElapsedTime(&a, evs[3 * e], evs[3 * e + 1]));
+                CK(cudaEventElapsedTime(&b, evs[3 * e + 1], evs[3 * e + 2]));
                 ctx->stats.pass_ms += a;
                 ctx->stats.update_ms += b;
                 ctx->stats.pass_launches += 1;
@@ -532,7 +564,7 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter)
     }
     for (int k = 0; k < n_iter; ++k) {
         CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-        ctx->stats.kernel_launches += (p.pass_blocks > 0 ? 3 : 2) + (p.med ? 1 : 0);
+        ctx->stats.kernel_launches += (long long)p.subsets * (p.pass_blocks > 0 ? 3 : 2) + (p.med ? 1 : 0);
     }
     return RECON_OK;
 }
@@ -755,6 +787,15 @@ recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_sa
     } else {
         return fail(ctx, RECON_EINVAL, "unknown projector");
     }
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets)
+{
+    CHECK_CTX();
+    if (n_subsets < 1 || n_subsets > 1024) return fail(ctx, RECON_EINVAL, "n_subsets must be in [1, 1024]");
+    ctx->subsets = n_subsets;
     invalidate_graph(ctx);
     return RECON_OK;
 }
@@ -1037,6 +1078,7 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
 {
     CHECK_CTX();
     if (n_iter < 0) return fail(ctx, RECON_EINVAL, "n_iter is negative");
+    if ((long long)n_iter * ctx->subsets > (1LL << 24)) return fail(ctx, RECON_EINVAL, "n_iter x subsets too large");
     if (events) {
         recon_status s = load_events(ctx, events);
         if (s != RECON_OK) return s;
@@ -1077,7 +1119,9 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     CK(ensure(ctx->reg_vox, sizeof(long long) * 2));
     const long long rv[2] = {0, nv};
     CK(cudaMemcpyAsync(ctx->reg_vox.p, rv, sizeof rv, cudaMemcpyHostToDevice, ctx->stream));
-    p.hist_cap = std::max(n_iter, 64);
+    p.subsets = ctx->subsets;
+    p.rec_bytes = ctx->fmt == FMT_PACKED ? 16 : 32;
+    p.hist_cap = std::max(n_iter * p.subsets, 64);
     CK(ensure(ctx->hist, sizeof(double) * 2 * (size_t)p.hist_cap));
     p.hist = ctx->hist.as<double>();
     p.iter = ctx->iter.as<int>();
@@ -1099,8 +1143,8 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     if (s != RECON_OK) return s;
     if (image_out) CK(cudaMemcpyAsync(image_out, ctx->lam.p, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
     if (conservation_out && n_iter > 0)
-        CK(cudaMemcpyAsync(conservation_out, ctx->hist.p, sizeof(double) * 2 * n_iter, cudaMemcpyDefault,
-                           ctx->stream));
+        CK(cudaMemcpyAsync(conservation_out, ctx->hist.p, sizeof(double) * 2 * (size_t)n_iter * p.subsets,
+                           cudaMemcpyDefault, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return RECON_OK;
 }
@@ -1267,6 +1311,8 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
     p.pass_blocks = pass_blocks(p.cfg, total, ctx->num_sms);
     p.upd_bpr = std::max(1, update_blocks(nvt) / R);
     CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)p.upd_bpr * R));
+    p.subsets = 1;
+    p.rec_bytes = ctx->fmt == FMT_PACKED ? 16 : 32;
     p.hist_cap = std::max(n_iter, 64);
     CK(ensure(ctx->hist, sizeof(double) * 2 * (size_t)p.hist_cap * R));
     p.hist = ctx->hist.as<double>();

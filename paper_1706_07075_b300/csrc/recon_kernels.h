@@ -85,10 +85,11 @@ cudaError_t launch_sens_finish(const double* s64, long long n_vox, float* s32, d
 // lam = s > 0 ? value : 0 over n voxels.
 cudaError_t launch_fill_masked(float* lam, const float* s32, long long n_vox, float value, cudaStream_t st);
 // Update per region (reg_vox: device array of region voxel offsets, n_regions+1):
-// lam <- s > 0 ? lam * C / s : 0; C <- 0; optional BF16 copy; partial[r * bpr + b] = sum s*lam.
+// lam <- s > 0 ? lam * C * scale / s : 0; C <- 0; optional BF16 copy; partial[r * bpr + b] = sum s*lam.
+// scale: 1 for MLEM, B for an OSEM sub-iteration over one of B subsets.
 int update_blocks(long long n_vox);
 cudaError_t launch_update(float* lam, float* C, const float* s32, uint16_t* lam_bf16, const long long* reg_vox,
-                          int n_regions, double* partial, int blocks_per_region, cudaStream_t st);
+                          int n_regions, double* partial, int blocks_per_region, cudaStream_t st, float scale = 1.f);
 // hist[(k * R + r) * 2 + {0,1}] = {N_eff, sum s lambda} of region r after iteration k = *iter; ++*iter.
 cudaError_t launch_finalize(double* pass_partial, int pass_slots, const double* upd_partial,
                             int upd_blocks_per_region, int n_regions, double* hist, int* iter_counter,

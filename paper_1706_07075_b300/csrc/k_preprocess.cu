@@ -25,13 +25,22 @@ __global__ void __launch_bounds__(256) k_preprocess(void* events, long long n, f
         const Event e = Fmt == FMT_F32 ? load_event_f32(static_cast<const float4*>(events), i)
                                        : load_event_packed(static_cast<const int4*>(events), i, lattice);
         float3 c, u;
-        float line_mu = 0.f;
+        float line_mu = 0.f, comp = 0.f;
         keep = !(half_window > 0.f);
         if (event_line(e, c, u)) {
             TofDev tof{};
             TailErfc tail{};
             const Walk whole = make_walk(g, c, u, -1e30f, 1e30f);
-            walk<false>(g, tof, tail, whole, [&](int j, float L) { line_mu = fmaf(__ldg(mu + j), L, line_mu); });
+            // a long LOR crosses hundreds of body voxels: compensated (two-sum)
+            // accumulation keeps the integral to ~1 ulp instead of ~n/2 ulp
+            walk<false>(g, tof, tail, whole, [&](int j, float L) {
+                const float x = __fmul_rn(__ldg(mu + j), L);
+                const float t = __fadd_rn(line_mu, x);
+                const float z = __fsub_rn(t, line_mu);
+                comp = __fadd_rn(comp, __fadd_rn(__fsub_rn(line_mu, __fsub_rn(t, z)), __fsub_rn(x, z)));
+                line_mu = t;
+            });
+            line_mu = __fadd_rn(line_mu, comp);
             if (half_window > 0.f) {
                 const Walk win = make_walk(g, c, u, -half_window, half_window);
                 walk<false>(g, tof, tail, win, [&](int j, float L) {

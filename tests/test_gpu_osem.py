@@ -49,7 +49,9 @@ def test_one_subset_is_mlem(tiny_osem):
             lam = np.zeros(g.n_vox, np.float32)
             ctx.mlem(B.make_events(ev), 2, None, lam)
             out.append(lam)
-    assert np.array_equal(out[0], out[1])
+    # FP32 reductions land in a different order on every run, so two runs agree
+    # to rounding, not bit for bit
+    assert rel_l2(out[1], out[0]) < 1e-6
 
 
 def test_more_subsets_than_events(tiny_osem):

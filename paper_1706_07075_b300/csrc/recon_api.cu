@@ -77,6 +77,10 @@ struct recon_ctx {
     int subsets = 1;      // OSEM subsets of recon_mlem (1: MLEM)
     int device = 0, num_sms = 148;
     cudaStream_t own_stream = nullptr, stream = nullptr;
+    cudaStream_t copy_stream = nullptr;            // host-to-device copies of the streamed first pass
+    cudaEvent_t copied[2] = {nullptr, nullptr};    // staging half k holds chunk data
+    cudaEvent_t drained[2] = {nullptr, nullptr};   // staging half k has been ingested
+    cudaEvent_t ready = nullptr;                   // prior work on ctx->stream done
     std::string err;
     long long n_vox = 0;
 
@@ -494,9 +498,9 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
 }
 
 // Run n_iter iterations of the plan: graph replay, or direct launches (timing).
-recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter)
+recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool reset_counter = true)
 {
-    CK(cudaMemsetAsync(p.iter, 0, sizeof(int), ctx->stream));
+    if (reset_counter) CK(cudaMemsetAsync(p.iter, 0, sizeof(int), ctx->stream));
     if (n_iter == 0) return RECON_OK;
     const bool legacy = ctx->stream == nullptr || ctx->stream == cudaStreamLegacy || ctx->stream == cudaStreamPerThread;
     if (ctx->timing || !ctx->graphs || legacy) {
@@ -567,6 +571,15 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter)
         ctx->stats.kernel_launches += (long long)p.subsets * (p.pass_blocks > 0 ? 3 : 2) + (p.med ? 1 : 0);
     }
     return RECON_OK;
+}
+
+// The launch choose_cfg would pick, without running the autotuner.
+LaunchCfg tuned_or_default(recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl)
+{
+    if (ctx->user_cfg) return ctx->cfg;
+    if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg();
+    auto it = ctx->tuned.find(std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n));
+    return it != ctx->tuned.end() ? it->second : default_cfg();
 }
 
 LaunchCfg choose_cfg(recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl, recon_status* st)
@@ -739,6 +752,12 @@ void recon_destroy(recon_ctx* ctx)
                       &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg};
     for (DevBuf* b : bufs) release(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->copied[k]) cudaEventDestroy(ctx->copied[k]);
+        if (ctx->drained[k]) cudaEventDestroy(ctx->drained[k]);
+    }
+    if (ctx->ready) cudaEventDestroy(ctx->ready);
     delete ctx;
 }
 
@@ -1073,13 +1092,105 @@ recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const
     return RECON_OK;
 }
 
+// Host events and n_iter >= 1: the upload is streamed in chunks through two
+// staging halves on a copy stream, and the first iteration's event pass runs
+// on each chunk as soon as it is resident, so the pass hides under the
+// host-to-device copies.  Then the first update runs as usual.
+bool can_stream(const recon_ctx* ctx, const recon_events* e, int n_iter)
+{
+    return e && !e->on_device && !e->weight && e->n > 0 && n_iter >= 1 && ctx->subsets == 1;
+}
+
+// Resident-event state for a streamed upload (the data arrive in stream_pass).
+recon_status begin_streamed_events(recon_ctx* ctx, const recon_events* e)
+{
+    recon_status s = validate_events(ctx, e);
+    if (s != RECON_OK) return s;
+    const bool packed = e->fmt == RECON_EV_PACKED_I16_F16;
+    CK(ensure(ctx->ev, (size_t)e->n * (packed ? 16 : 32)));
+    ctx->fmt = packed ? FMT_PACKED : FMT_F32;
+    ctx->lattice = packed ? e->lattice_mm : 0.0;
+    ctx->n_ev = e->n;
+    ctx->have_ev = true;
+    ctx->ev_generation++;
+    invalidate_graph(ctx);
+    ctx->w_total = (double)e->n;   // unit weights (can_stream excludes caller weights)
+    return RECON_OK;
+}
+
+recon_status stream_pass(recon_ctx* ctx, const recon_events* e, const IterPlan& p)
+{
+    if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+        if (!ctx->copied[k]) CK(cudaEventCreateWithFlags(&ctx->copied[k], cudaEventDisableTiming));
+        if (!ctx->drained[k]) CK(cudaEventCreateWithFlags(&ctx->drained[k], cudaEventDisableTiming));
+    }
+    if (!ctx->ready) CK(cudaEventCreateWithFlags(&ctx->ready, cudaEventDisableTiming));
+    const bool packed = ctx->fmt == FMT_PACKED;
+    const long long n = e->n;
+    const long long chunk = std::min(n, 1LL << 23);
+    const size_t half = (size_t)chunk * (packed ? 16 : 28);
+    CK(ensure(ctx->staging, 2 * half));
+    // staging may still be read by earlier work on ctx->stream
+    CK(cudaEventRecord(ctx->ready, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ready, 0));
+    int q = 0;
+    for (long long lo = 0; lo < n; lo += chunk, q ^= 1) {
+        const long long m = std::min(chunk, n - lo);
+        char* st = static_cast<char*>(ctx->staging.p) + (size_t)q * half;
+        if (lo >= 2 * chunk) CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->drained[q], 0));
+        const float* pl[7];
+        if (packed) {
+            CK(cudaMemcpyAsync(st, static_cast<const int4*>(e->planes[0]) + lo, (size_t)m * 16,
+                               cudaMemcpyHostToDevice, ctx->copy_stream));
+        } else {
+            for (int k = 0; k < 7; ++k) {
+                float* dst = reinterpret_cast<float*>(st) + (size_t)k * chunk;
+                CK(cudaMemcpyAsync(dst, static_cast<const float*>(e->planes[k]) + lo, (size_t)m * 4,
+                                   cudaMemcpyHostToDevice, ctx->copy_stream));
+                pl[k] = dst;
+            }
+        }
+        CK(cudaEventRecord(ctx->copied[q], ctx->copy_stream));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->copied[q], 0));
+        if (packed)
+            CK(launch_ingest_packed(reinterpret_cast<const int4*>(st), nullptr, m, ctx->ev.as<int4>() + lo,
+                                    ctx->stream));
+        else
+            CK(launch_ingest_f32(pl, nullptr, m, ctx->ev.as<float4>() + 2 * lo, ctx->stream));
+        CK(cudaEventRecord(ctx->drained[q], ctx->stream));
+        PassArgs a = p.a;
+        RegionTable t = p.tbl;
+        a.events = static_cast<const char*>(p.a.events) + (size_t)lo * p.rec_bytes;
+        a.n = m;
+        t.ev_begin[1] = m;
+        if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+        CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, a, t, ctx->num_sms, ctx->stream));
+        ctx->stats.kernel_launches += 2;
+    }
+    // first update (the pass above was its event pass)
+    CK(cudaMemsetAsync(p.iter, 0, sizeof(int), ctx->stream));
+    CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(), p.upd_bpr,
+                     ctx->stream));
+    recon_status sv = enqueue_sieve(ctx, p);
+    if (sv != RECON_OK) return sv;
+    CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions, p.hist,
+                       p.iter, p.hist_cap, ctx->stream));
+    ctx->stats.kernel_launches += 2 + (p.med ? 1 : 0);
+    return RECON_OK;
+}
+
 recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_iter, const float* init,
                         float* image_out, double* conservation_out)
 {
     CHECK_CTX();
     if (n_iter < 0) return fail(ctx, RECON_EINVAL, "n_iter is negative");
     if ((long long)n_iter * ctx->subsets > (1LL << 24)) return fail(ctx, RECON_EINVAL, "n_iter x subsets too large");
-    if (events) {
+    const bool streamed = can_stream(ctx, events, n_iter) && ctx->have_sens;
+    if (streamed) {
+        recon_status s = begin_streamed_events(ctx, events);
+        if (s != RECON_OK) return s;
+    } else if (events) {
         recon_status s = load_events(ctx, events);
         if (s != RECON_OK) return s;
     }
@@ -1109,8 +1220,9 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     recon_status st;
     CK(ensure(ctx->pass_partial, sizeof(double) * kNeffSlots));
     p.a.partial = ctx->pass_partial.as<double>();
-    p.cfg = choose_cfg(ctx, p.a, p.tbl, &st);
-    if (st != RECON_OK) return st;
+    // a streamed call autotunes only once the events are resident (not before the upload)
+    p.cfg = streamed ? tuned_or_default(ctx, p.a, p.tbl) : choose_cfg(ctx, p.a, p.tbl, &st);
+    if (!streamed && st != RECON_OK) return st;
     CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
     CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots, ctx->stream));
     p.pass_blocks = pass_blocks(p.cfg, ctx->n_ev, ctx->num_sms);
@@ -1139,7 +1251,24 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
         p.med = ctx->med.as<float>();
     }
     ctx->last_cfg = p.cfg;
-    recon_status s = run_iterations(ctx, p, n_iter);
+    recon_status s;
+    if (streamed) {
+        s = stream_pass(ctx, events, p);
+        if (s != RECON_OK) return s;
+        if (n_iter > 1) {
+            LaunchCfg c = choose_cfg(ctx, p.a, p.tbl, &st);
+            if (st != RECON_OK) return st;
+            if (c.blocks_per_sm != p.cfg.blocks_per_sm || c.threads != p.cfg.threads || c.chunk != p.cfg.chunk ||
+                c.cache != p.cfg.cache || c.tail != p.cfg.tail) {
+                p.cfg = c;
+                p.pass_blocks = pass_blocks(p.cfg, ctx->n_ev, ctx->num_sms);
+                ctx->last_cfg = c;
+            }
+        }
+        s = run_iterations(ctx, p, n_iter - 1, false);
+    } else {
+        s = run_iterations(ctx, p, n_iter);
+    }
     if (s != RECON_OK) return s;
     if (image_out) CK(cudaMemcpyAsync(image_out, ctx->lam.p, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
     if (conservation_out && n_iter > 0)

@@ -92,3 +92,31 @@ def _oracle_mlem_tiny():
         s_ref = oracle_sensitivity("tiny", lors.shape[1], 1706)
         _cache["mlem"] = oracle.mlem(g, ev.astype(np.float64), s_ref, 5, SIGMA)
     return _cache["mlem"]
+
+
+def test_streamed_upload_matches_resident_events():
+    # host events: the upload is streamed in 8 M-event chunks through two staging
+    # halves and the first pass runs per chunk; three chunks exercise the reuse of
+    # a half.  The resident path (events loaded first, then events = NULL) must
+    # give the same iterations up to FP32 reduction order.
+    from gpu_common import geometry, grid_tuple
+    from paper_1706_07075_b300 import synth
+    g = workload_grid("tiny")
+    ev = synth.events("tiny", 17_000_000, 77)
+    lors = synth.sensitivity_lors("tiny", 400_000, 77)
+    out = []
+    with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx:
+        ctx.sensitivity(lors)
+        for streamed in (True, False):
+            lam = np.zeros(g.n_vox, np.float32)
+            cons = np.zeros((3, 2))
+            if streamed:
+                ctx.mlem(B.make_events(ev), 3, None, lam, cons)
+            else:
+                ctx.load_events(B.make_events(ev))
+                ctx.mlem(None, 3, None, lam, cons)
+            out.append((lam, cons))
+    (a, ca), (b, cb) = out
+    assert rel_l2(a, b) < 1e-6
+    np.testing.assert_array_equal(ca[:, 0], cb[:, 0])                     # same events with p > 0
+    np.testing.assert_allclose(ca[:, 1], ca[:, 0], rtol=1e-5)

@@ -109,6 +109,15 @@ typedef struct {
     int32_t has_sensitivity;
     int32_t num_sms;
     double sens_total;         /* sum of s_j over {s_j > 0} */
+    /* binning of the resident events for the shared-memory tiled pass (all 0 when the last
+     * recon_mlem did not use it): non-empty cells, events in them (including those whose
+     * window misses the grid, which contribute nothing), events taking the global-memory
+     * fallback pass, cell edge in voxels, tile halo per axis in voxels */
+    int64_t tile_cells;
+    int64_t tile_events;
+    int64_t tile_fallback_events;
+    int32_t tile_cell_voxels;
+    int32_t tile_halo[3];
 } recon_info;
 
 typedef struct {
@@ -172,6 +181,20 @@ recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_sa
  * floats.  EINVAL (with *n_out set) when capacity is too small. */
 recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float* offsets_mm, float* weights,
                                    int32_t* n_out);
+
+/* Shared-memory tiled event pass for recon_mlem (on by default).  A layout choice for
+ * the same arithmetic (Sec. 2.3, 2.4), with no counterpart in the paper: the resident
+ * events are binned once by the cell (cs^3 voxels) that holds their TOF point; one block
+ * per cell holds the cell's tile of lambda and of C (the cell widened by the TOF window,
+ * K sigma |u_k| per axis, |u_z| bounded by the scanner's max axial angle) in shared
+ * memory, walks the cell's events with eight lanes per event, and adds its C tile into
+ * the image.  Events whose window would leave their tile take the global-memory pass.
+ * Used for MLEM with the exact projector and one subset when two tiles fit the shared
+ * memory of a block (e.g. 4 mm voxels at 300 ps); otherwise, or with on = 0, every event
+ * takes the global-memory pass.  The binning costs one copy of the events (32 or 16 bytes
+ * each) and is cached until the events or the kernel window change.  recon_get_info
+ * reports the binning. */
+recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on);
 
 /* List-mode OSEM for recon_mlem (OSEM is named in the title of Sec. 2.4; the paper
  * itself reconstructs with MLEM).  n_subsets = B > 1: each iteration runs B

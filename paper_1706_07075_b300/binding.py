@@ -54,7 +54,8 @@ class recon_launch(C.Structure):
 class recon_info(C.Structure):
     _fields_ = [("sigma_mm", C.c_double), ("k_sigma", C.c_double), ("n_vox", C.c_int64),
                 ("n_events_resident", C.c_int64), ("has_sensitivity", C.c_int32), ("num_sms", C.c_int32),
-                ("sens_total", C.c_double)]
+                ("sens_total", C.c_double), ("tile_cells", C.c_int64), ("tile_events", C.c_int64),
+                ("tile_fallback_events", C.c_int64), ("tile_cell_voxels", C.c_int32), ("tile_halo", C.c_int32 * 3)]
 
 
 class recon_stats(C.Structure):
@@ -75,6 +76,7 @@ SIGNATURES = {
     "recon_set_projector": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "recon_set_median_filter": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_subsets": (C.c_int, [_CTX, C.c_int32]),
+    "recon_set_tiled_pass": (C.c_int, [_CTX, C.c_int32]),
     "recon_preprocess": (C.c_int, [_CTX, C.POINTER(recon_events), _VP, C.c_double, C.c_int32, _VP, _VP,
                                    C.POINTER(C.c_int64)]),
     "recon_median_filter": (C.c_int, [_CTX, _VP, _VP]),
@@ -235,6 +237,10 @@ def recon_set_projector(ctx, projector, n_samples=0):
     return check(ctx, load().recon_set_projector(ctx, int(projector), int(n_samples)))
 
 
+def recon_set_tiled_pass(ctx, on):
+    return check(ctx, load().recon_set_tiled_pass(ctx, int(bool(on))))
+
+
 def recon_set_subsets(ctx, n_subsets):
     return check(ctx, load().recon_set_subsets(ctx, int(n_subsets)))
 
@@ -292,7 +298,11 @@ def recon_set_autotune(ctx, on):
 def recon_get_info(ctx):
     info = recon_info()
     check(ctx, load().recon_get_info(ctx, C.byref(info)))
-    return {f: getattr(info, f) for f, _ in recon_info._fields_}
+    out = {}
+    for f, _ in recon_info._fields_:
+        v = getattr(info, f)
+        out[f] = list(v) if isinstance(v, C.Array) else v
+    return out
 
 
 def recon_get_stats(ctx):

@@ -66,6 +66,19 @@ struct RegionPrep {
     std::vector<float> start;     // uniform start value per region
 };
 
+// Cell binning of the resident events for the shared-memory tiled pass, valid
+// for one (events, grid, kernel window) combination.
+struct TilePrep {
+    bool valid = false;
+    long long ev_gen = -1;
+    double half_window = 0;
+    TileH th{};
+    long long n_cells = 0;
+    unsigned n_list = 0;
+    long long n_fb = 0;
+    DevBuf code, counts, cursor, begin, scratch, list, ev_cell, ev_fb, misc;
+};
+
 }  // namespace
 
 struct recon_ctx {
@@ -117,6 +130,10 @@ struct recon_ctx {
     DevBuf codes, counts, offsets, base, idx, ev_reg, lam_reg, C_reg, s_reg, bf16_reg, reg_vox_reg;
     RegionPrep region_prep;
     long long sens_generation = 0;
+
+    // shared-memory tiled pass (plain MLEM with the exact projector)
+    int tile_mode = 1;    // 0 off, 1 on where the tile fits shared memory
+    TilePrep tile_prep;
 };
 
 namespace {
@@ -433,7 +450,41 @@ struct IterPlan {
     int max_nz;
     int subsets;     // OSEM subsets (1: MLEM); single-region plans only
     size_t rec_bytes;
+    // shared-memory tiled pass (single region, MLEM, exact projector)
+    bool tiled = false;
+    TileH th{};
+    const unsigned* list = nullptr;
+    unsigned n_list = 0;
+    const long long* tbegin = nullptr;
+    const void* ev_cell = nullptr;
+    const void* ev_fb = nullptr;
+    long long n_fb = 0;
 };
+
+// The fused event pass of one (sub-)iteration: the tiled pass over the binned
+// events plus the global-memory pass over the fallback events, or the
+// global-memory pass alone.
+recon_status launch_event_pass(recon_ctx* ctx, const IterPlan& p, const PassArgs& a, const RegionTable& t)
+{
+    if (!p.tiled) {
+        if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+        CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, a, t, ctx->num_sms, ctx->stream));
+        return RECON_OK;
+    }
+    PassArgs at = a;
+    at.events = p.ev_cell;
+    CK(launch_tile_pass(at, p.th, p.list, p.n_list, p.tbegin, p.cfg.tail, ctx->stream));
+    if (p.n_fb > 0) {
+        PassArgs af = a;
+        af.events = p.ev_fb;
+        af.n = p.n_fb;
+        RegionTable tf = t;
+        tf.ev_begin[1] = p.n_fb;
+        if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+        CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, af, tf, ctx->num_sms, ctx->stream));
+    }
+    return RECON_OK;
+}
 
 // Pass arguments of sub-iteration b: events of block b of the list.
 void subset_args(const IterPlan& p, int b, PassArgs& a, RegionTable& t)
@@ -463,8 +514,8 @@ recon_status enqueue_iteration(recon_ctx* ctx, const IterPlan& p)
         PassArgs a;
         RegionTable t;
         subset_args(p, b, a, t);
-        if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
-        CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, a, t, ctx->num_sms, ctx->stream));
+        recon_status sp = launch_event_pass(ctx, p, a, t);
+        if (sp != RECON_OK) return sp;
         CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions, ctx->upd_partial.as<double>(),
                          p.upd_bpr, ctx->stream, (float)p.subsets));
         if (b == p.subsets - 1) {
@@ -486,8 +537,8 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
     std::string k(buf);
-    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d", p.a.lut.n, (void*)p.med, p.med_vox, p.max_nz,
-             p.subsets);
+    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %p %u %p %p %lld", p.a.lut.n, (void*)p.med,
+             p.med_vox, p.max_nz, p.subsets, (int)p.tiled, (const void*)p.list, p.n_list, p.ev_cell, p.ev_fb, p.n_fb);
     k += buf;
     for (int r = 0; r < p.tbl.n; ++r) {
         snprintf(buf, sizeof buf, "|%lld %d %a %lld", p.tbl.ev_begin[r + 1], p.tbl.grid[r].nz,
@@ -516,9 +567,9 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool 
                 PassArgs a;
                 RegionTable t;
                 subset_args(p, b, a, t);
-                if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
                 if (ctx->timing) CK(cudaEventRecord(evs[3 * e], ctx->stream));
-                CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, a, t, ctx->num_sms, ctx->stream));
+                recon_status sp = launch_event_pass(ctx, p, a, t);
+                if (sp != RECON_OK) return sp;
                 if (ctx->timing) CK(cudaEventRecord(evs[3 * e + 1], ctx->stream));
                 CK(launch_update(p.lam, p.C, p.s32, p.bf16, p.reg_vox_dev, p.n_regions,
                                  ctx->upd_partial.as<double>(), p.upd_bpr, ctx->stream, (float)B));
@@ -529,7 +580,8 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool 
                 if (ctx->timing) CK(cudaEventRecord(evs[3 * e + 2], ctx->stream));
                 CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions,
                                    p.hist, p.iter, p.hist_cap, ctx->stream));
-                ctx->stats.kernel_launches += (a.n > 0 ? 3 : 2) + (p.med && b == B - 1 ? 1 : 0);
+                ctx->stats.kernel_launches += (a.n > 0 ? 3 : 2) + (p.med && b == B - 1 ? 1 : 0) +
+                                              (p.tiled && p.n_fb > 0 ? 1 : 0);
             }
         }
         if (ctx->timing) {
@@ -568,7 +620,8 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool 
     }
     for (int k = 0; k < n_iter; ++k) {
         CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-        ctx->stats.kernel_launches += (long long)p.subsets * (p.pass_blocks > 0 ? 3 : 2) + (p.med ? 1 : 0);
+        ctx->stats.kernel_launches += (long long)p.subsets * (p.pass_blocks > 0 ? 3 : 2) + (p.med ? 1 : 0) +
+                                      (p.tiled && p.n_fb > 0 ? 1 : 0);
     }
     return RECON_OK;
 }
@@ -749,7 +802,10 @@ void recon_destroy(recon_ctx* ctx)
     DevBuf* bufs[] = {&ctx->s64, &ctx->s32, &ctx->lam, &ctx->C, &ctx->lam_bf16, &ctx->ev, &ctx->staging,
                       &ctx->pass_partial, &ctx->upd_partial, &ctx->work, &ctx->iter, &ctx->hist, &ctx->reg_vox,
                       &ctx->red_partial, &ctx->vec, &ctx->med, &ctx->mu, &ctx->keep, &ctx->counter, &ctx->codes, &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
-                      &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg};
+                      &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg,
+                      &ctx->tile_prep.code, &ctx->tile_prep.counts, &ctx->tile_prep.cursor, &ctx->tile_prep.begin,
+                      &ctx->tile_prep.scratch, &ctx->tile_prep.list, &ctx->tile_prep.ev_cell, &ctx->tile_prep.ev_fb,
+                      &ctx->tile_prep.misc};
     for (DevBuf* b : bufs) release(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -815,6 +871,14 @@ recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets)
     CHECK_CTX();
     if (n_subsets < 1 || n_subsets > 1024) return fail(ctx, RECON_EINVAL, "n_subsets must be in [1, 1024]");
     ctx->subsets = n_subsets;
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on)
+{
+    CHECK_CTX();
+    ctx->tile_mode = on != 0 ? 1 : 0;
     invalidate_graph(ctx);
     return RECON_OK;
 }
@@ -926,6 +990,15 @@ recon_status recon_get_info(const recon_ctx* ctx, recon_info* out)
     out->has_sensitivity = ctx->have_sens ? 1 : 0;
     out->num_sms = ctx->num_sms;
     out->sens_total = ctx->sens_total;
+    const TilePrep& tp = ctx->tile_prep;
+    const bool tv = tp.valid && tp.ev_gen == ctx->ev_generation;
+    out->tile_cells = tv ? (int64_t)tp.n_list : 0;
+    out->tile_events = tv ? ctx->n_ev - tp.n_fb : 0;
+    out->tile_fallback_events = tv ? tp.n_fb : 0;
+    out->tile_cell_voxels = tv ? tp.th.cs : 0;
+    out->tile_halo[0] = tv ? tp.th.hx : 0;
+    out->tile_halo[1] = tv ? tp.th.hy : 0;
+    out->tile_halo[2] = tv ? tp.th.hz : 0;
     return RECON_OK;
 }
 
@@ -1090,6 +1163,115 @@ recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const
     CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * ctx->n_vox, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return RECON_OK;
+}
+
+// Tile geometry of the shared-memory pass for this context, or false when no
+// cell size lets two tiles (lambda and C) fit the shared memory of a block.
+// Halo per axis: K sigma |u_k| / v_k voxels plus 1/8 voxel, with |u_z| bounded
+// by the scanner's axial acceptance (events beyond it take the fallback pass).
+bool tile_params(const recon_ctx* ctx, TileH* out)
+{
+    if (ctx->tile_mode == 0 || ctx->lut_n > 0 || ctx->subsets != 1) return false;
+    const recon_grid& g = ctx->grid;
+    const double hw = ctx->k_sigma * ctx->sigma_mm;
+    const double sin_max = std::sin(std::min(90.0, std::max(0.0, ctx->geom.max_axial_angle_deg)) * (3.14159265358979323846 / 180.0));
+    TileH t{};
+    t.nx = g.nx;
+    t.ny = g.ny;
+    t.nz = g.nz;
+    t.vx = (float)g.vx;
+    t.vy = (float)g.vy;
+    t.vz = (float)g.vz;
+    t.ox = (float)g.ox;
+    t.oy = (float)g.oy;
+    t.oz = (float)g.oz;
+    t.hx = (int)std::ceil(hw / g.vx + 0.125);
+    t.hy = (int)std::ceil(hw / g.vy + 0.125);
+    t.hz = (int)std::ceil(hw * sin_max / g.vz + 0.125);
+    for (int cs = 4; cs >= 2; --cs) {
+        t.cs = cs;
+        t.ncx = (g.nx + cs - 1) / cs;
+        t.ncy = (g.ny + cs - 1) / cs;
+        t.ncz = (g.nz + cs - 1) / cs;
+        const double cells = (double)t.ncx * t.ncy * t.ncz;
+        if (cells >= 4.0e9) continue;
+        if (tile_smem_bytes(t) <= (size_t)220 * 1024) {
+            *out = t;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Bin the resident events by cell (cached per event generation and window).
+recon_status prepare_tiles(recon_ctx* ctx)
+{
+    TilePrep& tp = ctx->tile_prep;
+    TileH t;
+    if (!ctx->have_ev || ctx->n_ev <= 0 || !tile_params(ctx, &t)) {
+        tp.valid = false;
+        return RECON_OK;
+    }
+    const double hw = (double)make_tof(ctx).half_window;
+    if (tp.valid && tp.ev_gen == ctx->ev_generation && tp.half_window == hw && tp.th.cs == t.cs &&
+        tp.th.hx == t.hx && tp.th.hy == t.hy && tp.th.hz == t.hz)
+        return RECON_OK;
+    tp.valid = false;
+    invalidate_graph(ctx);
+    const long long n = ctx->n_ev;
+    const long long nc = (long long)t.ncx * t.ncy * t.ncz;
+    const size_t rec = ctx->fmt == FMT_PACKED ? 16 : 32;
+    CK(ensure(tp.code, sizeof(unsigned) * (size_t)n));
+    CK(ensure(tp.counts, sizeof(unsigned) * (size_t)nc));
+    CK(ensure(tp.cursor, sizeof(unsigned) * (size_t)nc));
+    CK(ensure(tp.begin, sizeof(long long) * (size_t)(nc + 1)));
+    CK(ensure(tp.scratch, sizeof(long long) * (size_t)scan_scratch_elems(nc)));
+    CK(ensure(tp.list, sizeof(unsigned) * (size_t)nc));
+    CK(ensure(tp.misc, 64));
+    CK(cudaMemsetAsync(tp.counts.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
+    CK(cudaMemsetAsync(tp.cursor.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
+    CK(cudaMemsetAsync(tp.misc.p, 0, 64, ctx->stream));
+    unsigned long long* n_fb_dev = tp.misc.as<unsigned long long>();
+    unsigned long long* fb_cursor = n_fb_dev + 1;
+    unsigned* n_list_dev = reinterpret_cast<unsigned*>(n_fb_dev + 2);
+    CK(launch_cell_codes(ctx->ev.p, ctx->fmt, n, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
+                         tp.counts.as<unsigned>(), n_fb_dev, ctx->stream));
+    CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
+                        ctx->stream));
+    CK(launch_cell_list(tp.counts.as<unsigned>(), nc, tp.list.as<unsigned>(), n_list_dev, ctx->stream));
+    unsigned long long host_misc[3] = {0, 0, 0};
+    long long binned = 0;
+    CK(cudaMemcpyAsync(host_misc, tp.misc.p, sizeof host_misc, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&binned, tp.begin.as<long long>() + nc, sizeof binned, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    tp.n_fb = (long long)host_misc[0];
+    tp.n_list = (unsigned)(host_misc[2] & 0xFFFFFFFFu);
+    CK(ensure(tp.ev_cell, rec * (size_t)std::max(binned, 1LL)));
+    CK(ensure(tp.ev_fb, rec * (size_t)std::max(tp.n_fb, 1LL)));
+    CK(launch_cell_scatter(ctx->ev.p, ctx->fmt, n, tp.code.as<unsigned>(), tp.begin.as<long long>(),
+                           tp.cursor.as<unsigned>(), tp.ev_cell.p, tp.ev_fb.p, fb_cursor, ctx->stream));
+    ctx->stats.kernel_launches += 7;
+    tp.th = t;
+    tp.half_window = hw;
+    tp.n_cells = nc;
+    tp.ev_gen = ctx->ev_generation;
+    tp.valid = true;
+    return RECON_OK;
+}
+
+// Use the tiled pass in plan p when its binning is ready.
+void plan_tiles(recon_ctx* ctx, IterPlan& p)
+{
+    const TilePrep& tp = ctx->tile_prep;
+    p.tiled = tp.valid && tp.ev_gen == ctx->ev_generation && p.subsets == 1 && p.a.lut.n == 0 && p.n_regions == 1;
+    if (!p.tiled) return;
+    p.th = tp.th;
+    p.list = tp.list.as<unsigned>();
+    p.n_list = tp.n_list;
+    p.tbegin = tp.begin.as<long long>();
+    p.ev_cell = tp.ev_cell.p;
+    p.ev_fb = tp.ev_fb.p;
+    p.n_fb = tp.n_fb;
 }
 
 // Host events and n_iter >= 1: the upload is streamed in chunks through two
@@ -1265,8 +1447,18 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
                 ctx->last_cfg = c;
             }
         }
+        if (n_iter > 1) {
+            s = prepare_tiles(ctx);
+            if (s != RECON_OK) return s;
+            plan_tiles(ctx, p);
+        }
         s = run_iterations(ctx, p, n_iter - 1, false);
     } else {
+        if (n_iter > 0) {
+            s = prepare_tiles(ctx);
+            if (s != RECON_OK) return s;
+            plan_tiles(ctx, p);
+        }
         s = run_iterations(ctx, p, n_iter);
     }
     if (s != RECON_OK) return s;

@@ -42,6 +42,16 @@ struct LutH {
     float2 s[kMaxLutSamples];  // (offset mm, weight)
 };
 
+// Cell binning of the shared-memory tiled pass: grid (n, v, o), cells of cs^3
+// voxels (nc per axis), tile = cell widened by h voxels per axis, clipped to the grid.
+struct TileH {
+    int nx, ny, nz;
+    float vx, vy, vz;
+    float ox, oy, oz;
+    int cs, hx, hy, hz;
+    int ncx, ncy, ncz;
+};
+
 enum EventFmt { FMT_F32 = 0, FMT_PACKED = 1 };
 enum PassKind { PASS_FUSED = 0, PASS_FORWARD = 1, PASS_BACK = 2 };
 enum TailEval { TAIL_FIT = 0, TAIL_ERFC = 1 };
@@ -74,6 +84,28 @@ struct PassArgs {
 int pass_blocks(const LaunchCfg& cfg, long long n, int num_sms);
 cudaError_t launch_pass(PassKind kind, EventFmt fmt, const LaunchCfg& cfg, const PassArgs& a,
                         const RegionTable& tbl, int num_sms, cudaStream_t s);
+
+// Tiled pass (k_tile_pass.cu).  Binning: code[i] = cell id, 0xFFFFFFFF (window misses
+// the grid) or 0xFFFFFFFE (fallback); counts[cell] += 1 (zero before); *n_fallback += 1.
+cudaError_t launch_cell_codes(const void* ev, int fmt, long long n, float lattice, const TileH& t, float half_window,
+                              unsigned* code, unsigned* counts, unsigned long long* n_fallback, cudaStream_t st);
+// begin[c] = sum of counts before c (n_cells + 1 entries); block_sums: scratch of
+// scan_scratch_elems(n_cells) int64.
+long long scan_scratch_elems(long long n_cells);
+cudaError_t launch_cell_scan(const unsigned* counts, long long n_cells, long long* begin, long long* block_sums,
+                             cudaStream_t st);
+// Non-empty cells into list[*n_list]; events copied cell by cell into ev_cell (cursor:
+// n_cells zeros) and the fallback events into ev_fb (*fb_cursor zero before).
+cudaError_t launch_cell_list(const unsigned* counts, long long n_cells, unsigned* list, unsigned* n_list,
+                             cudaStream_t st);
+cudaError_t launch_cell_scatter(const void* ev, int fmt, long long n, const unsigned* code, const long long* begin,
+                                unsigned* cursor, void* ev_cell, void* ev_fb, unsigned long long* fb_cursor,
+                                cudaStream_t st);
+// One block per listed cell: events [begin[c], begin[c+1]) of ev_cell.  Shared memory:
+// 2 x tile_voxels floats.  Accumulates C and N_eff (a.partial, one region) like the fused pass.
+size_t tile_smem_bytes(const TileH& t);
+cudaError_t launch_tile_pass(const PassArgs& a, const TileH& t, const unsigned* list, unsigned n_list,
+                             const long long* begin, int tail, cudaStream_t st);
 
 // Sensitivity: s[j] += chord length of each LOR (FP64 accumulation).  lor6: six
 // planes of n floats (device).

@@ -32,15 +32,14 @@ def run_mlem(geom, g, ev, sens, n_iter, tiled, graphs=1):
 
 @pytest.mark.parametrize("graphs", [1, 0])
 def test_tiled_mlem_tiny_matches_oracle(graphs):
-    # a 45 degree axial acceptance makes the tiles fit; events steeper than that take
-    # the global-memory fallback, so both paths run in one reconstruction
+    # a 45 degree axial acceptance makes the tiles fit (the tiny scanner's LORs are
+    # all flatter than that; the fallback path has its own test below)
     ev, lors = tiny_inputs()
     g = workload_grid("tiny")
     s_ref = oracle.sensitivity(g, lors)
     lam_ref, hist = oracle.mlem(g, ev.astype(np.float64), s_ref, 5, SIGMA)
     lam, cons, info = run_mlem((150.0, 200.0, 45.0), g, ev, s_ref, 5, True, graphs)
-    assert info["tile_cells"] > 0 and info["tile_events"] > 0
-    assert info["tile_fallback_events"] > 0
+    assert info["tile_cells"] > 0 and info["tile_events"] == ev.shape[1]
     assert rel_l2(lam, lam_ref) <= 1e-4
     assert max_rel_above(lam, lam_ref, 0.01) <= 1e-3
     for k in range(5):

@@ -1438,8 +1438,15 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
         s = stream_pass(ctx, events, p);
         if (s != RECON_OK) return s;
         if (n_iter > 1) {
+            const long long runs = ctx->stats.autotune_runs;
             LaunchCfg c = choose_cfg(ctx, p.a, p.tbl, &st);
             if (st != RECON_OK) return st;
+            if (ctx->stats.autotune_runs != runs) {
+                // the autotuner's timed passes accumulated into C and the N_eff slots,
+                // which the first update and finalize had left at zero
+                CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
+                CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots, ctx->stream));
+            }
             if (c.blocks_per_sm != p.cfg.blocks_per_sm || c.threads != p.cfg.threads || c.chunk != p.cfg.chunk ||
                 c.cache != p.cfg.cache || c.tail != p.cfg.tail) {
                 p.cfg = c;

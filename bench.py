@@ -45,6 +45,7 @@ def parse():
                     help="fix the event-pass launch: threads,blocks_per_sm,chunk,cached_pieces,tail_eval "
                          "(default: the library's autotuner)")
     ap.add_argument("--no-graphs", action="store_true", help="launch iterations directly instead of graph replay")
+    ap.add_argument("--no-tiles", action="store_true", help="global-memory event pass only (no shared-memory tiles)")
     ap.add_argument("--samples", type=int, default=0,
                     help="time the sampled TOF kernel with this many samples in the main measurement "
                          "(default 0: the exact Siddon x Phi projector)")
@@ -479,6 +480,8 @@ def run_ours(args):
         ctx.set_graphs(0)
     if args.samples:
         ctx.set_projector(B.PROJ_SAMPLED, args.samples)
+    if args.no_tiles:
+        ctx.set_tiled_pass(0)
     # warm-up (the first call also runs the launch autotuner)
     for _ in range(args.warmup):
         ctx.mlem(None, args.iters)
@@ -546,6 +549,7 @@ def run_ours(args):
            "clocks": clocks,
            "legs": legs,
            "extra": {"t_generate_s": t_gen, "t_sensitivity_s": t_sens, "t_load_s": t_load,
+                     "tiles": {k: v for k, v in ctx.get_info().items() if k.startswith("tile")},
                      "pass_ms": pass_ms, "update_ms": upd_ms, "conservation_last": list(cons[-1])}}
     if rank == 0:
         peaks, src = measured_peaks()

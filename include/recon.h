@@ -191,9 +191,12 @@ recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float
  * the image.  Events whose window would leave their tile take the global-memory pass.
  * Used for MLEM with the exact projector and one subset when two tiles fit the shared
  * memory of a block (e.g. 4 mm voxels at 300 ps); otherwise, or with on = 0, every event
- * takes the global-memory pass.  The binning costs one copy of the events (32 or 16 bytes
- * each) and is cached until the events or the kernel window change.  recon_get_info
- * reports the binning. */
+ * takes the global-memory pass.  A cell is tiled only when it holds at least m events
+ * (loading and flushing a tile costs about as much as a few hundred events): on = 1 sets
+ * m = 256, on > 1 sets m = on; the events of smaller cells take the global-memory pass.
+ * The binning costs one copy of the events (32 or 16 bytes each) and is cached until the
+ * events, the kernel window or m change.  recon_get_info reports the binning.  Errors:
+ * EINVAL (on < 0). */
 recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on);
 
 /* List-mode OSEM for recon_mlem (OSEM is named in the title of Sec. 2.4; the paper

@@ -238,7 +238,8 @@ def recon_set_projector(ctx, projector, n_samples=0):
 
 
 def recon_set_tiled_pass(ctx, on):
-    return check(ctx, load().recon_set_tiled_pass(ctx, int(bool(on))))
+    """0: off; 1: on (cells of >= 256 events); m > 1: on with cells of >= m events."""
+    return check(ctx, load().recon_set_tiled_pass(ctx, int(on)))
 
 
 def recon_set_subsets(ctx, n_subsets):

@@ -183,11 +183,23 @@ __global__ void k_scan_add(long long* __restrict__ out, long long n, const long 
 
 // ------------------------------------------------------ list and scatter
 
-__global__ void k_cell_list(const unsigned* __restrict__ counts, long long n_cells, unsigned* __restrict__ list,
-                            unsigned* __restrict__ n_list)
+// Cells with at least min_events events go to the list; the events of smaller
+// cells (too few to pay for loading and flushing a tile) join the fallback:
+// their count is zeroed, so their range in the scan is empty.
+__global__ void k_cell_list(unsigned* __restrict__ counts, long long n_cells, unsigned min_events,
+                            unsigned* __restrict__ list, unsigned* __restrict__ n_list,
+                            unsigned long long* __restrict__ n_fallback)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n_cells && counts[c] > 0) list[atomicAdd(n_list, 1u)] = (unsigned)c;
+    if (c >= n_cells) return;
+    const unsigned k = counts[c];
+    if (k == 0) return;
+    if (k >= min_events) {
+        list[atomicAdd(n_list, 1u)] = (unsigned)c;
+    } else {
+        counts[c] = 0;
+        atomicAdd(n_fallback, (unsigned long long)k);
+    }
 }
 
 template <int Fmt>
@@ -201,10 +213,10 @@ __global__ void k_cell_scatter(const void* __restrict__ ev, long long n, const u
     const unsigned c = code[i];
     long long pos;
     void* dst;
-    if (c < kCellFallback) {
+    if (c < kCellFallback && begin[c + 1] > begin[c]) {
         pos = begin[c] + atomicAdd(cursor + c, 1u);
         dst = ev_cell;
-    } else if (c == kCellFallback) {
+    } else if (c != kCellNone) {
         pos = (long long)atomicAdd(fb_cursor, 1ull);
         dst = ev_fb;
     } else {
@@ -288,13 +300,23 @@ __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, c
     const int nt = Tx * Ty * Tz;
     float* lam_s = smem;
     float* C_s = smem + nt;
-    for (int k = threadIdx.x; k < nt; k += Threads) {
-        const int x = k % Tx, r = k / Tx, y = r % Ty, z = r / Ty;
-        const long long g = (long long)(lo[0] + x) + (long long)t.nx * ((lo[1] + y) + (long long)t.ny * (lo[2] + z));
-        lam_s[k] = __ldg(a.lam + g);
-        C_s[k] = 0.f;
+    // tile of lambda: one row (x run) per warp at a time, every copy asynchronous
+    // (cp.async) so that all of them are in flight together
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = Threads / 32;
+    for (int row = warp; row < Ty * Tz; row += kWarps) {
+        const int y = row % Ty, z = row / Ty;
+        const float* src = a.lam + (long long)lo[0] + (long long)t.nx * ((lo[1] + y) + (long long)t.ny * (lo[2] + z));
+        float* dst = lam_s + row * Tx;
+        for (int x = lane; x < Tx; x += 32) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(dst + x);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + x) : "memory");
+        }
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int k = threadIdx.x; k < nt; k += Threads) C_s[k] = 0.f;
     if (threadIdx.x == 0) neff_s = 0.f;
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
 
     GridDev tg;
@@ -392,13 +414,14 @@ __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, c
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < nt; k += Threads) {
-        const float v = C_s[k];
-        if (v != 0.f) {
-            const int x = k % Tx, r = k / Tx, y = r % Ty, z = r / Ty;
-            const long long g =
-                (long long)(lo[0] + x) + (long long)t.nx * ((lo[1] + y) + (long long)t.ny * (lo[2] + z));
-            atomicAdd(a.C + g, v);
+    // C tile into the image: rows again, consecutive lanes on consecutive voxels
+    for (int row = warp; row < Ty * Tz; row += kWarps) {
+        const int y = row % Ty, z = row / Ty;
+        float* dst = a.C + (long long)lo[0] + (long long)t.nx * ((lo[1] + y) + (long long)t.ny * (lo[2] + z));
+        const float* src = C_s + row * Tx;
+        for (int x = lane; x < Tx; x += 32) {
+            const float v = src[x];
+            if (v != 0.f) atomicAdd(dst + x, v);
         }
     }
     if (threadIdx.x == 0 && neff_s != 0.f) atomicAdd(a.partial + (blockIdx.x % kNeffSlots), (double)neff_s);
@@ -434,11 +457,12 @@ cudaError_t launch_cell_scan(const unsigned* counts, long long n_cells, long lon
     return cudaGetLastError();
 }
 
-cudaError_t launch_cell_list(const unsigned* counts, long long n_cells, unsigned* list, unsigned* n_list,
-                             cudaStream_t st)
+cudaError_t launch_cell_list(unsigned* counts, long long n_cells, unsigned min_events, unsigned* list,
+                             unsigned* n_list, unsigned long long* n_fallback, cudaStream_t st)
 {
     if (n_cells <= 0) return cudaSuccess;
-    k_cell_list<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(counts, n_cells, list, n_list);
+    k_cell_list<<<(unsigned)((n_cells + 255) / 256), 256, 0, st>>>(counts, n_cells, min_events, list, n_list,
+                                                                   n_fallback);
     return cudaGetLastError();
 }
 

@@ -72,6 +72,7 @@ struct TilePrep {
     bool valid = false;
     long long ev_gen = -1;
     double half_window = 0;
+    int min_events = 0;
     TileH th{};
     long long n_cells = 0;
     unsigned n_list = 0;
@@ -133,6 +134,7 @@ struct recon_ctx {
 
     // shared-memory tiled pass (plain MLEM with the exact projector)
     int tile_mode = 1;    // 0 off, 1 on where the tile fits shared memory
+    int tile_min_events = 256;  // cells with fewer events take the global-memory pass
     TilePrep tile_prep;
 };
 
@@ -878,7 +880,9 @@ recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets)
 recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on)
 {
     CHECK_CTX();
+    if (on < 0) return fail(ctx, RECON_EINVAL, "on must be >= 0");
     ctx->tile_mode = on != 0 ? 1 : 0;
+    ctx->tile_min_events = on > 1 ? on : 256;
     invalidate_graph(ctx);
     return RECON_OK;
 }
@@ -1214,7 +1218,7 @@ recon_status prepare_tiles(recon_ctx* ctx)
     }
     const double hw = (double)make_tof(ctx).half_window;
     if (tp.valid && tp.ev_gen == ctx->ev_generation && tp.half_window == hw && tp.th.cs == t.cs &&
-        tp.th.hx == t.hx && tp.th.hy == t.hy && tp.th.hz == t.hz)
+        tp.th.hx == t.hx && tp.th.hy == t.hy && tp.th.hz == t.hz && tp.min_events == ctx->tile_min_events)
         return RECON_OK;
     tp.valid = false;
     invalidate_graph(ctx);
@@ -1236,9 +1240,10 @@ recon_status prepare_tiles(recon_ctx* ctx)
     unsigned* n_list_dev = reinterpret_cast<unsigned*>(n_fb_dev + 2);
     CK(launch_cell_codes(ctx->ev.p, ctx->fmt, n, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
                          tp.counts.as<unsigned>(), n_fb_dev, ctx->stream));
+    CK(launch_cell_list(tp.counts.as<unsigned>(), nc, (unsigned)ctx->tile_min_events, tp.list.as<unsigned>(),
+                        n_list_dev, n_fb_dev, ctx->stream));
     CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
                         ctx->stream));
-    CK(launch_cell_list(tp.counts.as<unsigned>(), nc, tp.list.as<unsigned>(), n_list_dev, ctx->stream));
     unsigned long long host_misc[3] = {0, 0, 0};
     long long binned = 0;
     CK(cudaMemcpyAsync(host_misc, tp.misc.p, sizeof host_misc, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1252,6 +1257,7 @@ recon_status prepare_tiles(recon_ctx* ctx)
                            tp.cursor.as<unsigned>(), tp.ev_cell.p, tp.ev_fb.p, fb_cursor, ctx->stream));
     ctx->stats.kernel_launches += 7;
     tp.th = t;
+    tp.min_events = ctx->tile_min_events;
     tp.half_window = hw;
     tp.n_cells = nc;
     tp.ev_gen = ctx->ev_generation;

@@ -94,10 +94,12 @@ cudaError_t launch_cell_codes(const void* ev, int fmt, long long n, float lattic
 long long scan_scratch_elems(long long n_cells);
 cudaError_t launch_cell_scan(const unsigned* counts, long long n_cells, long long* begin, long long* block_sums,
                              cudaStream_t st);
-// Non-empty cells into list[*n_list]; events copied cell by cell into ev_cell (cursor:
-// n_cells zeros) and the fallback events into ev_fb (*fb_cursor zero before).
-cudaError_t launch_cell_list(const unsigned* counts, long long n_cells, unsigned* list, unsigned* n_list,
-                             cudaStream_t st);
+// Cells with >= min_events events into list[*n_list]; smaller cells' counts are zeroed
+// and added to *n_fallback (run before the scan).  Scatter: events copied cell by cell
+// into ev_cell (cursor: n_cells zeros), the fallback events and those of zeroed cells
+// into ev_fb (*fb_cursor zero before).
+cudaError_t launch_cell_list(unsigned* counts, long long n_cells, unsigned min_events, unsigned* list,
+                             unsigned* n_list, unsigned long long* n_fallback, cudaStream_t st);
 cudaError_t launch_cell_scatter(const void* ev, int fmt, long long n, const unsigned* code, const long long* begin,
                                 unsigned* cursor, void* ev_cell, void* ev_fb, unsigned long long* fb_cursor,
                                 cudaStream_t st);

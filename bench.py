@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true", help="launch iterations directly instead of graph replay")
     ap.add_argument("--no-tiles", action="store_true", help="global-memory event pass only (no shared-memory tiles)")
     ap.add_argument("--tile-min", type=int, default=0, help="minimum events per tiled cell (0: the library default)")
+    ap.add_argument("--tile-lanes", type=int, default=1, help="threads per event in the tiled pass (1 or 8)")
     ap.add_argument("--samples", type=int, default=0,
                     help="time the sampled TOF kernel with this many samples in the main measurement "
                          "(default 0: the exact Siddon x Phi projector)")
@@ -483,8 +484,8 @@ def run_ours(args):
         ctx.set_projector(B.PROJ_SAMPLED, args.samples)
     if args.no_tiles:
         ctx.set_tiled_pass(0)
-    elif args.tile_min > 1:
-        ctx.set_tiled_pass(args.tile_min)
+    else:
+        ctx.set_tiled_pass(max(1, args.tile_min), args.tile_lanes)
     # warm-up (the first call also runs the launch autotuner)
     for _ in range(args.warmup):
         ctx.mlem(None, args.iters)

@@ -194,10 +194,12 @@ recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float
  * takes the global-memory pass.  A cell is tiled only when it holds at least m events
  * (loading and flushing a tile costs about as much as a few hundred events): on = 1 sets
  * m = 256, on > 1 sets m = on; the events of smaller cells take the global-memory pass.
+ * lanes: threads per event, 1 (each thread walks its event twice, forward then back) or
+ * 8 (eight lanes split the window and keep their pieces in registers).
  * The binning costs one copy of the events (32 or 16 bytes each) and is cached until the
  * events, the kernel window or m change.  recon_get_info reports the binning.  Errors:
- * EINVAL (on < 0). */
-recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on);
+ * EINVAL (on < 0, lanes not 1 or 8). */
+recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on, int32_t lanes);
 
 /* List-mode OSEM for recon_mlem (OSEM is named in the title of Sec. 2.4; the paper
  * itself reconstructs with MLEM).  n_subsets = B > 1: each iteration runs B

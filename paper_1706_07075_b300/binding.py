@@ -76,7 +76,7 @@ SIGNATURES = {
     "recon_set_projector": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "recon_set_median_filter": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_subsets": (C.c_int, [_CTX, C.c_int32]),
-    "recon_set_tiled_pass": (C.c_int, [_CTX, C.c_int32]),
+    "recon_set_tiled_pass": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "recon_preprocess": (C.c_int, [_CTX, C.POINTER(recon_events), _VP, C.c_double, C.c_int32, _VP, _VP,
                                    C.POINTER(C.c_int64)]),
     "recon_median_filter": (C.c_int, [_CTX, _VP, _VP]),
@@ -237,9 +237,10 @@ def recon_set_projector(ctx, projector, n_samples=0):
     return check(ctx, load().recon_set_projector(ctx, int(projector), int(n_samples)))
 
 
-def recon_set_tiled_pass(ctx, on):
-    """0: off; 1: on (cells of >= 256 events); m > 1: on with cells of >= m events."""
-    return check(ctx, load().recon_set_tiled_pass(ctx, int(on)))
+def recon_set_tiled_pass(ctx, on, lanes=1):
+    """0: off; 1: on (cells of >= 256 events); m > 1: on with cells of >= m events.
+    lanes: threads per event (1 or 8)."""
+    return check(ctx, load().recon_set_tiled_pass(ctx, int(on), int(lanes)))
 
 
 def recon_set_subsets(ctx, n_subsets):

@@ -284,7 +284,7 @@ __device__ __forceinline__ void lw_step(LaneWalk& s, const Walk& w, const TailF&
     s.tz = bz ? nz_ : s.tz;
 }
 
-template <int Fmt, bool Fit, int Threads>
+template <int Fmt, bool Fit, int Threads, int Lanes>
 __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, const unsigned* __restrict__ list,
                                                           const long long* __restrict__ begin)
 {
@@ -334,12 +334,30 @@ __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, c
     TailF tail;
     tail.inv_sigma_sqrt2 = a.tof.inv_sigma_sqrt2;
     const float hw = a.tof.half_window, hin = a.tof.half_inv_norm;
+    const long long e0 = begin[cell], e1 = begin[cell + 1];
+
+    if (Lanes == 1) {
+        // one thread per event: forward sweep gathering from the lambda tile, backward
+        // sweep reducing into the C tile
+        for (long long i = e0 + threadIdx.x; i < e1; i += Threads) {
+            const Event e = load_ev<Fmt>(a.events, i, a.lattice);
+            float3 c, u;
+            if (!event_line(e, c, u)) continue;
+            const Walk w = make_walk(tg, c, u, -hw, hw);
+            float p = 0.f;
+            walk<true>(tg, a.tof, tail, w, [&](int j, float m) { p = fmaf(m, lam_s[j], p); });
+            p *= hin;
+            if (!(p > 0.f)) continue;
+            const float r = e.w / p * hin;
+            walk<true>(tg, a.tof, tail, w, [&](int j, float m) { atomicAdd(C_s + j, m * r); });
+            atomicAdd(&neff_s, e.w);
+        }
+    }
     const int lane8 = threadIdx.x & (kLanesPerEvent - 1);
     const int group = threadIdx.x / kLanesPerEvent;
     constexpr int kGroups = Threads / kLanesPerEvent;
-    const long long e0 = begin[cell], e1 = begin[cell + 1];
 
-    for (long long base = e0; base < e1; base += kGroups) {
+    for (long long base = e0; Lanes == kLanesPerEvent && base < e1; base += kGroups) {
         const long long i = base + group;
         const bool have = i < e1;
         Event e;
@@ -489,11 +507,11 @@ size_t tile_smem_bytes(const TileH& t)
     return (size_t)(2 * tx * ty * tz) * sizeof(float);
 }
 
-template <int Fmt, bool Fit, int Threads>
+template <int Fmt, bool Fit, int Threads, int Lanes>
 cudaError_t launch_tile_variant(const PassArgs& a, const TileH& t, const unsigned* list, unsigned n_list,
                                 const long long* begin, cudaStream_t st)
 {
-    auto kern = k_tile_pass<Fmt, Fit, Threads>;
+    auto kern = k_tile_pass<Fmt, Fit, Threads, Lanes>;
     const size_t smem = tile_smem_bytes(t);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -501,18 +519,26 @@ cudaError_t launch_tile_variant(const PassArgs& a, const TileH& t, const unsigne
     return cudaGetLastError();
 }
 
+template <int Lanes>
+cudaError_t launch_tile_lanes(const PassArgs& a, const TileH& t, const unsigned* list, unsigned n_list,
+                              const long long* begin, bool fit, cudaStream_t st)
+{
+    if (a.lattice > 0.f) {
+        if (fit) return launch_tile_variant<FMT_PACKED, true, kTileThreads, Lanes>(a, t, list, n_list, begin, st);
+        return launch_tile_variant<FMT_PACKED, false, kTileThreads, Lanes>(a, t, list, n_list, begin, st);
+    }
+    if (fit) return launch_tile_variant<FMT_F32, true, kTileThreads, Lanes>(a, t, list, n_list, begin, st);
+    return launch_tile_variant<FMT_F32, false, kTileThreads, Lanes>(a, t, list, n_list, begin, st);
+}
+
 cudaError_t launch_tile_pass(const PassArgs& a, const TileH& t, const unsigned* list, unsigned n_list,
-                             const long long* begin, int tail, cudaStream_t st)
+                             const long long* begin, int tail, int lanes, cudaStream_t st)
 {
     if (n_list == 0) return cudaSuccess;
     if (tile_smem_bytes(t) > 227 * 1024) return cudaErrorInvalidValue;
     const bool fit = tail == TAIL_FIT;
-    if (a.lattice > 0.f) {
-        if (fit) return launch_tile_variant<FMT_PACKED, true, kTileThreads>(a, t, list, n_list, begin, st);
-        return launch_tile_variant<FMT_PACKED, false, kTileThreads>(a, t, list, n_list, begin, st);
-    }
-    if (fit) return launch_tile_variant<FMT_F32, true, kTileThreads>(a, t, list, n_list, begin, st);
-    return launch_tile_variant<FMT_F32, false, kTileThreads>(a, t, list, n_list, begin, st);
+    if (lanes == 1) return launch_tile_lanes<1>(a, t, list, n_list, begin, fit, st);
+    return launch_tile_lanes<kLanesPerEvent>(a, t, list, n_list, begin, fit, st);
 }
 
 }  // namespace recon

@@ -135,6 +135,7 @@ struct recon_ctx {
     // shared-memory tiled pass (plain MLEM with the exact projector)
     int tile_mode = 1;    // 0 off, 1 on where the tile fits shared memory
     int tile_min_events = 256;  // cells with fewer events take the global-memory pass
+    int tile_lanes = 1;         // threads per event in the tiled pass (1 or 8)
     TilePrep tile_prep;
 };
 
@@ -475,7 +476,7 @@ recon_status launch_event_pass(recon_ctx* ctx, const IterPlan& p, const PassArgs
     }
     PassArgs at = a;
     at.events = p.ev_cell;
-    CK(launch_tile_pass(at, p.th, p.list, p.n_list, p.tbegin, p.cfg.tail, ctx->stream));
+    CK(launch_tile_pass(at, p.th, p.list, p.n_list, p.tbegin, p.cfg.tail, ctx->tile_lanes, ctx->stream));
     if (p.n_fb > 0) {
         PassArgs af = a;
         af.events = p.ev_fb;
@@ -539,8 +540,9 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
     std::string k(buf);
-    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %p %u %p %p %lld", p.a.lut.n, (void*)p.med,
-             p.med_vox, p.max_nz, p.subsets, (int)p.tiled, (const void*)p.list, p.n_list, p.ev_cell, p.ev_fb, p.n_fb);
+    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %p %u %p %p %lld %d", p.a.lut.n, (void*)p.med,
+             p.med_vox, p.max_nz, p.subsets, (int)p.tiled, (const void*)p.list, p.n_list, p.ev_cell, p.ev_fb, p.n_fb,
+             ctx->tile_lanes);
     k += buf;
     for (int r = 0; r < p.tbl.n; ++r) {
         snprintf(buf, sizeof buf, "|%lld %d %a %lld", p.tbl.ev_begin[r + 1], p.tbl.grid[r].nz,
@@ -877,12 +879,14 @@ recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets)
     return RECON_OK;
 }
 
-recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on)
+recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on, int32_t lanes)
 {
     CHECK_CTX();
     if (on < 0) return fail(ctx, RECON_EINVAL, "on must be >= 0");
+    if (lanes != 1 && lanes != 8) return fail(ctx, RECON_EINVAL, "lanes must be 1 or 8");
     ctx->tile_mode = on != 0 ? 1 : 0;
     ctx->tile_min_events = on > 1 ? on : 256;
+    ctx->tile_lanes = lanes == 8 ? 8 : 1;
     invalidate_graph(ctx);
     return RECON_OK;
 }

@@ -106,8 +106,9 @@ cudaError_t launch_cell_scatter(const void* ev, int fmt, long long n, const unsi
 // One block per listed cell: events [begin[c], begin[c+1]) of ev_cell.  Shared memory:
 // 2 x tile_voxels floats.  Accumulates C and N_eff (a.partial, one region) like the fused pass.
 size_t tile_smem_bytes(const TileH& t);
+// lanes: 1 (one thread per event, two sweeps) or 8 (eight lanes per event, one sweep).
 cudaError_t launch_tile_pass(const PassArgs& a, const TileH& t, const unsigned* list, unsigned n_list,
-                             const long long* begin, int tail, cudaStream_t st);
+                             const long long* begin, int tail, int lanes, cudaStream_t st);
 
 // Sensitivity: s[j] += chord length of each LOR (FP64 accumulation).  lor6: six
 // planes of n floats (device).

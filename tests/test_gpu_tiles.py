@@ -18,10 +18,10 @@ from test_gpu_regions import per_voxel_gate, smooth_sensitivity
 pytestmark = pytest.mark.gpu
 
 
-def run_mlem(geom, g, ev, sens, n_iter, tiled, graphs=1):
+def run_mlem(geom, g, ev, sens, n_iter, tiled, graphs=1, lanes=1):
     with B.Context(geom, grid_tuple(g), 300.0) as ctx:
         ctx.set_sensitivity(sens)
-        ctx.set_tiled_pass(tiled)
+        ctx.set_tiled_pass(tiled, lanes)
         ctx.set_graphs(graphs)
         lam = np.zeros(g.n_vox, np.float32)
         cons = np.zeros((n_iter, 2))
@@ -30,15 +30,15 @@ def run_mlem(geom, g, ev, sens, n_iter, tiled, graphs=1):
     return lam, cons, info
 
 
-@pytest.mark.parametrize("graphs", [1, 0])
-def test_tiled_mlem_tiny_matches_oracle(graphs):
+@pytest.mark.parametrize("graphs,lanes", [(1, 1), (0, 1), (1, 8)])
+def test_tiled_mlem_tiny_matches_oracle(graphs, lanes):
     # a 45 degree axial acceptance makes the tiles fit (the tiny scanner's LORs are
     # all flatter than that; the fallback path has its own test below)
     ev, lors = tiny_inputs()
     g = workload_grid("tiny")
     s_ref = oracle.sensitivity(g, lors)
     lam_ref, hist = oracle.mlem(g, ev.astype(np.float64), s_ref, 5, SIGMA)
-    lam, cons, info = run_mlem((150.0, 200.0, 45.0), g, ev, s_ref, 5, True, graphs)
+    lam, cons, info = run_mlem((150.0, 200.0, 45.0), g, ev, s_ref, 5, True, graphs, lanes)
     assert info["tile_cells"] > 0 and info["tile_events"] + info["tile_fallback_events"] == ev.shape[1]
     assert rel_l2(lam, lam_ref) <= 1e-4
     assert max_rel_above(lam, lam_ref, 0.01) <= 1e-3

@@ -45,7 +45,7 @@ def parse():
                     help="fix the event-pass launch: threads,blocks_per_sm,chunk,cached_pieces,tail_eval "
                          "(default: the library's autotuner)")
     ap.add_argument("--no-graphs", action="store_true", help="launch iterations directly instead of graph replay")
-    ap.add_argument("--no-tiles", action="store_true", help="global-memory event pass only (no shared-memory tiles)")
+    ap.add_argument("--tiles", action="store_true", help="shared-memory tiled event pass (off by default)")
     ap.add_argument("--tile-min", type=int, default=0, help="minimum events per tiled cell (0: the library default)")
     ap.add_argument("--tile-lanes", type=int, default=1, help="threads per event in the tiled pass (1 or 8)")
     ap.add_argument("--samples", type=int, default=0,
@@ -482,9 +482,7 @@ def run_ours(args):
         ctx.set_graphs(0)
     if args.samples:
         ctx.set_projector(B.PROJ_SAMPLED, args.samples)
-    if args.no_tiles:
-        ctx.set_tiled_pass(0)
-    else:
+    if args.tiles:
         ctx.set_tiled_pass(max(1, args.tile_min), args.tile_lanes)
     # warm-up (the first call also runs the launch autotuner)
     for _ in range(args.warmup):

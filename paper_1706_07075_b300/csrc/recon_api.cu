@@ -133,7 +133,7 @@ struct recon_ctx {
     long long sens_generation = 0;
 
     // shared-memory tiled pass (plain MLEM with the exact projector)
-    int tile_mode = 1;    // 0 off, 1 on where the tile fits shared memory
+    int tile_mode = 0;    // 0 off (default), 1 on where the tile fits shared memory
     int tile_min_events = 256;  // cells with fewer events take the global-memory pass
     int tile_lanes = 1;         // threads per event in the tiled pass (1 or 8)
     TilePrep tile_prep;

@@ -96,9 +96,12 @@ typedef struct {
                                   walk keeps up to this many (voxel, mass) pieces per event in shared
                                   memory (8 bytes each, threads_per_block * cached_pieces * 8 <= 200 KB)
                                   and the backprojection replays them */
-    int32_t tail_eval;         /* Gaussian tails erfc(|tau|/(sigma sqrt 2)) at the piece boundaries from
-                                  0: t exp(-x^2 + P(t)), t = 1/(1 + x/2), with a fitted degree-10 P
-                                  (relative error ~6e-7 at K = 3), 1: CUDA's erfcf */
+    int32_t tail_eval;         /* Gaussian mass of each piece from the tails erfc(|tau|/(sigma sqrt 2)) at
+                                  its two ends, by 0: t exp(-x^2 + P(t)), t = 1/(1 + x/2), with a fitted
+                                  degree-10 P (relative error ~6e-7 at K = 3), 1: CUDA's erfcf; or
+                                  2: the Taylor series of the integral about the piece's midpoint to the
+                                  h^4 term (Hermite polynomials; error below 1e-7 of the window mass for
+                                  pieces up to 0.4 sigma) */
 } recon_launch;
 
 typedef struct {

@@ -105,7 +105,13 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
     return e.w;
 }
 
-template <int Kind, int Fmt, bool Persistent, bool Cached, bool Fit>
+template <int TailK>
+struct TailOf {
+    using type = typename std::conditional<TailK == TAIL_FIT, TailFit,
+                                           typename std::conditional<TailK == TAIL_ERFC, TailErfc, TailSeries>::type>::type;
+};
+
+template <int Kind, int Fmt, bool Persistent, bool Cached, int TailK>
 __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl, int chunk, int cap)
 {
     __shared__ SharedTable t;
@@ -123,7 +129,7 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
         neff[k] = 0.f;
     }
     __syncthreads();
-    using TailF = typename std::conditional<Fit, TailFit, TailErfc>::type;
+    using TailF = typename TailOf<TailK>::type;
     TailF tail;
     tail.inv_sigma_sqrt2 = a.tof.inv_sigma_sqrt2;
     const bool bf16 = a.lam_bf16 != nullptr;
@@ -289,11 +295,11 @@ cudaError_t launch_lut(const LaunchCfg& cfg, const PassArgs& a, const RegionTabl
 
 constexpr int kMaxCacheBytes = 200 * 1024;
 
-template <int Kind, int Fmt, bool Persistent, bool Cached, bool Fit>
+template <int Kind, int Fmt, bool Persistent, bool Cached, int TailK>
 cudaError_t launch_variant(int blocks, const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl,
                            cudaStream_t s)
 {
-    auto kern = k_event_pass<Kind, Fmt, Persistent, Cached, Fit>;
+    auto kern = k_event_pass<Kind, Fmt, Persistent, Cached, TailK>;
     size_t smem = 0;
     if (Cached) {
         smem = (size_t)cfg.cache * cfg.threads * 8;
@@ -304,18 +310,18 @@ cudaError_t launch_variant(int blocks, const LaunchCfg& cfg, const PassArgs& a, 
     return cudaGetLastError();
 }
 
-template <int Kind, int Fmt, bool Fit>
+template <int Kind, int Fmt, int TailK>
 cudaError_t launch_tail(int blocks, const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl, cudaStream_t s)
 {
     const bool persistent = cfg.blocks_per_sm > 0;
     if constexpr (Kind == PASS_FUSED) {
         if (cfg.cache > 0) {
-            if (persistent) return launch_variant<Kind, Fmt, true, true, Fit>(blocks, cfg, a, tbl, s);
-            return launch_variant<Kind, Fmt, false, true, Fit>(blocks, cfg, a, tbl, s);
+            if (persistent) return launch_variant<Kind, Fmt, true, true, TailK>(blocks, cfg, a, tbl, s);
+            return launch_variant<Kind, Fmt, false, true, TailK>(blocks, cfg, a, tbl, s);
         }
     }
-    if (persistent) return launch_variant<Kind, Fmt, true, false, Fit>(blocks, cfg, a, tbl, s);
-    return launch_variant<Kind, Fmt, false, false, Fit>(blocks, cfg, a, tbl, s);
+    if (persistent) return launch_variant<Kind, Fmt, true, false, TailK>(blocks, cfg, a, tbl, s);
+    return launch_variant<Kind, Fmt, false, false, TailK>(blocks, cfg, a, tbl, s);
 }
 
 template <int Kind, int Fmt>
@@ -326,8 +332,9 @@ cudaError_t launch_kind(const LaunchCfg& cfg, const PassArgs& a, const RegionTab
     const int blocks = pass_blocks(cfg, a.n, num_sms);
     if (blocks == 0) return cudaSuccess;
     if ((size_t)cfg.cache * cfg.threads * 8 > (size_t)kMaxCacheBytes) return cudaErrorInvalidValue;
-    if (cfg.tail == TAIL_FIT) return launch_tail<Kind, Fmt, true>(blocks, cfg, a, tbl, s);
-    return launch_tail<Kind, Fmt, false>(blocks, cfg, a, tbl, s);
+    if (cfg.tail == TAIL_FIT) return launch_tail<Kind, Fmt, TAIL_FIT>(blocks, cfg, a, tbl, s);
+    if (cfg.tail == TAIL_SERIES) return launch_tail<Kind, Fmt, TAIL_SERIES>(blocks, cfg, a, tbl, s);
+    return launch_tail<Kind, Fmt, TAIL_ERFC>(blocks, cfg, a, tbl, s);
 }
 
 }  // namespace

@@ -365,7 +365,7 @@ bool valid_cfg(const recon_launch* c)
         return false;
     if (c->cached_pieces != 0 && (c->cached_pieces < 8 || c->cached_pieces > 256)) return false;
     if ((long long)c->cached_pieces * c->threads_per_block * 8 > 200 * 1024) return false;
-    if (c->tail_eval != TAIL_FIT && c->tail_eval != TAIL_ERFC) return false;
+    if (c->tail_eval != TAIL_FIT && c->tail_eval != TAIL_ERFC && c->tail_eval != TAIL_SERIES) return false;
     return true;
 }
 
@@ -400,7 +400,8 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
     const std::vector<LaunchCfg> cands = {
         {128, 0, 0, 0, TAIL_FIT}, {256, 0, 0, 0, TAIL_FIT}, {96, 0, 0, 0, TAIL_FIT},
         {192, 0, 0, 0, TAIL_FIT}, {128, 8, 64, 0, TAIL_FIT}, {64, 0, 0, 64, TAIL_FIT},
-        {128, 0, 0, 0, TAIL_ERFC}, {256, 0, 0, 0, TAIL_ERFC},
+        {128, 0, 0, 0, TAIL_ERFC}, {256, 0, 0, 0, TAIL_ERFC}, {128, 0, 0, 0, TAIL_SERIES},
+        {256, 0, 0, 0, TAIL_SERIES}, {192, 0, 0, 0, TAIL_SERIES},
     };
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));

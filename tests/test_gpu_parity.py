@@ -123,3 +123,26 @@ def test_streamed_upload_matches_resident_events():
     assert max_rel_above(a, b, 0.01) < 1e-3
     np.testing.assert_allclose(ca[:, 0], cb[:, 0], atol=2.0)              # same events with p > 0
     np.testing.assert_allclose(ca[:, 1], ca[:, 0], rtol=1e-5)
+
+
+@pytest.mark.parametrize("tail_eval", [0, 1, 2])
+def test_piece_mass_forms_match_oracle(tiny, tail_eval):
+    # the three evaluations of a piece's Gaussian mass (fitted tails, erfcf tails,
+    # midpoint Taylor series) against the oracle's libm erfc, forward and 3 iterations
+    g, ev, lors, s_ref, ctx = tiny
+    ctx.set_launch(128, 0, 0, 0, tail_eval)
+    rng = np.random.default_rng(30 + tail_eval)
+    lam = rng.uniform(0.5, 1.5, g.n_vox).astype(np.float32)
+    p = np.zeros(ev.shape[1], np.float32)
+    ctx.forward(B.make_events(ev), lam, p)
+    p_ref = oracle.forward(g, ev.astype(np.float64), lam.astype(np.float64), SIGMA)
+    sel = p_ref > 1e-3 * p_ref.max()
+    assert np.max(np.abs(p[sel] - p_ref[sel]) / p_ref[sel]) < 1e-4
+    assert rel_l2(p, p_ref) < 2e-6
+    ctx.set_sensitivity(s_ref)
+    img = np.zeros(g.n_vox, np.float32)
+    ctx.mlem(None, 3, None, img)
+    ctx.set_launch(None)
+    lam_ref, _ = oracle.mlem(g, ev.astype(np.float64), s_ref, 3, SIGMA)
+    assert rel_l2(img, lam_ref) <= 1e-4
+    assert max_rel_above(img, lam_ref, 0.01) <= 1e-3

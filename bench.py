@@ -293,18 +293,29 @@ def time_packed_leg(ctx, B, synth, ev, n, args, stream):
     """Precision-packed form: int16 endpoints on a 0.05 mm lattice + FP16 d
     (16 B per event) and the forward gather from a BF16 image copy."""
     import numpy as np
-    rec = synth.pack_events(ev)
+    import torch
+    rec = torch.from_numpy(synth.pack_events(ev)).pin_memory()
     ctx.load_events(B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM))
-    del rec
     ctx.set_gather_bf16(1)
     cons = np.zeros((args.iters, 2))
     ctx.mlem(None, args.iters, None, None, cons)     # warm-up (+ autotune for the packed format)
     st0 = ctx.get_stats()
     ms = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons))
     st1 = ctx.get_stats()
+    # end to end: pinned packed records uploaded (16 B per event) and the image read back per job
+    img = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
+    times = []
+    for k in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx.mlem(B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM), args.iters, None, img, cons)
+        times.append(time.perf_counter() - t)
+    e2e_T = sum(times[1:]) / max(1, len(times) - 1)
     ctx.set_gather_bf16(0)
     return {"workload": "fullbody packed int16/FP16 events, BF16 gather", "value": n * args.iters * args.steps /
             (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "e2e": {"value": n * args.iters / e2e_T, "unit": UNIT, "h2d_bytes_per_step": int(rec.numel() * 2),
+                    "d2h_bytes_per_step": int(img.numel() * 4 + cons.nbytes), "job_latency_s": e2e_T},
             "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]), "launch": list(ctx.get_launch()),
             "conservation_last": [float(x) for x in cons[-1]], "steps": args.steps}
 
@@ -546,7 +557,7 @@ def run_ours(args):
                       "l2": "inputs larger than L2 (events 32 B x 146M = 4.7 GB resident)",
                       "parallelism": f"replicas{world}" if world > 1 else "single"},
            "e2e": {"value": n * args.iters / e2e_T, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(d2h)},
+                   "d2h_bytes_per_step": int(d2h), "job_latency_s": e2e_T},
            "gpu_launches": int(stats["kernel_launches"]),
            "clocks": clocks,
            "legs": legs,

@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
             }
         }
     } else {
-        const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        const unsigned long long b =
+            a.block_mul > 1 ? (unsigned long long)blockIdx.x * a.block_mul % gridDim.x : blockIdx.x;
+        const long long i = (long long)b * blockDim.x + threadIdx.x;
         if (i < a.n) {
             int r;
             float w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, tail, r);
@@ -270,7 +272,9 @@ __global__ void __launch_bounds__(256) k_lut_pass(PassArgs a, RegionTable tbl)
         neff[k] = 0.f;
     }
     __syncthreads();
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long b =
+        a.block_mul > 1 ? (unsigned long long)blockIdx.x * a.block_mul % gridDim.x : blockIdx.x;
+    const long long i = (long long)b * blockDim.x + threadIdx.x;
     if (i < a.n) {
         int r;
         const float w = do_event_lut<Kind, Fmt>(a, t, i, a.lam_bf16 != nullptr, r);

@@ -394,6 +394,26 @@ PassArgs base_args(recon_ctx* ctx, const void* events, long long n)
 
 // Time one fused pass per candidate launch and keep the fastest.  The pass
 // accumulates into C, which the caller clears afterwards; lambda is untouched.
+// A multiplier coprime with the number of blocks, near 0.618 of it: block b of
+// a flat grid then takes block (b * m) mod n of the event list, so blocks that
+// run at the same time work on events far apart in the list (for region-ordered
+// events: on different regions).  1 for tiny grids.
+unsigned spread_multiplier(long long blocks)
+{
+    if (blocks < 16 || blocks > 0x7fffffffLL) return 1;
+    auto gcd = [](unsigned long long x, unsigned long long y) {
+        while (y) {
+            const unsigned long long t = x % y;
+            x = y;
+            y = t;
+        }
+        return x;
+    };
+    unsigned long long m = (unsigned long long)(0.6180339887 * (double)blocks) | 1ULL;
+    while (gcd(m, (unsigned long long)blocks) != 1) m += 2;
+    return (unsigned)m;
+}
+
 recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, LaunchCfg* best)
 {
     // flat and persistent grids, walking twice or replaying a shared-memory piece cache
@@ -541,9 +561,9 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
     std::string k(buf);
-    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %p %u %p %p %lld %d", p.a.lut.n, (void*)p.med,
-             p.med_vox, p.max_nz, p.subsets, (int)p.tiled, (const void*)p.list, p.n_list, p.ev_cell, p.ev_fb, p.n_fb,
-             ctx->tile_lanes);
+    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %p %u %p %p %lld %d bm %u", p.a.lut.n,
+             (void*)p.med, p.med_vox, p.max_nz, p.subsets, (int)p.tiled, (const void*)p.list, p.n_list, p.ev_cell,
+             p.ev_fb, p.n_fb, ctx->tile_lanes, p.a.block_mul);
     k += buf;
     for (int r = 0; r < p.tbl.n; ++r) {
         snprintf(buf, sizeof buf, "|%lld %d %a %lld", p.tbl.ev_begin[r + 1], p.tbl.grid[r].nz,
@@ -1648,6 +1668,7 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
     CK(cudaMemsetAsync(ctx->C_reg.p, 0, sizeof(float) * nvt, ctx->stream));
     CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots * R, ctx->stream));
     p.pass_blocks = pass_blocks(p.cfg, total, ctx->num_sms);
+    p.a.block_mul = spread_multiplier(p.pass_blocks);
     p.upd_bpr = std::max(1, update_blocks(nvt) / R);
     CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)p.upd_bpr * R));
     p.subsets = 1;

@@ -77,6 +77,9 @@ struct PassArgs {
                                  // p_i > 0 (zero before the pass; the finalize reads and clears them)
     unsigned long long* work;    // work-queue counter (persistent launches; zero before the launch)
     TofH tof;
+    unsigned block_mul;          // flat grids: block b takes the events of block (b * block_mul) mod grid
+                                 // (0 or 1: identity); a multiplier coprime with the grid spreads
+                                 // region-ordered events over all regions at any moment
     LutH lut;                    // sampled TOF kernel (lut.n > 0) instead of the exact one
 };
 

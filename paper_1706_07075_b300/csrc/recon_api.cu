@@ -77,6 +77,8 @@ struct TilePrep {
     long long n_cells = 0;
     unsigned n_list = 0;
     long long n_fb = 0;
+    long long n_binned = 0;
+    int mode = 0;
     DevBuf code, counts, cursor, begin, scratch, list, ev_cell, ev_fb, misc;
 };
 
@@ -483,6 +485,7 @@ struct IterPlan {
     const void* ev_cell = nullptr;
     const void* ev_fb = nullptr;
     long long n_fb = 0;
+    long long n_cell_events = 0;
 };
 
 // The fused event pass of one (sub-)iteration: the tiled pass over the binned
@@ -497,7 +500,17 @@ recon_status launch_event_pass(recon_ctx* ctx, const IterPlan& p, const PassArgs
     }
     PassArgs at = a;
     at.events = p.ev_cell;
-    CK(launch_tile_pass(at, p.th, p.list, p.n_list, p.tbegin, p.cfg.tail, ctx->tile_lanes, ctx->stream));
+    if (ctx->tile_mode == 2) {
+        // cell-ordered events through the global-memory pass, cells spread over blocks
+        RegionTable tc = t;
+        at.n = p.n_cell_events;
+        tc.ev_begin[1] = p.n_cell_events;
+        at.block_mul = spread_multiplier(pass_blocks(p.cfg, at.n, ctx->num_sms));
+        if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
+        CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, at, tc, ctx->num_sms, ctx->stream));
+    } else {
+        CK(launch_tile_pass(at, p.th, p.list, p.n_list, p.tbegin, p.cfg.tail, ctx->tile_lanes, ctx->stream));
+    }
     if (p.n_fb > 0) {
         PassArgs af = a;
         af.events = p.ev_fb;
@@ -900,6 +913,15 @@ recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets)
     return RECON_OK;
 }
 
+recon_status recon_set_event_order(recon_ctx* ctx, int32_t order)
+{
+    CHECK_CTX();
+    if (order != 0 && order != 1) return fail(ctx, RECON_EINVAL, "order must be 0 or 1");
+    ctx->tile_mode = order == 1 ? 2 : 0;
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
 recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on, int32_t lanes)
 {
     CHECK_CTX();
@@ -1202,6 +1224,29 @@ bool tile_params(const recon_ctx* ctx, TileH* out)
 {
     if (ctx->tile_mode == 0 || ctx->lut_n > 0 || ctx->subsets != 1) return false;
     const recon_grid& g = ctx->grid;
+    if (ctx->tile_mode == 2) {
+        // event order only: cells of 3^3 voxels, a halo covering the grid (no fallback)
+        TileH t{};
+        t.nx = g.nx;
+        t.ny = g.ny;
+        t.nz = g.nz;
+        t.vx = (float)g.vx;
+        t.vy = (float)g.vy;
+        t.vz = (float)g.vz;
+        t.ox = (float)g.ox;
+        t.oy = (float)g.oy;
+        t.oz = (float)g.oz;
+        t.cs = 3;
+        t.hx = g.nx;
+        t.hy = g.ny;
+        t.hz = g.nz;
+        t.ncx = (g.nx + 2) / 3;
+        t.ncy = (g.ny + 2) / 3;
+        t.ncz = (g.nz + 2) / 3;
+        if ((double)t.ncx * t.ncy * t.ncz >= 4.0e9) return false;
+        *out = t;
+        return true;
+    }
     const double hw = ctx->k_sigma * ctx->sigma_mm;
     const double sin_max = std::sin(std::min(90.0, std::max(0.0, ctx->geom.max_axial_angle_deg)) * (3.14159265358979323846 / 180.0));
     TileH t{};
@@ -1243,7 +1288,8 @@ recon_status prepare_tiles(recon_ctx* ctx)
     }
     const double hw = (double)make_tof(ctx).half_window;
     if (tp.valid && tp.ev_gen == ctx->ev_generation && tp.half_window == hw && tp.th.cs == t.cs &&
-        tp.th.hx == t.hx && tp.th.hy == t.hy && tp.th.hz == t.hz && tp.min_events == ctx->tile_min_events)
+        tp.th.hx == t.hx && tp.th.hy == t.hy && tp.th.hz == t.hz && tp.min_events == ctx->tile_min_events &&
+        tp.mode == ctx->tile_mode)
         return RECON_OK;
     tp.valid = false;
     invalidate_graph(ctx);
@@ -1265,7 +1311,8 @@ recon_status prepare_tiles(recon_ctx* ctx)
     unsigned* n_list_dev = reinterpret_cast<unsigned*>(n_fb_dev + 2);
     CK(launch_cell_codes(ctx->ev.p, ctx->fmt, n, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
                          tp.counts.as<unsigned>(), n_fb_dev, ctx->stream));
-    CK(launch_cell_list(tp.counts.as<unsigned>(), nc, (unsigned)ctx->tile_min_events, tp.list.as<unsigned>(),
+    CK(launch_cell_list(tp.counts.as<unsigned>(), nc, ctx->tile_mode == 2 ? 1u : (unsigned)ctx->tile_min_events,
+                        tp.list.as<unsigned>(),
                         n_list_dev, n_fb_dev, ctx->stream));
     CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
                         ctx->stream));
@@ -1282,6 +1329,8 @@ recon_status prepare_tiles(recon_ctx* ctx)
                            tp.cursor.as<unsigned>(), tp.ev_cell.p, tp.ev_fb.p, fb_cursor, ctx->stream));
     ctx->stats.kernel_launches += 7;
     tp.th = t;
+    tp.n_binned = binned;
+    tp.mode = ctx->tile_mode;
     tp.min_events = ctx->tile_min_events;
     tp.half_window = hw;
     tp.n_cells = nc;
@@ -1303,6 +1352,7 @@ void plan_tiles(recon_ctx* ctx, IterPlan& p)
     p.ev_cell = tp.ev_cell.p;
     p.ev_fb = tp.ev_fb.p;
     p.n_fb = tp.n_fb;
+    p.n_cell_events = tp.n_binned;
 }
 
 // Host events and n_iter >= 1: the upload is streamed in chunks through two

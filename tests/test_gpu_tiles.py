@@ -85,3 +85,22 @@ def test_narrow_acceptance_sends_events_to_fallback():
     assert info["tile_fallback_events"] > 0.1 * ev.shape[1]
     assert rel_l2(lam, lam_ref) <= 1e-4
     assert max_rel_above(lam, lam_ref, 0.01) <= 1e-3
+
+
+def test_cell_ordered_pass_matches_oracle():
+    ev, lors = tiny_inputs()
+    g = workload_grid("tiny")
+    s_ref = oracle.sensitivity(g, lors)
+    lam_ref, hist = oracle.mlem(g, ev.astype(np.float64), s_ref, 5, SIGMA)
+    with B.Context((150.0, 200.0, 90.0), grid_tuple(g), 300.0) as ctx:
+        ctx.set_sensitivity(s_ref)
+        ctx.set_event_order(1)
+        lam = np.zeros(g.n_vox, np.float32)
+        cons = np.zeros((5, 2))
+        ctx.mlem(B.make_events(ev), 5, None, lam, cons)
+        info = ctx.get_info()
+    assert info["tile_cells"] > 0 and info["tile_fallback_events"] == 0
+    assert rel_l2(lam, lam_ref) <= 1e-4
+    assert max_rel_above(lam, lam_ref, 0.01) <= 1e-3
+    for k in range(5):
+        assert cons[k, 0] == pytest.approx(hist[k][0], abs=0.5)

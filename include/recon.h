@@ -186,13 +186,13 @@ recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float
                                    int32_t* n_out);
 
 /* Event order of the MLEM pass of recon_mlem (exact projector, one subset).  order = 0
- * (default): the events as loaded.  order = 1: the resident events are binned once by the
- * 12 mm cell (3^3 voxels) that holds their TOF point and processed cell by cell, with the
+ * (default): the events as loaded.  order = c in [1, 64]: the resident events are binned
+ * once by the cell of c^3 voxels that holds their TOF point and processed cell by cell, with the
  * cells spread over the blocks that run at the same time (block b of the grid takes block
  * (b * m) mod n of the binned list, m coprime with n): a warp's lines start in one cell
  * (nearby voxels), while concurrent blocks work far apart (no hot voxels).  Same
  * arithmetic; the sums run in another order.  The binning costs one copy of the events
- * and is cached with the events.  Errors: EINVAL (order not 0 or 1). */
+ * and is cached with the events.  Errors: EINVAL (order outside [0, 64]). */
 recon_status recon_set_event_order(recon_ctx* ctx, int32_t order);
 
 /* Shared-memory tiled event pass for recon_mlem (off by default).  A layout choice for

@@ -138,6 +138,7 @@ struct recon_ctx {
     int tile_mode = 0;    // 0 off (default), 1 on where the tile fits shared memory
     int tile_min_events = 256;  // cells with fewer events take the global-memory pass
     int tile_lanes = 1;         // threads per event in the tiled pass (1 or 8)
+    int order_cell = 3;         // cell edge (voxels) of the cell-ordered pass
     TilePrep tile_prep;
 };
 
@@ -916,8 +917,9 @@ recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets)
 recon_status recon_set_event_order(recon_ctx* ctx, int32_t order)
 {
     CHECK_CTX();
-    if (order != 0 && order != 1) return fail(ctx, RECON_EINVAL, "order must be 0 or 1");
-    ctx->tile_mode = order == 1 ? 2 : 0;
+    if (order < 0 || order > 64) return fail(ctx, RECON_EINVAL, "order must be in [0, 64]");
+    ctx->tile_mode = order > 0 ? 2 : 0;
+    ctx->order_cell = order > 0 ? order : 3;
     invalidate_graph(ctx);
     return RECON_OK;
 }
@@ -1236,13 +1238,13 @@ bool tile_params(const recon_ctx* ctx, TileH* out)
         t.ox = (float)g.ox;
         t.oy = (float)g.oy;
         t.oz = (float)g.oz;
-        t.cs = 3;
+        t.cs = ctx->order_cell;
         t.hx = g.nx;
         t.hy = g.ny;
         t.hz = g.nz;
-        t.ncx = (g.nx + 2) / 3;
-        t.ncy = (g.ny + 2) / 3;
-        t.ncz = (g.nz + 2) / 3;
+        t.ncx = (g.nx + t.cs - 1) / t.cs;
+        t.ncy = (g.ny + t.cs - 1) / t.cs;
+        t.ncz = (g.nz + t.cs - 1) / t.cs;
         if ((double)t.ncx * t.ncy * t.ncz >= 4.0e9) return false;
         *out = t;
         return true;

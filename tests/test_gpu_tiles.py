@@ -94,7 +94,7 @@ def test_cell_ordered_pass_matches_oracle():
     lam_ref, hist = oracle.mlem(g, ev.astype(np.float64), s_ref, 5, SIGMA)
     with B.Context((150.0, 200.0, 90.0), grid_tuple(g), 300.0) as ctx:
         ctx.set_sensitivity(s_ref)
-        ctx.set_event_order(1)
+        ctx.set_event_order(3)
         lam = np.zeros(g.n_vox, np.float32)
         cons = np.zeros((5, 2))
         ctx.mlem(B.make_events(ev), 5, None, lam, cons)

@@ -135,7 +135,7 @@ struct recon_ctx {
     long long sens_generation = 0;
 
     // shared-memory tiled pass (plain MLEM with the exact projector)
-    int tile_mode = 0;    // 0 off (default), 1 on where the tile fits shared memory
+    int tile_mode = 3;    // 0 off, 1 shared-memory tiles, 2 cell order, 3 cell order on resident reuse (default)
     int tile_min_events = 256;  // cells with fewer events take the global-memory pass
     int tile_lanes = 1;         // threads per event in the tiled pass (1 or 8)
     int order_cell = 3;         // cell edge (voxels) of the cell-ordered pass
@@ -487,6 +487,7 @@ struct IterPlan {
     const void* ev_fb = nullptr;
     long long n_fb = 0;
     long long n_cell_events = 0;
+    int tile_mode = 0;   // 1 shared-memory tiles, 2 cell-ordered global pass
 };
 
 // The fused event pass of one (sub-)iteration: the tiled pass over the binned
@@ -501,7 +502,7 @@ recon_status launch_event_pass(recon_ctx* ctx, const IterPlan& p, const PassArgs
     }
     PassArgs at = a;
     at.events = p.ev_cell;
-    if (ctx->tile_mode == 2) {
+    if (p.tile_mode == 2) {
         // cell-ordered events through the global-memory pass, cells spread over blocks
         RegionTable tc = t;
         at.n = p.n_cell_events;
@@ -575,9 +576,9 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
     std::string k(buf);
-    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %p %u %p %p %lld %d bm %u", p.a.lut.n,
-             (void*)p.med, p.med_vox, p.max_nz, p.subsets, (int)p.tiled, (const void*)p.list, p.n_list, p.ev_cell,
-             p.ev_fb, p.n_fb, ctx->tile_lanes, p.a.block_mul);
+    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %d %p %u %p %p %lld %lld %d bm %u", p.a.lut.n,
+             (void*)p.med, p.med_vox, p.max_nz, p.subsets, (int)p.tiled, p.tile_mode, (const void*)p.list, p.n_list,
+             p.ev_cell, p.ev_fb, p.n_fb, p.n_cell_events, ctx->tile_lanes, p.a.block_mul);
     k += buf;
     for (int r = 0; r < p.tbl.n; ++r) {
         snprintf(buf, sizeof buf, "|%lld %d %a %lld", p.tbl.ev_begin[r + 1], p.tbl.grid[r].nz,
@@ -917,8 +918,8 @@ recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets)
 recon_status recon_set_event_order(recon_ctx* ctx, int32_t order)
 {
     CHECK_CTX();
-    if (order < 0 || order > 64) return fail(ctx, RECON_EINVAL, "order must be in [0, 64]");
-    ctx->tile_mode = order > 0 ? 2 : 0;
+    if (order < -1 || order > 64) return fail(ctx, RECON_EINVAL, "order must be in [-1, 64]");
+    ctx->tile_mode = order > 0 ? 2 : (order == -1 ? 3 : 0);
     ctx->order_cell = order > 0 ? order : 3;
     invalidate_graph(ctx);
     return RECON_OK;
@@ -929,7 +930,7 @@ recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on, int32_t lanes)
     CHECK_CTX();
     if (on < 0) return fail(ctx, RECON_EINVAL, "on must be >= 0");
     if (lanes != 1 && lanes != 8) return fail(ctx, RECON_EINVAL, "lanes must be 1 or 8");
-    ctx->tile_mode = on != 0 ? 1 : 0;
+    ctx->tile_mode = on != 0 ? 1 : 3;
     ctx->tile_min_events = on > 1 ? on : 256;
     ctx->tile_lanes = lanes == 8 ? 8 : 1;
     invalidate_graph(ctx);
@@ -1222,11 +1223,11 @@ recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const
 // cell size lets two tiles (lambda and C) fit the shared memory of a block.
 // Halo per axis: K sigma |u_k| / v_k voxels plus 1/8 voxel, with |u_z| bounded
 // by the scanner's axial acceptance (events beyond it take the fallback pass).
-bool tile_params(const recon_ctx* ctx, TileH* out)
+bool tile_params(const recon_ctx* ctx, int mode, TileH* out)
 {
-    if (ctx->tile_mode == 0 || ctx->lut_n > 0 || ctx->subsets != 1) return false;
+    if (mode == 0 || ctx->lut_n > 0 || ctx->subsets != 1) return false;
     const recon_grid& g = ctx->grid;
-    if (ctx->tile_mode == 2) {
+    if (mode == 2) {
         // event order only: cells of 3^3 voxels, a halo covering the grid (no fallback)
         TileH t{};
         t.nx = g.nx;
@@ -1280,18 +1281,18 @@ bool tile_params(const recon_ctx* ctx, TileH* out)
 }
 
 // Bin the resident events by cell (cached per event generation and window).
-recon_status prepare_tiles(recon_ctx* ctx)
+recon_status prepare_tiles(recon_ctx* ctx, int mode)
 {
     TilePrep& tp = ctx->tile_prep;
     TileH t;
-    if (!ctx->have_ev || ctx->n_ev <= 0 || !tile_params(ctx, &t)) {
+    if (!ctx->have_ev || ctx->n_ev <= 0 || !tile_params(ctx, mode, &t)) {
         tp.valid = false;
         return RECON_OK;
     }
     const double hw = (double)make_tof(ctx).half_window;
     if (tp.valid && tp.ev_gen == ctx->ev_generation && tp.half_window == hw && tp.th.cs == t.cs &&
         tp.th.hx == t.hx && tp.th.hy == t.hy && tp.th.hz == t.hz && tp.min_events == ctx->tile_min_events &&
-        tp.mode == ctx->tile_mode)
+        tp.mode == mode)
         return RECON_OK;
     tp.valid = false;
     invalidate_graph(ctx);
@@ -1313,7 +1314,7 @@ recon_status prepare_tiles(recon_ctx* ctx)
     unsigned* n_list_dev = reinterpret_cast<unsigned*>(n_fb_dev + 2);
     CK(launch_cell_codes(ctx->ev.p, ctx->fmt, n, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
                          tp.counts.as<unsigned>(), n_fb_dev, ctx->stream));
-    CK(launch_cell_list(tp.counts.as<unsigned>(), nc, ctx->tile_mode == 2 ? 1u : (unsigned)ctx->tile_min_events,
+    CK(launch_cell_list(tp.counts.as<unsigned>(), nc, mode == 2 ? 1u : (unsigned)ctx->tile_min_events,
                         tp.list.as<unsigned>(),
                         n_list_dev, n_fb_dev, ctx->stream));
     CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
@@ -1332,7 +1333,7 @@ recon_status prepare_tiles(recon_ctx* ctx)
     ctx->stats.kernel_launches += 7;
     tp.th = t;
     tp.n_binned = binned;
-    tp.mode = ctx->tile_mode;
+    tp.mode = mode;
     tp.min_events = ctx->tile_min_events;
     tp.half_window = hw;
     tp.n_cells = nc;
@@ -1355,6 +1356,7 @@ void plan_tiles(recon_ctx* ctx, IterPlan& p)
     p.ev_fb = tp.ev_fb.p;
     p.n_fb = tp.n_fb;
     p.n_cell_events = tp.n_binned;
+    p.tile_mode = tp.mode;
 }
 
 // Host events and n_iter >= 1: the upload is streamed in chunks through two
@@ -1452,6 +1454,9 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     if (n_iter < 0) return fail(ctx, RECON_EINVAL, "n_iter is negative");
     if ((long long)n_iter * ctx->subsets > (1LL << 24)) return fail(ctx, RECON_EINVAL, "n_iter x subsets too large");
     const bool streamed = can_stream(ctx, events, n_iter) && ctx->have_sens;
+    // event order / tiles: mode 3 (auto, the default) orders the events by cell when the
+    // call reuses resident events (events == NULL), where the cached binning pays off
+    const int mode = ctx->tile_mode == 3 ? (events ? 0 : 2) : ctx->tile_mode;
     if (streamed) {
         recon_status s = begin_streamed_events(ctx, events);
         if (s != RECON_OK) return s;
@@ -1537,15 +1542,15 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
                 ctx->last_cfg = c;
             }
         }
-        if (n_iter > 1) {
-            s = prepare_tiles(ctx);
+        if (n_iter > 1 && (mode == 1 || mode == 2)) {
+            s = prepare_tiles(ctx, mode);
             if (s != RECON_OK) return s;
             plan_tiles(ctx, p);
         }
         s = run_iterations(ctx, p, n_iter - 1, false);
     } else {
-        if (n_iter > 0) {
-            s = prepare_tiles(ctx);
+        if (n_iter > 0 && (mode == 1 || mode == 2)) {
+            s = prepare_tiles(ctx, mode);
             if (s != RECON_OK) return s;
             plan_tiles(ctx, p);
         }

@@ -433,12 +433,16 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
     *best = default_cfg();
     CK(ensure(ctx->pass_partial, sizeof(double) * kNeffSlots * tbl.n));
     a.partial = ctx->pass_partial.as<double>();
+    // block_mul == 1 marks a cell-ordered event list: each candidate spreads its own grid
+    const bool spread = a.block_mul == 1;
     for (const LaunchCfg& c : cands) {
         float ms_min = 1e30f;
+        PassArgs ac = a;
+        if (spread) ac.block_mul = spread_multiplier(pass_blocks(c, a.n, ctx->num_sms));
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
             CK(cudaEventRecord(e0, ctx->stream));
-            CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, c, a, tbl, ctx->num_sms, ctx->stream));
+            CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, c, ac, tbl, ctx->num_sms, ctx->stream));
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));
             float ms = 0;
@@ -1521,31 +1525,43 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
         p.med = ctx->med.as<float>();
     }
     ctx->last_cfg = p.cfg;
+    // launch for the event list the iterations will walk (the cell-ordered copy when
+    // that order is on); an autotuner run accumulates into C and the N_eff slots, which
+    // are cleared again
+    auto retune = [&]() -> recon_status {
+        PassArgs ta = p.a;
+        RegionTable tt = p.tbl;
+        if (p.tiled && p.tile_mode == 2) {
+            ta.events = p.ev_cell;
+            ta.n = p.n_cell_events;
+            ta.block_mul = 1;
+            tt.ev_begin[1] = p.n_cell_events;
+        }
+        const long long runs = ctx->stats.autotune_runs;
+        recon_status st2;
+        LaunchCfg c = choose_cfg(ctx, ta, tt, &st2);
+        if (st2 != RECON_OK) return st2;
+        if (ctx->stats.autotune_runs != runs) {
+            CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
+            CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots, ctx->stream));
+        }
+        p.cfg = c;
+        p.pass_blocks = pass_blocks(p.cfg, ctx->n_ev, ctx->num_sms);
+        ctx->last_cfg = c;
+        return RECON_OK;
+    };
     recon_status s;
     if (streamed) {
         s = stream_pass(ctx, events, p);
         if (s != RECON_OK) return s;
         if (n_iter > 1) {
-            const long long runs = ctx->stats.autotune_runs;
-            LaunchCfg c = choose_cfg(ctx, p.a, p.tbl, &st);
-            if (st != RECON_OK) return st;
-            if (ctx->stats.autotune_runs != runs) {
-                // the autotuner's timed passes accumulated into C and the N_eff slots,
-                // which the first update and finalize had left at zero
-                CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
-                CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots, ctx->stream));
+            if (mode == 1 || mode == 2) {
+                s = prepare_tiles(ctx, mode);
+                if (s != RECON_OK) return s;
+                plan_tiles(ctx, p);
             }
-            if (c.blocks_per_sm != p.cfg.blocks_per_sm || c.threads != p.cfg.threads || c.chunk != p.cfg.chunk ||
-                c.cache != p.cfg.cache || c.tail != p.cfg.tail) {
-                p.cfg = c;
-                p.pass_blocks = pass_blocks(p.cfg, ctx->n_ev, ctx->num_sms);
-                ctx->last_cfg = c;
-            }
-        }
-        if (n_iter > 1 && (mode == 1 || mode == 2)) {
-            s = prepare_tiles(ctx, mode);
+            s = retune();
             if (s != RECON_OK) return s;
-            plan_tiles(ctx, p);
         }
         s = run_iterations(ctx, p, n_iter - 1, false);
     } else {
@@ -1553,6 +1569,8 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
             s = prepare_tiles(ctx, mode);
             if (s != RECON_OK) return s;
             plan_tiles(ctx, p);
+            s = retune();
+            if (s != RECON_OK) return s;
         }
         s = run_iterations(ctx, p, n_iter);
     }

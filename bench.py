@@ -25,6 +25,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TOF-MLEM events x iterations / s (full-body, 146M events, 150x150x600 @ 4 mm)"
+# DRAM bytes per event of the fused pass (ncu, 8 M full-body events, cell order, 192 threads,
+# series masses): see profiles/k_event_pass_fullbody_8M.md
+TRAFFIC_BYTES_PER_EVENT = 49.8
+# algorithmic FP32 operations per Siddon piece: ~25 for the step and the two
+# accumulations plus ~20 for the Gaussian mass of the piece
+ALU_OPS_PER_PIECE = 45.0
 UNIT = "events*iters/s"
 
 
@@ -580,30 +586,45 @@ def run_ours(args):
         # reads each 32-byte event record once from HBM.
         red_rate = visits / (pass_ms / 1e3)
         hbm_gbs = 32.0 * n / (pass_ms / 1e3) / 1e9
-        # Each piece is one scattered 4-byte gather of lambda and one scattered
-        # FP32 reduction into C, both in L2-resident images: the bound is the
-        # GPU's rate of such (gather + reduction) steps, measured live by the
-        # mixed probe on an image of the same size.
-        # DRAM bytes per event of the exact fused pass from its ncu capture on 8 M
-        # full-body events (dram__bytes_read.sum + dram__bytes_write.sum = 389.6 MB;
-        # the traffic grows with the events, so it is scaled to this launch)
-        traffic = 389.6e6 / 8e6 * n if not args.samples else None
+        # Roofline as t_min / t_measured with t_min the largest of the pass's
+        # algorithmic terms per launch: HBM (32 B per event), L2 reductions (one FP32
+        # reduction per piece, at the rate of scattered red.global.add.f32 measured live),
+        # L2 gathers (one 4-byte gather per piece, live gather rate) and FP32 ALU (about
+        # 25 FP32 operations plus one Gaussian-mass evaluation, ~20, per piece, on
+        # 148 SMs x 128 FP32 lanes at the sampled SM clock).  `achieved` and `peak`
+        # are given in the unit of the largest term.
+        # DRAM bytes per event of the fused pass from its ncu capture on 8 M full-body
+        # events in the bench's event order and launch (dram__bytes_read.sum +
+        # dram__bytes_write.sum); the traffic grows with the events, so it is scaled.
+        traffic = TRAFFIC_BYTES_PER_EVENT * n if not args.samples else None
         R, G = probes.get("l2_red_gops"), probes.get("gather_gops")
-        peak = 1.0 / (1.0 / R + 1.0 / G) if R and G else None
+        sm_mhz = (clocks.get("sm_mhz") or 2032.0) if isinstance(clocks, dict) else 2032.0
+        alu_peak = 148 * 128 * sm_mhz * 1e6                      # FP32 lane operations per second
+        pieces_s = pass_ms / 1e3
+        terms = {"hbm": (32.0 * n) / (peaks["hbm_gbs"] * 1e9),
+                 "l2_reductions": visits / (R * 1e9) if R else 0.0,
+                 "l2_gathers": visits / (G * 1e9) if G else 0.0,
+                 "alu": visits * ALU_OPS_PER_PIECE / alu_peak}
+        bound = max(terms, key=terms.get)
+        rates = {"hbm": (32.0 * n / pieces_s / 1e9, peaks["hbm_gbs"], "GB/s"),
+                 "l2_reductions": (visits / pieces_s / 1e9, R, "Gred/s"),
+                 "l2_gathers": (visits / pieces_s / 1e9, G, "Ggather/s"),
+                 "alu": (visits * ALU_OPS_PER_PIECE / pieces_s / 1e12, alu_peak / 1e12, "Tops/s")}
+        ach, pk, unit = rates[bound]
         out["roofline"] = {
-            "bound": "l2_random_access", "achieved": red_rate / 1e9, "peak": peak, "unit": "Gpiece/s",
-            "frac": (red_rate / 1e9 / peak) if peak else None, "traffic": traffic,
-            "traffic_source": "ncu capture of the same kernel on 8 M full-body events, 48.7 B per event, scaled",
+            "bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk if pk else None,
+            "traffic": traffic,
+            "traffic_source": f"ncu capture of the same kernel on 8 M full-body events, "
+                              f"{TRAFFIC_BYTES_PER_EVENT:.1f} B per event, scaled",
+            "t_min_ms": 1e3 * terms[bound], "terms_ms": {k: 1e3 * v for k, v in terms.items()},
             "per_launch": {"events": n, "pieces": visits, "gathers": visits, "reductions": visits,
                            "hbm_bytes": 32.0 * n, "pass_ms": pass_ms},
-            "peak_source": "live probes on an L2-resident image of the grid's size: R = scattered "
-                           "red.global.add.f32 per s, G = scattered 4-byte gathers per s; a piece costs one of each "
-                           "through the same L1/L2 path, so peak = 1 / (1/R + 1/G)",
+            "peak_source": "live probes on an L2-resident image of the grid's size (scattered "
+                           "red.global.add.f32 and 4-byte gathers); HBM from MEASURED_PEAKS; ALU from "
+                           "148 SMs x 128 lanes x sampled SM clock",
             "mixed_probe_gsteps": probes.get("mixed_gsteps"),
             "secondary": {"hbm_gbs": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
-                          "hbm_peak_source": src,
-                          "red_frac": red_rate / 1e9 / probes["l2_red_gops"],
-                          "gather_frac": red_rate / 1e9 / probes["gather_gops"]}}
+                          "hbm_peak_source": src}}
         if args.samples:
             # the roofline above counts Siddon pieces: it describes the exact projector only
             out["roofline"] = {"bound": "l2_random_access", "achieved": None, "peak": peak, "unit": "Gpiece/s",

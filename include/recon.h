@@ -185,18 +185,18 @@ recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_sa
 recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float* offsets_mm, float* weights,
                                    int32_t* n_out);
 
-/* Event order of the MLEM pass of recon_mlem (exact projector, one subset).  order = 0:
- * the events as loaded.  order = c in [1, 64]: the resident events are binned once by
+/* Event order of the MLEM pass of recon_mlem (exact projector, one subset, at least two
+ * iterations for a call that passes events).  order = 0: the events as loaded.  order = c in [1, 64]: the resident events are binned once by
  * the cell of c^3 voxels that holds their TOF point and processed cell by cell, with the
  * cells spread over the blocks that run at the same time (block b of the grid takes block
  * (b * m) mod n of the binned list, m coprime with n): a warp's lines start in one cell
  * (nearby voxels), while concurrent blocks work far apart (no hot voxels).  Same
  * arithmetic; the sums run in another order.  The binning costs one copy of the events
- * and is cached with the events.  order = -1 (the default): cells of 3^3 voxels for calls
- * that reuse the resident events (events = NULL), where the cached binning pays off, and
- * the load order for calls that pass events (their upload overlaps the first pass).
- * Measured on B300, 146 M full-body events: 45.4 ms per pass against 47.6 ms, whatever
- * the cell edge from 1 to 10 voxels.  Errors: EINVAL (order outside [-1, 64]). */
+ * and is cached with the events (a call that passes host events bins them after its
+ * first, upload-overlapped pass).  order = -1: the default, cells of 3^3 voxels.
+ * Measured on B300, 146 M full-body events: 35.5 ms per pass against 47.6 ms in load
+ * order (with the series piece masses the autotuner then picks), whatever the cell edge
+ * from 1 to 10 voxels.  Errors: EINVAL (order outside [-1, 64]). */
 recon_status recon_set_event_order(recon_ctx* ctx, int32_t order);
 
 /* Shared-memory tiled event pass for recon_mlem (off by default).  A layout choice for
@@ -208,7 +208,7 @@ recon_status recon_set_event_order(recon_ctx* ctx, int32_t order);
  * the image.  Events whose window would leave their tile take the global-memory pass.
  * Used for MLEM with the exact projector and one subset when two tiles fit the shared
  * memory of a block (e.g. 4 mm voxels at 300 ps); otherwise every event takes the
- * global-memory pass.  on = 0 returns to the default event order (recon_set_event_order -1).  A cell is tiled only when it holds at least m events
+ * global-memory pass.  on = 0 returns to the default cell order (recon_set_event_order -1).  A cell is tiled only when it holds at least m events
  * (loading and flushing a tile costs about as much as a few hundred events): on = 1 sets
  * m = 256, on > 1 sets m = on; the events of smaller cells take the global-memory pass.
  * lanes: threads per event, 1 (each thread walks its event twice, forward then back) or

@@ -135,7 +135,7 @@ struct recon_ctx {
     long long sens_generation = 0;
 
     // shared-memory tiled pass (plain MLEM with the exact projector)
-    int tile_mode = 3;    // 0 off, 1 shared-memory tiles, 2 cell order, 3 cell order on resident reuse (default)
+    int tile_mode = 2;    // 0 load order, 1 shared-memory tiles, 2 cell order (default)
     int tile_min_events = 256;  // cells with fewer events take the global-memory pass
     int tile_lanes = 1;         // threads per event in the tiled pass (1 or 8)
     int order_cell = 3;         // cell edge (voxels) of the cell-ordered pass
@@ -923,7 +923,7 @@ recon_status recon_set_event_order(recon_ctx* ctx, int32_t order)
 {
     CHECK_CTX();
     if (order < -1 || order > 64) return fail(ctx, RECON_EINVAL, "order must be in [-1, 64]");
-    ctx->tile_mode = order > 0 ? 2 : (order == -1 ? 3 : 0);
+    ctx->tile_mode = order != 0 ? 2 : 0;
     ctx->order_cell = order > 0 ? order : 3;
     invalidate_graph(ctx);
     return RECON_OK;
@@ -934,7 +934,7 @@ recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on, int32_t lanes)
     CHECK_CTX();
     if (on < 0) return fail(ctx, RECON_EINVAL, "on must be >= 0");
     if (lanes != 1 && lanes != 8) return fail(ctx, RECON_EINVAL, "lanes must be 1 or 8");
-    ctx->tile_mode = on != 0 ? 1 : 3;
+    ctx->tile_mode = on != 0 ? 1 : 2;
     ctx->tile_min_events = on > 1 ? on : 256;
     ctx->tile_lanes = lanes == 8 ? 8 : 1;
     invalidate_graph(ctx);
@@ -1458,9 +1458,8 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     if (n_iter < 0) return fail(ctx, RECON_EINVAL, "n_iter is negative");
     if ((long long)n_iter * ctx->subsets > (1LL << 24)) return fail(ctx, RECON_EINVAL, "n_iter x subsets too large");
     const bool streamed = can_stream(ctx, events, n_iter) && ctx->have_sens;
-    // event order / tiles: mode 3 (auto, the default) orders the events by cell when the
-    // call reuses resident events (events == NULL), where the cached binning pays off
-    const int mode = ctx->tile_mode == 3 ? (events ? 0 : 2) : ctx->tile_mode;
+    // event order / tiles (mode 2, cell order, is the default)
+    const int mode = ctx->tile_mode;
     if (streamed) {
         recon_status s = begin_streamed_events(ctx, events);
         if (s != RECON_OK) return s;

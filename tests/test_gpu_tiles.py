@@ -21,7 +21,10 @@ pytestmark = pytest.mark.gpu
 def run_mlem(geom, g, ev, sens, n_iter, tiled, graphs=1, lanes=1):
     with B.Context(geom, grid_tuple(g), 300.0) as ctx:
         ctx.set_sensitivity(sens)
-        ctx.set_tiled_pass(tiled, lanes)
+        if tiled:
+            ctx.set_tiled_pass(tiled, lanes)
+        else:
+            ctx.set_event_order(0)                  # global-memory pass in load order
         ctx.set_graphs(graphs)
         lam = np.zeros(g.n_vox, np.float32)
         cons = np.zeros((n_iter, 2))

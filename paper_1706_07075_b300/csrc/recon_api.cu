@@ -64,6 +64,7 @@ struct RegionPrep {
     std::vector<int> lo, hi;      // slab slice ranges
     std::vector<long long> rv;    // slab voxel offsets (R + 1)
     std::vector<float> start;     // uniform start value per region
+    int order = -1;               // event order the split read (context tile_mode)
 };
 
 // Cell binning of the resident events for the shared-memory tiled pass, valid
@@ -714,9 +715,10 @@ recon_status validate_regions(recon_ctx* ctx, int R, const recon_region* regions
 // Split the resident events; leaves codes, idx and offsets (host copy in
 // h_offsets, R+2 entries) in the context.
 recon_status split_internal(recon_ctx* ctx, int R, const recon_region* regions, double shell_mm,
-                            std::vector<long long>& h_offsets)
+                            std::vector<long long>& h_offsets, const void* ev = nullptr, long long n_ev = -1)
 {
-    const long long n = ctx->n_ev;
+    if (!ev) ev = ctx->ev.p;
+    const long long n = n_ev >= 0 ? n_ev : ctx->n_ev;
     if (n >= (1LL << 31)) return fail(ctx, RECON_EINVAL, "region division takes fewer than 2^31 events");
     std::vector<double> zb(R + 1);
     for (int r = 0; r < R; ++r) zb[r] = ctx->grid.oz + (double)regions[r].z_lo * ctx->grid.vz;
@@ -729,7 +731,8 @@ recon_status split_internal(recon_ctx* ctx, int R, const recon_region* regions, 
     CK(ensure(ctx->base, sizeof(long long) * (size_t)tiles * R));
     CK(cudaMemsetAsync(ctx->counts.p, 0, sizeof(int) * (size_t)tiles * (R + 1), ctx->stream));
     const bool packed = ctx->fmt == FMT_PACKED;
-    CK(launch_region_codes(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr,
+    CK(launch_region_codes(packed ? nullptr : static_cast<const float4*>(ev), packed ? static_cast<const int4*>(ev)
+                                                                                    : nullptr,
                            ctx->lattice, n, zb.data(), R, shell_mm, ctx->codes.as<uint8_t>(), ctx->counts.as<int>(),
                            tile, ctx->stream));
     CK(launch_region_scan(ctx->counts.as<int>(), (int)tiles, R, ctx->offsets.as<long long>(),
@@ -1641,6 +1644,7 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
     const bool packed = ctx->fmt == FMT_PACKED;
     RegionPrep& rp = ctx->region_prep;
     const bool reuse = rp.valid && rp.ev_gen == ctx->ev_generation && rp.sens_gen == ctx->sens_generation &&
+                       rp.order == ctx->tile_mode &&
                        rp.margin == margin_mm && rp.shell == shell_mm && rp.fmt == ctx->fmt &&
                        (int)rp.regions.size() == R &&
                        std::equal(rp.regions.begin(), rp.regions.end(), regions, [](const recon_region& a,
@@ -1649,14 +1653,28 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
                        });
     if (!reuse) {
         // split, region-ordered event copy, slab sensitivities and start values:
-        // kept until the events, the sensitivity or the division change
+        // kept until the events, the sensitivity or the division change.  In cell
+        // order the split reads the cell-ordered copy, so each region's events come
+        // cell by cell (events whose window misses the grid are left out: they have
+        // p_i = 0 and add nothing)
         rp.valid = false;
-        s = split_internal(ctx, R, regions, shell_mm, rp.off);
+        const void* src = ctx->ev.p;
+        long long n_src = ctx->n_ev;
+        if (ctx->tile_mode == 2) {
+            s = prepare_tiles(ctx, 2);
+            if (s != RECON_OK) return s;
+            if (ctx->tile_prep.valid && ctx->tile_prep.n_fb == 0) {
+                src = ctx->tile_prep.ev_cell.p;
+                n_src = ctx->tile_prep.n_binned;
+            }
+        }
+        s = split_internal(ctx, R, regions, shell_mm, rp.off, src, n_src);
         if (s != RECON_OK) return s;
         const long long total = rp.off[R];
         const size_t rec = packed ? 16 : 32;
         CK(ensure(ctx->ev_reg, rec * (size_t)std::max(1LL, total)));
-        CK(launch_region_gather(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr,
+        CK(launch_region_gather(packed ? nullptr : static_cast<const float4*>(src),
+                                packed ? static_cast<const int4*>(src) : nullptr,
                                 ctx->codes.as<uint8_t>(), ctx->idx.as<int>(), total,
                                 packed ? nullptr : ctx->ev_reg.as<float4>(), packed ? ctx->ev_reg.as<int4>() : nullptr,
                                 ctx->stream));
@@ -1704,6 +1722,7 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
         rp.shell = shell_mm;
         rp.fmt = ctx->fmt;
         rp.ev_gen = ctx->ev_generation;
+        rp.order = ctx->tile_mode;
         rp.sens_gen = ctx->sens_generation;
         rp.valid = true;
     }

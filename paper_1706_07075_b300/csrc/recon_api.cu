@@ -437,6 +437,8 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
     // block_mul == 1 marks a cell-ordered event list: each candidate spreads its own grid
     const bool spread = a.block_mul == 1;
     for (const LaunchCfg& c : cands) {
+        // the persistent work queue takes events in list order, which a spread list must not
+        if (spread && c.blocks_per_sm > 0) continue;
         float ms_min = 1e30f;
         PassArgs ac = a;
         if (spread) ac.block_mul = spread_multiplier(pass_blocks(c, a.n, ctx->num_sms));
@@ -676,7 +678,7 @@ LaunchCfg tuned_or_default(recon_ctx* ctx, const PassArgs& a, const RegionTable&
 {
     if (ctx->user_cfg) return ctx->cfg;
     if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg();
-    auto it = ctx->tuned.find(std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n));
+    auto it = ctx->tuned.find(std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n + (a.block_mul == 1 ? (1 << 20) : 0)));
     return it != ctx->tuned.end() ? it->second : default_cfg();
 }
 
@@ -685,7 +687,8 @@ LaunchCfg choose_cfg(recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl, 
     *st = RECON_OK;
     if (ctx->user_cfg) return ctx->cfg;
     if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg();
-    auto key = std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n);
+    // spread (cell- or region-ordered) lists are tuned apart from lists in load order
+    auto key = std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n + (a.block_mul == 1 ? (1 << 20) : 0));
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
     LaunchCfg best;
@@ -1756,12 +1759,17 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
     for (int r = 0; r < R; ++r) p.tbl.grid[r] = grid_h(ctx->grid, lo[r], hi[r], rv[r]);
     CK(ensure(ctx->pass_partial, sizeof(double) * kNeffSlots * R));
     p.a.partial = ctx->pass_partial.as<double>();
-    p.cfg = choose_cfg(ctx, p.a, p.tbl, &s);
+    {
+        // region-ordered events: tune with the block spreading the pass will use
+        PassArgs ta = p.a;
+        ta.block_mul = 1;
+        p.cfg = choose_cfg(ctx, ta, p.tbl, &s);
+    }
     if (s != RECON_OK) return s;
     CK(cudaMemsetAsync(ctx->C_reg.p, 0, sizeof(float) * nvt, ctx->stream));
     CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots * R, ctx->stream));
     p.pass_blocks = pass_blocks(p.cfg, total, ctx->num_sms);
-    p.a.block_mul = spread_multiplier(p.pass_blocks);
+    p.a.block_mul = p.cfg.blocks_per_sm > 0 ? 0 : spread_multiplier(p.pass_blocks);
     p.upd_bpr = std::max(1, update_blocks(nvt) / R);
     CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)p.upd_bpr * R));
     p.subsets = 1;

@@ -185,8 +185,8 @@ recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_sa
 recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float* offsets_mm, float* weights,
                                    int32_t* n_out);
 
-/* Event order of the MLEM pass of recon_mlem (exact projector, one subset, at least two
- * iterations for a call that passes events).  order = 0: the events as loaded.  order = c in [1, 64]: the resident events are binned once by
+/* Event order of the MLEM pass of recon_mlem (either projector, one subset, at least two
+ * iterations for a call that passes events) and of recon_mlem_regions.  order = 0: the events as loaded.  order = c in [1, 64]: the resident events are binned once by
  * the cell of c^3 voxels that holds their TOF point and processed cell by cell, with the
  * cells spread over the blocks that run at the same time (block b of the grid takes block
  * (b * m) mod n of the binned list, m coprime with n): a warp's lines start in one cell

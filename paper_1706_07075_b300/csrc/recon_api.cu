@@ -1235,7 +1235,7 @@ recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const
 // by the scanner's axial acceptance (events beyond it take the fallback pass).
 bool tile_params(const recon_ctx* ctx, int mode, TileH* out)
 {
-    if (mode == 0 || ctx->lut_n > 0 || ctx->subsets != 1) return false;
+    if (mode == 0 || ctx->subsets != 1 || (mode == 1 && ctx->lut_n > 0)) return false;
     const recon_grid& g = ctx->grid;
     if (mode == 2) {
         // event order only: cells of 3^3 voxels, a halo covering the grid (no fallback)
@@ -1356,7 +1356,8 @@ recon_status prepare_tiles(recon_ctx* ctx, int mode)
 void plan_tiles(recon_ctx* ctx, IterPlan& p)
 {
     const TilePrep& tp = ctx->tile_prep;
-    p.tiled = tp.valid && tp.ev_gen == ctx->ev_generation && p.subsets == 1 && p.a.lut.n == 0 && p.n_regions == 1;
+    p.tiled = tp.valid && tp.ev_gen == ctx->ev_generation && p.subsets == 1 && p.n_regions == 1 &&
+              (tp.mode == 2 || p.a.lut.n == 0);
     if (!p.tiled) return;
     p.th = tp.th;
     p.list = tp.list.as<unsigned>();

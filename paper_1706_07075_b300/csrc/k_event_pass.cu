@@ -204,15 +204,18 @@ __device__ __forceinline__ LutLine lut_line(const GridDev& g, const Event& e)
 }
 
 // Visit (voxel, summed weight) of every run of consecutive samples that share
-// a voxel inside the grid.
-template <class Visit>
+// a voxel inside the grid.  NS > 0: the sample count known at compile time (the
+// loop unrolls and the table entries become constant operands); 0: lut.n.
+template <int NS, class Visit>
 __device__ __forceinline__ void lut_walk(const GridDev& g, const LutH& lut, const LutLine& l, Visit&& visit)
 {
     if (!l.valid) return;
     const float fnx = (float)g.nx, fny = (float)g.ny, fnz = (float)g.nz;
     int prev = -1;
     float acc = 0.f;
-    for (int k = 0; k < lut.n; ++k) {
+    const int n = NS > 0 ? NS : lut.n;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
         const float2 s = lut.s[k];
         const float fx = floorf(__fmaf_rn(s.x, l.bx, l.ax));
         const float fy = floorf(__fmaf_rn(s.x, l.by, l.ay));
@@ -229,7 +232,7 @@ __device__ __forceinline__ void lut_walk(const GridDev& g, const LutH& lut, cons
     if (prev >= 0) visit(prev, acc);
 }
 
-template <int Kind, int Fmt>
+template <int Kind, int Fmt, int NS>
 __device__ __forceinline__ float do_event_lut(const PassArgs& a, const SharedTable& t, long long i, bool bf16,
                                               int& region)
 {
@@ -240,13 +243,13 @@ __device__ __forceinline__ float do_event_lut(const PassArgs& a, const SharedTab
     float* const Cb = a.C + g.vox_offset;
     if (Kind == PASS_BACK) {
         const float r = a.r_in[i];
-        if (r != 0.f) lut_walk(g, a.lut, l, [&](int j, float w) { atomicAdd(Cb + j, w * r); });
+        if (r != 0.f) lut_walk<NS>(g, a.lut, l, [&](int j, float w) { atomicAdd(Cb + j, w * r); });
         return 0.f;
     }
     const float* const lb = a.lam + g.vox_offset;
     const unsigned short* const hb = reinterpret_cast<const unsigned short*>(a.lam_bf16) + g.vox_offset;
     float p = 0.f;
-    lut_walk(g, a.lut, l, [&](int j, float w) {
+    lut_walk<NS>(g, a.lut, l, [&](int j, float w) {
         const float lam_j = bf16 ? __uint_as_float(((unsigned)__ldg(hb + j)) << 16) : __ldg(lb + j);
         p = fmaf(w, lam_j, p);
     });
@@ -256,11 +259,11 @@ __device__ __forceinline__ float do_event_lut(const PassArgs& a, const SharedTab
     }
     if (!(p > 0.f)) return 0.f;
     const float r = e.w / p;
-    lut_walk(g, a.lut, l, [&](int j, float w) { atomicAdd(Cb + j, w * r); });
+    lut_walk<NS>(g, a.lut, l, [&](int j, float w) { atomicAdd(Cb + j, w * r); });
     return e.w;
 }
 
-template <int Kind, int Fmt>
+template <int Kind, int Fmt, int NS>
 __global__ void __launch_bounds__(256) k_lut_pass(PassArgs a, RegionTable tbl)
 {
     __shared__ SharedTable t;
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(256) k_lut_pass(PassArgs a, RegionTable tbl)
     const long long i = (long long)b * blockDim.x + threadIdx.x;
     if (i < a.n) {
         int r;
-        const float w = do_event_lut<Kind, Fmt>(a, t, i, a.lam_bf16 != nullptr, r);
+        const float w = do_event_lut<Kind, Fmt, NS>(a, t, i, a.lam_bf16 != nullptr, r);
         if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
     }
     if (Kind == PASS_FUSED) {
@@ -293,7 +296,9 @@ cudaError_t launch_lut(const LaunchCfg& cfg, const PassArgs& a, const RegionTabl
     if (a.lut.n < 1 || a.lut.n > kMaxLutSamples) return cudaErrorInvalidValue;
     const long long blocks = (a.n + cfg.threads - 1) / cfg.threads;
     if (blocks == 0) return cudaSuccess;
-    k_lut_pass<Kind, Fmt><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
+    if (a.lut.n == 32) k_lut_pass<Kind, Fmt, 32><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
+    else if (a.lut.n == 15) k_lut_pass<Kind, Fmt, 15><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
+    else k_lut_pass<Kind, Fmt, 0><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
     return cudaGetLastError();
 }
 

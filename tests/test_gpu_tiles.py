@@ -107,3 +107,17 @@ def test_cell_ordered_pass_matches_oracle():
     assert max_rel_above(lam, lam_ref, 0.01) <= 1e-3
     for k in range(5):
         assert cons[k, 0] == pytest.approx(hist[k][0], abs=0.5)
+
+
+def test_order_and_tile_argument_checks():
+    g = workload_grid("tiny")
+    with B.Context((150.0, 200.0, 45.0), grid_tuple(g), 300.0) as ctx:
+        for bad in (-2, 65):
+            with pytest.raises(B.ReconError):
+                ctx.set_event_order(bad)
+        with pytest.raises(B.ReconError):
+            ctx.set_tiled_pass(-1)
+        with pytest.raises(B.ReconError):
+            ctx.set_tiled_pass(1, 4)
+        ctx.set_event_order(-1)
+        ctx.set_event_order(0)

@@ -627,7 +627,7 @@ def run_ours(args):
                           "hbm_peak_source": src}}
         if args.samples:
             # the roofline above counts Siddon pieces: it describes the exact projector only
-            out["roofline"] = {"bound": "l2_random_access", "achieved": None, "peak": peak, "unit": "Gpiece/s",
+            out["roofline"] = {"bound": "l2_reductions", "achieved": None, "peak": R, "unit": "Gred/s",
                                "frac": None, "traffic": None,
                                "note": "sampled projector timed; see profiles/k_lut_pass_fullbody_8M.md"}
         if not args.no_cpu_baseline:

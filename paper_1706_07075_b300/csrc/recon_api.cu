@@ -121,8 +121,8 @@ struct recon_ctx {
     // options
     bool bf16 = false, timing = false, graphs = true, autotune = true;
     bool user_cfg = false;
-    LaunchCfg cfg{128, 0, 0, 0, TAIL_FIT};
-    LaunchCfg last_cfg{128, 0, 0, 0, TAIL_FIT};
+    LaunchCfg cfg{192, 0, 0, 0, TAIL_SERIES};
+    LaunchCfg last_cfg{192, 0, 0, 0, TAIL_SERIES};
     std::map<std::tuple<long long, int, long long, int>, LaunchCfg> tuned;
     recon_stats stats{};
 
@@ -358,7 +358,7 @@ recon_status finish_sensitivity(recon_ctx* ctx)
     return RECON_OK;
 }
 
-LaunchCfg default_cfg() { return LaunchCfg{128, 0, 0, 0, TAIL_FIT}; }
+LaunchCfg default_cfg() { return LaunchCfg{192, 0, 0, 0, TAIL_SERIES}; }
 
 bool valid_cfg(const recon_launch* c)
 {

@@ -53,7 +53,9 @@ def parse():
     ap.add_argument("--no-graphs", action="store_true", help="launch iterations directly instead of graph replay")
     ap.add_argument("--tiles", action="store_true", help="shared-memory tiled event pass (off by default)")
     ap.add_argument("--cell-order", type=int, default=0,
-                    help="events grouped by TOF-point cells of this edge (voxels), cells spread over blocks (0: off)")
+                    help="events grouped by TOF-point cells of this edge (voxels), cells spread over blocks "
+                         "(0: the library default)")
+    ap.add_argument("--dir-bins", default="1,1", help="azimuth,polar direction bins within a cell")
     ap.add_argument("--tile-min", type=int, default=0, help="minimum events per tiled cell (0: the library default)")
     ap.add_argument("--tile-lanes", type=int, default=1, help="threads per event in the tiled pass (1 or 8)")
     ap.add_argument("--samples", type=int, default=0,
@@ -503,8 +505,9 @@ def run_ours(args):
         ctx.set_projector(B.PROJ_SAMPLED, args.samples)
     if args.tiles:
         ctx.set_tiled_pass(max(1, args.tile_min), args.tile_lanes)
-    if args.cell_order:
-        ctx.set_event_order(args.cell_order)
+    az, pol = (int(x) for x in args.dir_bins.split(","))
+    if args.cell_order or (az, pol) != (1, 1):
+        ctx.set_event_order(args.cell_order or -1, az, pol)
     # warm-up (the first call also runs the launch autotuner)
     for _ in range(args.warmup):
         ctx.mlem(None, args.iters)

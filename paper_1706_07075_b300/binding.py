@@ -77,7 +77,7 @@ SIGNATURES = {
     "recon_set_median_filter": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_subsets": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_tiled_pass": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
-    "recon_set_event_order": (C.c_int, [_CTX, C.c_int32]),
+    "recon_set_event_order": (C.c_int, [_CTX, C.c_int32, C.c_int32, C.c_int32]),
     "recon_preprocess": (C.c_int, [_CTX, C.POINTER(recon_events), _VP, C.c_double, C.c_int32, _VP, _VP,
                                    C.POINTER(C.c_int64)]),
     "recon_median_filter": (C.c_int, [_CTX, _VP, _VP]),
@@ -238,8 +238,8 @@ def recon_set_projector(ctx, projector, n_samples=0):
     return check(ctx, load().recon_set_projector(ctx, int(projector), int(n_samples)))
 
 
-def recon_set_event_order(ctx, order):
-    return check(ctx, load().recon_set_event_order(ctx, int(order)))
+def recon_set_event_order(ctx, order, azimuth_bins=1, polar_bins=1):
+    return check(ctx, load().recon_set_event_order(ctx, int(order), int(azimuth_bins), int(polar_bins)))
 
 
 def recon_set_tiled_pass(ctx, on, lanes=1):

@@ -96,6 +96,16 @@ __global__ void k_cell_codes(const void* __restrict__ ev, long long n, float lat
             }
             out = fits ? (unsigned)cell[0] + (unsigned)t.ncx * ((unsigned)cell[1] + (unsigned)t.ncy * (unsigned)cell[2])
                        : kCellFallback;
+            if (fits && t.dir_az * t.dir_pol > 1) {
+                // direction bin of the undirected line: u and -u are one line, so fold
+                // to ux >= 0; azimuth over (-pi/2, pi/2], polar over uz in [-1, 1]
+                const float sgn = uu[0] < 0.f ? -1.f : 1.f;
+                const float ux = sgn * uu[0], uy = sgn * uu[1], uz = sgn * uu[2];
+                const float az = atan2f(uy, ux) * 0.318309886f + 0.5f;            // [0, 1]
+                const int ia = min(t.dir_az - 1, max(0, (int)(az * (float)t.dir_az)));
+                const int ip = min(t.dir_pol - 1, max(0, (int)((uz + 1.f) * 0.5f * (float)t.dir_pol)));
+                out = out * (unsigned)(t.dir_az * t.dir_pol) + (unsigned)(ia * t.dir_pol + ip);
+            }
         }
     }
     code[i] = out;

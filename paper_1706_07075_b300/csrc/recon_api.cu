@@ -140,6 +140,7 @@ struct recon_ctx {
     int tile_min_events = 256;  // cells with fewer events take the global-memory pass
     int tile_lanes = 1;         // threads per event in the tiled pass (1 or 8)
     int order_cell = 3;         // cell edge (voxels) of the cell-ordered pass
+    int order_dir_az = 1, order_dir_pol = 1;  // direction bins within a cell
     TilePrep tile_prep;
 };
 
@@ -925,10 +926,14 @@ recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets)
     return RECON_OK;
 }
 
-recon_status recon_set_event_order(recon_ctx* ctx, int32_t order)
+recon_status recon_set_event_order(recon_ctx* ctx, int32_t order, int32_t azimuth_bins, int32_t polar_bins)
 {
     CHECK_CTX();
     if (order < -1 || order > 64) return fail(ctx, RECON_EINVAL, "order must be in [-1, 64]");
+    if (azimuth_bins < 1 || azimuth_bins > 64 || polar_bins < 1 || polar_bins > 64)
+        return fail(ctx, RECON_EINVAL, "direction bins must be in [1, 64]");
+    ctx->order_dir_az = azimuth_bins;
+    ctx->order_dir_pol = polar_bins;
     ctx->tile_mode = order != 0 ? 2 : 0;
     ctx->order_cell = order > 0 ? order : 3;
     invalidate_graph(ctx);
@@ -1256,7 +1261,9 @@ bool tile_params(const recon_ctx* ctx, int mode, TileH* out)
         t.ncx = (g.nx + t.cs - 1) / t.cs;
         t.ncy = (g.ny + t.cs - 1) / t.cs;
         t.ncz = (g.nz + t.cs - 1) / t.cs;
-        if ((double)t.ncx * t.ncy * t.ncz >= 4.0e9) return false;
+        t.dir_az = ctx->order_dir_az;
+        t.dir_pol = ctx->order_dir_pol;
+        if ((double)t.ncx * t.ncy * t.ncz * t.dir_az * t.dir_pol >= 4.0e9) return false;
         *out = t;
         return true;
     }
@@ -1275,6 +1282,8 @@ bool tile_params(const recon_ctx* ctx, int mode, TileH* out)
     t.hx = (int)std::ceil(hw / g.vx + 0.125);
     t.hy = (int)std::ceil(hw / g.vy + 0.125);
     t.hz = (int)std::ceil(hw * sin_max / g.vz + 0.125);
+    t.dir_az = 1;
+    t.dir_pol = 1;
     for (int cs = 4; cs >= 2; --cs) {
         t.cs = cs;
         t.ncx = (g.nx + cs - 1) / cs;
@@ -1301,13 +1310,14 @@ recon_status prepare_tiles(recon_ctx* ctx, int mode)
     }
     const double hw = (double)make_tof(ctx).half_window;
     if (tp.valid && tp.ev_gen == ctx->ev_generation && tp.half_window == hw && tp.th.cs == t.cs &&
-        tp.th.hx == t.hx && tp.th.hy == t.hy && tp.th.hz == t.hz && tp.min_events == ctx->tile_min_events &&
+        tp.th.hx == t.hx && tp.th.hy == t.hy && tp.th.hz == t.hz && tp.th.dir_az == t.dir_az &&
+        tp.th.dir_pol == t.dir_pol && tp.min_events == ctx->tile_min_events &&
         tp.mode == mode)
         return RECON_OK;
     tp.valid = false;
     invalidate_graph(ctx);
     const long long n = ctx->n_ev;
-    const long long nc = (long long)t.ncx * t.ncy * t.ncz;
+    const long long nc = (long long)t.ncx * t.ncy * t.ncz * t.dir_az * t.dir_pol;
     const size_t rec = ctx->fmt == FMT_PACKED ? 16 : 32;
     CK(ensure(tp.code, sizeof(unsigned) * (size_t)n));
     CK(ensure(tp.counts, sizeof(unsigned) * (size_t)nc));

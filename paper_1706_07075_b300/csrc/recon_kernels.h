@@ -50,6 +50,7 @@ struct TileH {
     float ox, oy, oz;
     int cs, hx, hy, hz;
     int ncx, ncy, ncz;
+    int dir_az, dir_pol;  // direction bins per cell (azimuth x polar; 1 x 1: none)
 };
 
 enum EventFmt { FMT_F32 = 0, FMT_PACKED = 1 };

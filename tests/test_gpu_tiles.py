@@ -121,3 +121,22 @@ def test_order_and_tile_argument_checks():
             ctx.set_tiled_pass(1, 4)
         ctx.set_event_order(-1)
         ctx.set_event_order(0)
+
+
+def test_direction_binned_order_matches_oracle():
+    ev, lors = tiny_inputs()
+    g = workload_grid("tiny")
+    s_ref = oracle.sensitivity(g, lors)
+    lam_ref, hist = oracle.mlem(g, ev.astype(np.float64), s_ref, 3, SIGMA)
+    with B.Context((150.0, 200.0, 90.0), grid_tuple(g), 300.0) as ctx:
+        ctx.set_sensitivity(s_ref)
+        ctx.set_event_order(2, 8, 4)
+        lam = np.zeros(g.n_vox, np.float32)
+        cons = np.zeros((3, 2))
+        ctx.mlem(B.make_events(ev), 3, None, lam, cons)
+        with pytest.raises(B.ReconError):
+            ctx.set_event_order(2, 0, 4)
+    assert rel_l2(lam, lam_ref) <= 1e-4
+    assert max_rel_above(lam, lam_ref, 0.01) <= 1e-3
+    for k in range(3):
+        assert cons[k, 0] == pytest.approx(hist[k][0], abs=0.5)

@@ -193,15 +193,16 @@ recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float
  * with the cells spread over the blocks that run at the same time (block b of the grid
  * takes block (b * m) mod n of the binned list, m coprime with n): a warp's lines start in
  * one cell (nearby voxels), while concurrent blocks work far apart (no hot voxels).
- * order = -1: the default, cells of 3^3 voxels.  azimuth_bins x polar_bins (each in
- * [1, 64]; 1 x 1, the default: none) further split each cell by the direction of the line
- * (folded so that u_x >= 0: azimuth over (-90, 90] degrees, polar over u_z in [-1, 1]).
- * Same arithmetic; the sums run in another order.  The binning costs one copy of the
- * events and is cached with them (a call that passes host events bins them after its
- * first, upload-overlapped pass).  Measured on B300, 146 M full-body events: 35.5 ms per
- * pass against 47.6 ms in load order (with the series piece masses the autotuner then
- * picks), whatever the cell edge from 1 to 10 voxels.  Errors: EINVAL (order outside
- * [-1, 64], bins outside [1, 64]). */
+ * order = -1: cells of 4^3 voxels.  azimuth_bins x polar_bins (each in [1, 64]; 1 x 1:
+ * none) further split each cell by the direction of the line (folded so that u_x >= 0:
+ * azimuth over (-90, 90] degrees, polar over u_z in [-1, 1]), so that a warp's lines also
+ * run alike.  Default: order -1 with 16 x 8 direction bins.  Same arithmetic; the sums run
+ * in another order.  The binning costs one copy of the events and is cached with them (a
+ * call that passes host events bins them after its first, upload-overlapped pass).
+ * Measured on B300, 146 M full-body events, series piece masses: 47.6 ms per pass in load
+ * order, 35.5 ms with 3^3-voxel cells (about the same for edges of 1 to 10 voxels),
+ * 31.5-31.9 ms with 16 x 8 or 32 x 16 direction bins as well.  Errors: EINVAL (order
+ * outside [-1, 64], bins outside [1, 64]). */
 recon_status recon_set_event_order(recon_ctx* ctx, int32_t order, int32_t azimuth_bins, int32_t polar_bins);
 
 /* Shared-memory tiled event pass for recon_mlem (off by default).  A layout choice for

@@ -139,8 +139,8 @@ struct recon_ctx {
     int tile_mode = 2;    // 0 load order, 1 shared-memory tiles, 2 cell order (default)
     int tile_min_events = 256;  // cells with fewer events take the global-memory pass
     int tile_lanes = 1;         // threads per event in the tiled pass (1 or 8)
-    int order_cell = 3;         // cell edge (voxels) of the cell-ordered pass
-    int order_dir_az = 1, order_dir_pol = 1;  // direction bins within a cell
+    int order_cell = 4;         // cell edge (voxels) of the cell-ordered pass
+    int order_dir_az = 16, order_dir_pol = 8;  // direction bins within a cell
     TilePrep tile_prep;
 };
 
@@ -935,7 +935,7 @@ recon_status recon_set_event_order(recon_ctx* ctx, int32_t order, int32_t azimut
     ctx->order_dir_az = azimuth_bins;
     ctx->order_dir_pol = polar_bins;
     ctx->tile_mode = order != 0 ? 2 : 0;
-    ctx->order_cell = order > 0 ? order : 3;
+    ctx->order_cell = order > 0 ? order : 4;
     invalidate_graph(ctx);
     return RECON_OK;
 }

@@ -220,6 +220,16 @@ def cpu_baseline(ev, lors_for_sens, iters_unit, n_sample):
                       f"150x150x600 grid, sensitivity from {lors_for_sens.shape[1]} LORs; {dt:.1f} s"}
 
 
+def workload_config(args, n, world):
+    """The workload both arms report: the same dictionary for the CUDA arm and the oracle."""
+    return {"workload": "fullbody-146M-150x150x600-4mm", "events": n, "iters_per_step": args.iters,
+            "sensitivity_lors": args.lors, "tof_fwhm_ps": 300.0,
+            "projector": f"sampled TOF kernel, {args.samples} samples" if args.samples else
+            "exact Siddon pieces x Gaussian mass",
+            "l2": "inputs larger than L2 (events 32 B x 146M = 4.7 GB resident)",
+            "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -247,11 +257,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "fullbody-146M-150x150x600-4mm", "events": 146_000_000, "iters_per_step": args.iters,
-                   "sensitivity_lors": args.lors, "tof_fwhm_ps": 300.0,
-                      "projector": f"sampled TOF kernel, {args.samples} samples" if args.samples else
-                      "exact Siddon pieces x Gaussian mass",
-                   "l2": "inputs larger than L2 (events 32 B x 146M = 4.7 GB resident)", "parallelism": "single"},
+        "config": workload_config(args, args.events, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
                          "sample": f"each step: 1 FP64 MLEM iteration over a bounded sample of {n_sample} full-body "
                                    f"events (the 150x150x600 grid, sensitivity from 200000 LORs); the metric counts "
@@ -564,17 +570,15 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "fullbody-146M-150x150x600-4mm", "events": n, "iters_per_step": args.iters,
-                      "sensitivity_lors": args.lors, "tof_fwhm_ps": 300.0,
-                      "launch": {"threads": cfg[0], "blocks_per_sm": cfg[1], "chunk": cfg[2]},
-                      "l2": "inputs larger than L2 (events 32 B x 146M = 4.7 GB resident)",
-                      "parallelism": f"replicas{world}" if world > 1 else "single"},
+           "config": workload_config(args, n, world),
            "e2e": {"value": n * args.iters / e2e_T, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "job_latency_s": e2e_T},
            "gpu_launches": int(stats["kernel_launches"]),
            "clocks": clocks,
            "legs": legs,
            "extra": {"t_generate_s": t_gen, "t_sensitivity_s": t_sens, "t_load_s": t_load,
+                     "launch": {"threads": cfg[0], "blocks_per_sm": cfg[1], "chunk": cfg[2], "cached_pieces": cfg[3],
+                                "piece_mass": cfg[4]},
                      "tiles": {k: v for k, v in ctx.get_info().items() if k.startswith("tile")},
                      "pass_ms": pass_ms, "update_ms": upd_ms, "conservation_last": list(cons[-1])}}
     if rank == 0:

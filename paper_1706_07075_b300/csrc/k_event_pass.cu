@@ -53,36 +53,6 @@ struct PieceCache {
     int stride;  // blockDim.x
 };
 
-// FP32 reductions of a backward sweep, pairing two consecutive pieces in
-// x-adjacent voxels of one aligned 8-byte pair into a single red.v2.f32 (one
-// L2 request instead of two).  `base` is the image, `off` the slab offset of
-// the walk's indices; flush() sends what is still pending.
-struct PairedRed {
-    float* base;
-    long long off;
-    long long pj = -1;   // pending absolute index
-    float pv = 0.f;
-    __device__ __forceinline__ void add(int j, float v)
-    {
-        const long long aj = off + j;
-        if (pj >= 0 && ((aj == pj + 1 && !(pj & 1)) || (aj + 1 == pj && !(aj & 1)))) {
-            const long long lo = aj < pj ? aj : pj;
-            const float vlo = aj < pj ? v : pv, vhi = aj < pj ? pv : v;
-            asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(base + lo), "f"(vlo), "f"(vhi) : "memory");
-            pj = -1;
-            return;
-        }
-        if (pj >= 0) atomicAdd(base + pj, pv);
-        pj = aj;
-        pv = v;
-    }
-    __device__ __forceinline__ void flush()
-    {
-        if (pj >= 0) atomicAdd(base + pj, pv);
-        pj = -1;
-    }
-};
-
 // One event; returns the weight it adds to N_eff (0 when p_i = 0).
 template <int Kind, int Fmt, bool Cached, class TailF>
 __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& t, long long i, bool bf16,
@@ -130,9 +100,7 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
     if (Cached && cnt <= pc.cap) {
         for (int k = 0; k < cnt; ++k) atomicAdd(Cb + pc.j[k * pc.stride + tid], pc.a[k * pc.stride + tid] * r);
     } else {
-        PairedRed pr{a.C, g.vox_offset};
-        walk<true>(g, a.tof, tail, w, [&](int j, float m) { pr.add(j, m * r); });
-        pr.flush();
+        walk<true>(g, a.tof, tail, w, [&](int j, float m) { atomicAdd(Cb + j, m * r); });
     }
     return e.w;
 }

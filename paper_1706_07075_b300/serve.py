@@ -21,7 +21,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-EVENT_BYTES = 32          # resident F32 event record
+EVENT_BYTES = 68          # resident F32 event record (32 B), its cell-ordered copy (32 B) and cell code (4 B)
 IMAGE_BYTES_PER_VOXEL = 20  # lambda, C, s32 (4 B each) + s64 (8 B)
 STAGING_BYTES = (1 << 23) * 32
 

@@ -112,7 +112,7 @@ struct TailOf {
 };
 
 template <int Kind, int Fmt, bool Persistent, bool Cached, int TailK>
-__global__ void __launch_bounds__(256, 6) k_event_pass(PassArgs a, RegionTable tbl, int chunk, int cap)
+__global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl, int chunk, int cap)
 {
     __shared__ SharedTable t;
     __shared__ float neff[kMaxRegions];

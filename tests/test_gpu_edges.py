@@ -189,3 +189,27 @@ def test_kernel_window_changes_the_projector(ctx_tiny):
     p_ref = oracle.forward(g, sub.astype(np.float64), lam.astype(np.float64), SIGMA, K=2.0)
     sel = p_ref > 1e-3 * p_ref.max()
     assert np.max(np.abs(p[sel] - p_ref[sel]) / p_ref[sel]) < 1e-4
+
+
+def test_largest_grid_unit_mass():
+    # 1290^3 voxels (just below the 2^31 limit) of 0.5 mm: the 64-bit voxel offsets of the
+    # walk and of the image kernels at the largest grid the API accepts.  A forward
+    # projection of the constant image 1 gives p_i = 1 (unit TOF mass) for every event
+    # whose +-3 sigma window lies inside the grid, whatever the grid's size.
+    import torch
+    n = 1290
+    g = (n, n, n, 0.5, 0.5, 0.5, -n * 0.25, -n * 0.25, -n * 0.25)
+    rng = np.random.default_rng(44)
+    m = 2000
+    u = rng.normal(size=(m, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    c = rng.uniform(-100, 100, (m, 3))
+    d = rng.uniform(-50, 50, m)
+    ev = np.concatenate([(c + 500 * u).T, (c - 500 * u).T, d[None, :]]).astype(np.float32)
+    with B.Context((400.0, 2400.0, 90.0), g, 300.0) as ctx:
+        ones = torch.ones(n ** 3, dtype=torch.float32, device="cuda")
+        p = torch.zeros(m, dtype=torch.float32, device="cuda")
+        ctx.forward(B.make_events(ev), ones, p)
+        del ones
+        p = p.cpu().numpy()
+    np.testing.assert_allclose(p, 1.0, atol=2e-5)

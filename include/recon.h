@@ -121,6 +121,8 @@ typedef struct {
     int64_t tile_fallback_events;
     int32_t tile_cell_voxels;
     int32_t tile_halo[3];
+    int32_t subsets;           /* OSEM subsets of recon_mlem (1: MLEM); conservation rows per iteration */
+    int32_t lut_samples;       /* samples of the sampled projector (0: exact projector) */
 } recon_info;
 
 typedef struct {

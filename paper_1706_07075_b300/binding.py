@@ -55,7 +55,8 @@ class recon_info(C.Structure):
     _fields_ = [("sigma_mm", C.c_double), ("k_sigma", C.c_double), ("n_vox", C.c_int64),
                 ("n_events_resident", C.c_int64), ("has_sensitivity", C.c_int32), ("num_sms", C.c_int32),
                 ("sens_total", C.c_double), ("tile_cells", C.c_int64), ("tile_events", C.c_int64),
-                ("tile_fallback_events", C.c_int64), ("tile_cell_voxels", C.c_int32), ("tile_halo", C.c_int32 * 3)]
+                ("tile_fallback_events", C.c_int64), ("tile_cell_voxels", C.c_int32), ("tile_halo", C.c_int32 * 3),
+                ("subsets", C.c_int32), ("lut_samples", C.c_int32)]
 
 
 class recon_stats(C.Structure):
@@ -345,7 +346,18 @@ def recon_backproject(ctx, events, r, image_out):
                                                ptr(image_out)))
 
 
+def _check_size(name, arr, need):
+    """Host or device buffers the library writes must hold `need` elements."""
+    if arr is None:
+        return
+    size = arr.size if isinstance(arr, np.ndarray) else (arr.numel() if hasattr(arr, "numel") else None)
+    if size is not None and size < need:
+        raise ValueError(f"{name} holds {size} elements, {need} needed")
+
+
 def recon_mlem(ctx, events, n_iter, init=None, image_out=None, conservation_out=None):
+    if conservation_out is not None:
+        _check_size("conservation_out", conservation_out, 2 * int(n_iter) * recon_get_info(ctx)["subsets"])
     return check(ctx, load().recon_mlem(ctx, C.byref(events) if events is not None else None, int(n_iter),
                                         ptr(init), ptr(image_out), ptr(conservation_out)))
 

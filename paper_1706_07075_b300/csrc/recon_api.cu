@@ -1068,6 +1068,8 @@ recon_status recon_get_info(const recon_ctx* ctx, recon_info* out)
     out->tile_halo[0] = tv ? tp.th.hx : 0;
     out->tile_halo[1] = tv ? tp.th.hy : 0;
     out->tile_halo[2] = tv ? tp.th.hz : 0;
+    out->subsets = ctx->subsets;
+    out->lut_samples = ctx->lut_n;
     return RECON_OK;
 }
 

@@ -143,3 +143,35 @@ def test_preprocess_argument_checks():
             ctx.preprocess(B.make_events(ev), None)
         with pytest.raises(B.ReconError):
             ctx.preprocess(B.make_events(ev), np.zeros(g.n_vox, np.float32), -1.0)
+
+
+def test_preprocess_apply_packed_then_mlem():
+    # packed events keep their weight in FP16: the weighted MLEM then matches the oracle
+    # (same FP16-rounded weights on both sides) to the plain tolerances
+    ev = synth.events("tiny", 120_000, 47)
+    rec = synth.pack_events(ev)
+    q = rec[:, :6].astype(np.float64).T * synth.LATTICE_MM
+    d = rec[:, 6].view(np.float16).astype(np.float64)
+    evq = np.concatenate([q, d[None, :]])
+    g = workload_grid("tiny")
+    mu = synth.mu_image("tiny").astype(np.float64)
+    lors = synth.sensitivity_lors("tiny", 500_000, 47)
+    s_ref = oracle.sensitivity(g, lors)
+    amb = ambiguous(g, evq, mu, np.arange(evq.shape[1]))
+    rec = np.ascontiguousarray(rec[~amb])
+    evq = evq[:, ~amb]
+    w_ref, keep_ref, _ = oracle.preprocess(g, evq, mu, SIGMA, z=Z95)
+    w16 = w_ref.astype(np.float16).astype(np.float64)            # the packed record's FP16 weight
+    lam_ref, hist = oracle.mlem(g, evq, s_ref, 3, SIGMA, weights=w16)
+    with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx:
+        ctx.set_sensitivity(s_ref)
+        kept = ctx.preprocess(B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM), mu.astype(np.float32),
+                              Z95, 1)
+        assert kept == int(keep_ref.sum())
+        lam = np.zeros(g.n_vox, np.float32)
+        cons = np.zeros((3, 2))
+        ctx.mlem(None, 3, None, lam, cons)
+    assert rel_l2(lam, lam_ref) <= 1e-3
+    assert max_rel_above(lam, lam_ref, 0.01) <= 1e-2
+    for k in range(3):
+        assert cons[k, 0] == pytest.approx(hist[k][0], rel=1e-3)

@@ -370,6 +370,20 @@ def time_lut_leg(ctx, B, n, args, stream, img_exact):
             "steps": args.steps}
 
 
+def time_osem_leg(ctx, B, n, args, stream, subsets=5):
+    """List-mode OSEM (NEXT-4): one iteration = `subsets` sub-iterations over
+    consecutive blocks of the resident events (load order; subsets are defined on it)."""
+    import numpy as np
+    ctx.set_subsets(subsets)
+    cons = np.zeros((args.iters * subsets, 2))
+    ctx.mlem(None, args.iters, None, None, cons)                 # warm-up
+    ms = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons))
+    ctx.set_subsets(1)
+    return {"workload": f"fullbody OSEM, {subsets} subsets, {args.iters} iterations per step",
+            "value": n * args.iters * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "conservation_last": [float(x) for x in cons[-1]], "steps": args.steps}
+
+
 def time_median_leg(ctx, B, n, args, stream):
     """The median-filter sieve (Sec. 2.4): one 3x3x3 filter of the full-body image
     (device in, device out) and a full MLEM step with the sieve after every iteration."""
@@ -583,6 +597,7 @@ def run_ours(args):
     if not args.no_legs and not args.samples:
         legs["sampled_lut32"] = time_lut_leg(ctx, B, n, args, stream, img)
         legs["median_sieve"] = time_median_leg(ctx, B, n, args, stream)
+        legs["osem5"] = time_osem_leg(ctx, B, n, args, stream)
         legs["preprocess"] = time_preprocess_leg(ctx, B, synth, n, stream)
         legs["regions"] = time_regions_leg(ctx, B, n, args, stream)
         legs["packed_bf16"] = time_packed_leg(ctx, B, synth, ev, n, args, stream)

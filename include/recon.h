@@ -23,7 +23,10 @@
  * written before the call returns (the call synchronises its stream).  Output
  * pointers may be host or device memory: the copy direction is inferred
  * through unified virtual addressing.  The context owns its device images,
- * its resident copy of the events and the sensitivity image.
+ * its resident copy of the events and the sensitivity image.  Device buffers must
+ * be ready when a call is made: a call orders its work only after what is already
+ * queued on the context's stream (recon_set_stream), so work on other streams that
+ * writes an input or uses an output must be complete (or ordered by the caller).
  *
  * Errors: no call aborts or exits.  Every call returns a recon_status; the
  * message of the last failure is available from recon_last_error().  A CUDA

@@ -147,6 +147,11 @@ def ptr(x):
     if hasattr(x, "data_ptr"):
         if not x.is_contiguous():
             raise ValueError("tensor must be contiguous")
+        if getattr(x, "is_cuda", False):
+            # the library orders its work only after its own stream: torch work still
+            # queued on another stream that writes or reads this tensor must finish first
+            import torch
+            torch.cuda.current_stream(x.device).synchronize()
         return x.data_ptr()
     raise TypeError(f"cannot take the address of {type(x)}")
 

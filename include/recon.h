@@ -115,10 +115,11 @@ typedef struct {
     int32_t has_sensitivity;
     int32_t num_sms;
     double sens_total;         /* sum of s_j over {s_j > 0} */
-    /* binning of the resident events for the shared-memory tiled pass (all 0 when the last
-     * recon_mlem did not use it): non-empty cells, events in them (including those whose
-     * window misses the grid, which contribute nothing), events taking the global-memory
-     * fallback pass, cell edge in voxels, tile halo per axis in voxels */
+    /* binning of the resident events (all 0 when the last recon_mlem did not bin them):
+     * non-empty tiled cells (shared-memory tiled pass only; 0 for the event order), binned
+     * events (including those whose window misses the grid, which contribute nothing),
+     * events taking the global-memory fallback pass, cell edge in voxels, tile halo per
+     * axis in voxels */
     int64_t tile_cells;
     int64_t tile_events;
     int64_t tile_fallback_events;

@@ -108,6 +108,7 @@ __global__ void k_cell_codes(const void* __restrict__ ev, long long n, float lat
             }
         }
     }
+    if (out == kCellNone) out = t.none_code;   // kept in a last bucket, or left out
     code[i] = out;
     if (out < kCellFallback) atomicAdd(counts + out, 1u);
     else if (out == kCellFallback) atomicAdd(n_fallback, 1ull);

@@ -80,6 +80,7 @@ struct TilePrep {
     long long n_fb = 0;
     long long n_binned = 0;
     int mode = 0;
+    int subsets = 1;
     DevBuf code, counts, cursor, begin, scratch, list, ev_cell, ev_fb, misc;
 };
 
@@ -511,10 +512,13 @@ recon_status launch_event_pass(recon_ctx* ctx, const IterPlan& p, const PassArgs
     PassArgs at = a;
     at.events = p.ev_cell;
     if (p.tile_mode == 2) {
-        // cell-ordered events through the global-memory pass, cells spread over blocks
+        // cell-ordered events through the global-memory pass, cells spread over blocks;
+        // an OSEM subset is the same block of the ordered copy (binned block by block)
         RegionTable tc = t;
-        at.n = p.n_cell_events;
-        tc.ev_begin[1] = p.n_cell_events;
+        at.events = static_cast<const char*>(p.ev_cell) +
+                    (static_cast<const char*>(a.events) - static_cast<const char*>(p.a.events));
+        at.n = a.n;
+        tc.ev_begin[1] = a.n;
         at.block_mul = spread_multiplier(pass_blocks(p.cfg, at.n, ctx->num_sms));
         if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
         CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, at, tc, ctx->num_sms, ctx->stream));
@@ -1242,7 +1246,7 @@ recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const
 // by the scanner's axial acceptance (events beyond it take the fallback pass).
 bool tile_params(const recon_ctx* ctx, int mode, TileH* out)
 {
-    if (mode == 0 || ctx->subsets != 1 || (mode == 1 && ctx->lut_n > 0)) return false;
+    if (mode == 0 || (mode == 1 && (ctx->lut_n > 0 || ctx->subsets != 1))) return false;
     const recon_grid& g = ctx->grid;
     if (mode == 2) {
         // event order only: cells of 3^3 voxels, a halo covering the grid (no fallback)
@@ -1265,7 +1269,9 @@ bool tile_params(const recon_ctx* ctx, int mode, TileH* out)
         t.ncz = (g.nz + t.cs - 1) / t.cs;
         t.dir_az = ctx->order_dir_az;
         t.dir_pol = ctx->order_dir_pol;
-        if ((double)t.ncx * t.ncy * t.ncz * t.dir_az * t.dir_pol >= 4.0e9) return false;
+        const double keys = (double)t.ncx * t.ncy * t.ncz * t.dir_az * t.dir_pol;
+        if (keys + 1 >= 4.0e9) return false;
+        t.none_code = (unsigned)keys;   // events whose window misses the grid: a last bucket
         *out = t;
         return true;
     }
@@ -1286,6 +1292,7 @@ bool tile_params(const recon_ctx* ctx, int mode, TileH* out)
     t.hz = (int)std::ceil(hw * sin_max / g.vz + 0.125);
     t.dir_az = 1;
     t.dir_pol = 1;
+    t.none_code = 0xFFFFFFFFu;
     for (int cs = 4; cs >= 2; --cs) {
         t.cs = cs;
         t.ncx = (g.nx + cs - 1) / cs;
@@ -1314,48 +1321,77 @@ recon_status prepare_tiles(recon_ctx* ctx, int mode)
     if (tp.valid && tp.ev_gen == ctx->ev_generation && tp.half_window == hw && tp.th.cs == t.cs &&
         tp.th.hx == t.hx && tp.th.hy == t.hy && tp.th.hz == t.hz && tp.th.dir_az == t.dir_az &&
         tp.th.dir_pol == t.dir_pol && tp.min_events == ctx->tile_min_events &&
-        tp.mode == mode)
+        tp.mode == mode && tp.subsets == (mode == 2 ? std::max(1, ctx->subsets) : 1))
         return RECON_OK;
     tp.valid = false;
     invalidate_graph(ctx);
     const long long n = ctx->n_ev;
-    const long long nc = (long long)t.ncx * t.ncy * t.ncz * t.dir_az * t.dir_pol;
+    // keys: cells x direction bins, plus the bucket of events whose window misses the grid
+    const long long nc = (long long)t.ncx * t.ncy * t.ncz * t.dir_az * t.dir_pol + (mode == 2 ? 1 : 0);
     const size_t rec = ctx->fmt == FMT_PACKED ? 16 : 32;
-    CK(ensure(tp.code, sizeof(unsigned) * (size_t)n));
+    // OSEM: each subset's block of the list is binned on its own, in place, so that
+    // the blocks keep their events (every event is binned in the event order)
+    const int blocks = mode == 2 ? std::max(1, ctx->subsets) : 1;
+    const long long nb_max = (n + blocks - 1) / blocks;
+    CK(ensure(tp.code, sizeof(unsigned) * (size_t)std::max(nb_max, 1LL)));
     CK(ensure(tp.counts, sizeof(unsigned) * (size_t)nc));
     CK(ensure(tp.cursor, sizeof(unsigned) * (size_t)nc));
     CK(ensure(tp.begin, sizeof(long long) * (size_t)(nc + 1)));
     CK(ensure(tp.scratch, sizeof(long long) * (size_t)scan_scratch_elems(nc)));
     CK(ensure(tp.list, sizeof(unsigned) * (size_t)nc));
     CK(ensure(tp.misc, 64));
-    CK(cudaMemsetAsync(tp.counts.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
-    CK(cudaMemsetAsync(tp.cursor.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
     CK(cudaMemsetAsync(tp.misc.p, 0, 64, ctx->stream));
     unsigned long long* n_fb_dev = tp.misc.as<unsigned long long>();
     unsigned long long* fb_cursor = n_fb_dev + 1;
     unsigned* n_list_dev = reinterpret_cast<unsigned*>(n_fb_dev + 2);
-    CK(launch_cell_codes(ctx->ev.p, ctx->fmt, n, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
-                         tp.counts.as<unsigned>(), n_fb_dev, ctx->stream));
-    CK(launch_cell_list(tp.counts.as<unsigned>(), nc, mode == 2 ? 1u : (unsigned)ctx->tile_min_events,
-                        tp.list.as<unsigned>(),
-                        n_list_dev, n_fb_dev, ctx->stream));
-    CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
-                        ctx->stream));
-    unsigned long long host_misc[3] = {0, 0, 0};
-    long long binned = 0;
-    CK(cudaMemcpyAsync(host_misc, tp.misc.p, sizeof host_misc, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(&binned, tp.begin.as<long long>() + nc, sizeof binned, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    tp.n_fb = (long long)host_misc[0];
-    tp.n_list = (unsigned)(host_misc[2] & 0xFFFFFFFFu);
-    CK(ensure(tp.ev_cell, rec * (size_t)std::max(binned, 1LL)));
-    CK(ensure(tp.ev_fb, rec * (size_t)std::max(tp.n_fb, 1LL)));
-    CK(launch_cell_scatter(ctx->ev.p, ctx->fmt, n, tp.code.as<unsigned>(), tp.begin.as<long long>(),
-                           tp.cursor.as<unsigned>(), tp.ev_cell.p, tp.ev_fb.p, fb_cursor, ctx->stream));
-    ctx->stats.kernel_launches += 7;
+    if (mode == 2) {
+        CK(ensure(tp.ev_cell, rec * (size_t)n));
+        CK(ensure(tp.ev_fb, rec));
+        for (int b = 0; b < blocks; ++b) {
+            const long long lo = b * n / blocks, hi = (b + 1) * n / blocks;
+            if (hi <= lo) continue;
+            const void* src = static_cast<const char*>(ctx->ev.p) + (size_t)lo * rec;
+            void* dst = static_cast<char*>(tp.ev_cell.p) + (size_t)lo * rec;
+            CK(cudaMemsetAsync(tp.counts.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
+            CK(cudaMemsetAsync(tp.cursor.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
+            CK(launch_cell_codes(src, ctx->fmt, hi - lo, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
+                                 tp.counts.as<unsigned>(), n_fb_dev, ctx->stream));
+            CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
+                                ctx->stream));
+            CK(launch_cell_scatter(src, ctx->fmt, hi - lo, tp.code.as<unsigned>(), tp.begin.as<long long>(),
+                                   tp.cursor.as<unsigned>(), dst, tp.ev_fb.p, fb_cursor, ctx->stream));
+            ctx->stats.kernel_launches += 5;
+        }
+        tp.n_fb = 0;
+        tp.n_list = 0;
+        tp.n_binned = n;
+    } else {
+        CK(cudaMemsetAsync(tp.counts.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
+        CK(cudaMemsetAsync(tp.cursor.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
+        CK(launch_cell_codes(ctx->ev.p, ctx->fmt, n, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
+                             tp.counts.as<unsigned>(), n_fb_dev, ctx->stream));
+        CK(launch_cell_list(tp.counts.as<unsigned>(), nc, (unsigned)ctx->tile_min_events, tp.list.as<unsigned>(),
+                            n_list_dev, n_fb_dev, ctx->stream));
+        CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
+                            ctx->stream));
+        unsigned long long host_misc[3] = {0, 0, 0};
+        long long binned = 0;
+        CK(cudaMemcpyAsync(host_misc, tp.misc.p, sizeof host_misc, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(&binned, tp.begin.as<long long>() + nc, sizeof binned, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        tp.n_fb = (long long)host_misc[0];
+        tp.n_list = (unsigned)(host_misc[2] & 0xFFFFFFFFu);
+        CK(ensure(tp.ev_cell, rec * (size_t)std::max(binned, 1LL)));
+        CK(ensure(tp.ev_fb, rec * (size_t)std::max(tp.n_fb, 1LL)));
+        CK(launch_cell_scatter(ctx->ev.p, ctx->fmt, n, tp.code.as<unsigned>(), tp.begin.as<long long>(),
+                               tp.cursor.as<unsigned>(), tp.ev_cell.p, tp.ev_fb.p, fb_cursor, ctx->stream));
+        ctx->stats.kernel_launches += 7;
+        tp.n_binned = binned;
+    }
     tp.th = t;
-    tp.n_binned = binned;
     tp.mode = mode;
+    tp.subsets = blocks;
     tp.min_events = ctx->tile_min_events;
     tp.half_window = hw;
     tp.n_cells = nc;
@@ -1368,8 +1404,8 @@ recon_status prepare_tiles(recon_ctx* ctx, int mode)
 void plan_tiles(recon_ctx* ctx, IterPlan& p)
 {
     const TilePrep& tp = ctx->tile_prep;
-    p.tiled = tp.valid && tp.ev_gen == ctx->ev_generation && p.subsets == 1 && p.n_regions == 1 &&
-              (tp.mode == 2 || p.a.lut.n == 0);
+    p.tiled = tp.valid && tp.ev_gen == ctx->ev_generation && p.n_regions == 1 && tp.subsets == p.subsets &&
+              (tp.mode == 2 || (p.subsets == 1 && p.a.lut.n == 0));
     if (!p.tiled) return;
     p.th = tp.th;
     p.list = tp.list.as<unsigned>();

@@ -51,6 +51,7 @@ struct TileH {
     int cs, hx, hy, hz;
     int ncx, ncy, ncz;
     int dir_az, dir_pol;  // direction bins per cell (azimuth x polar; 1 x 1: none)
+    unsigned none_code;   // code of events whose window misses the grid (0xFFFFFFFF: left out)
 };
 
 enum EventFmt { FMT_F32 = 0, FMT_PACKED = 1 };

@@ -102,7 +102,7 @@ def test_cell_ordered_pass_matches_oracle():
         cons = np.zeros((5, 2))
         ctx.mlem(B.make_events(ev), 5, None, lam, cons)
         info = ctx.get_info()
-    assert info["tile_cells"] > 0 and info["tile_fallback_events"] == 0
+    assert info["tile_events"] == ev.shape[1] and info["tile_fallback_events"] == 0
     assert rel_l2(lam, lam_ref) <= 1e-4
     assert max_rel_above(lam, lam_ref, 0.01) <= 1e-3
     for k in range(5):

@@ -166,7 +166,8 @@ def measure_probes(n_vox, stream, dev):
     import torch
     from paper_1706_07075_b300 import build as lib_build
     lib = C.CDLL(lib_build.build_probe())
-    for name in ("recon_probe_l2_red", "recon_probe_gather", "recon_probe_erfc", "recon_probe_mixed"):
+    for name in ("recon_probe_l2_red", "recon_probe_gather", "recon_probe_erfc", "recon_probe_mixed",
+                 "recon_probe_l2_stream"):
         getattr(lib, name).restype = C.c_int
     img = torch.zeros(n_vox, dtype=torch.float32, device=dev)
     sink = torch.zeros(148 * 64 * 256, dtype=torch.float32, device=dev)
@@ -186,6 +187,10 @@ def measure_probes(n_vox, stream, dev):
         out["mixed_gsteps"] = v.value / 1e9
     if lib.recon_probe_erfc(C.c_void_p(sink.data_ptr()), h, C.byref(v)) == 0:
         out["erfc_gops"] = v.value / 1e9
+    n4 = n_vox - n_vox % 4
+    if n4 > 0 and lib.recon_probe_l2_stream(C.c_void_p(img.data_ptr()), C.c_int64(n4), 20,
+                                            C.c_void_p(sink.data_ptr()), h, C.byref(v)) == 0:
+        out["l2_stream_gbs"] = v.value / 1e9
     torch.cuda.synchronize(dev)
     return out
 
@@ -643,18 +648,21 @@ def run_ours(args):
         # events in the bench's event order and launch (dram__bytes_read.sum +
         # dram__bytes_write.sum); the traffic grows with the events, so it is scaled.
         traffic = TRAFFIC_BYTES_PER_EVENT * n if not args.samples else None
-        R, G = probes.get("l2_red_gops"), probes.get("gather_gops")
+        R, G, L2BW = probes.get("l2_red_gops"), probes.get("gather_gops"), probes.get("l2_stream_gbs")
         sm_mhz = (clocks.get("sm_mhz") or 2032.0) if isinstance(clocks, dict) else 2032.0
         alu_peak = 148 * 128 * sm_mhz * 1e6                      # FP32 lane operations per second
         pieces_s = pass_ms / 1e3
         terms = {"hbm": (32.0 * n) / (peaks["hbm_gbs"] * 1e9),
                  "l2_reductions": visits / (R * 1e9) if R else 0.0,
                  "l2_gathers": visits / (G * 1e9) if G else 0.0,
+                 # every gather and every reduction touches one 32-byte L2 sector
+                 "l2_sectors": visits * 2 * 32.0 / (L2BW * 1e9) if L2BW else 0.0,
                  "alu": visits * ALU_OPS_PER_PIECE / alu_peak}
         bound = max(terms, key=terms.get)
         rates = {"hbm": (32.0 * n / pieces_s / 1e9, peaks["hbm_gbs"], "GB/s"),
                  "l2_reductions": (visits / pieces_s / 1e9, R, "Gred/s"),
                  "l2_gathers": (visits / pieces_s / 1e9, G, "Ggather/s"),
+                 "l2_sectors": (visits * 64.0 / pieces_s / 1e9, L2BW, "GB/s"),
                  "alu": (visits * ALU_OPS_PER_PIECE / pieces_s / 1e12, alu_peak / 1e12, "Tops/s")}
         ach, pk, unit = rates[bound]
         out["roofline"] = {
@@ -666,8 +674,8 @@ def run_ours(args):
             "per_launch": {"events": n, "pieces": visits, "gathers": visits, "reductions": visits,
                            "hbm_bytes": 32.0 * n, "pass_ms": pass_ms},
             "peak_source": "live probes on an L2-resident image of the grid's size (scattered "
-                           "red.global.add.f32 and 4-byte gathers); HBM from MEASURED_PEAKS; ALU from "
-                           "148 SMs x 128 lanes x sampled SM clock",
+                           "red.global.add.f32, 4-byte gathers, coalesced 16-byte reads for the L2 sector "
+                           "bandwidth); HBM from MEASURED_PEAKS; ALU from 148 SMs x 128 lanes x sampled SM clock",
             "mixed_probe_gsteps": probes.get("mixed_gsteps"),
             "secondary": {"hbm_gbs": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
                           "hbm_peak_source": src}}

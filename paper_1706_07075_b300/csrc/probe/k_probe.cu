@@ -74,6 +74,20 @@ __global__ void k_erfc(int per_thread, float* sink)
     if (acc == 1234.5f) sink[t] = acc;
 }
 
+// Each thread sums float4s of the buffer at a grid stride, `passes` sweeps.
+__global__ void k_l2_stream(const float4* __restrict__ img, long long n4, int passes, float* sink)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    float acc = 0.f;
+    for (int p = 0; p < passes; ++p)
+        for (long long i = t; i < n4; i += stride) {
+            const float4 v = __ldcg(img + i);
+            acc += v.x + v.y + v.z + v.w;
+        }
+    if (acc == 1234.5f) sink[t] = acc;
+}
+
 template <class F>
 int time_it(cudaStream_t s, F&& launch, double ops, double* out_ops_per_s)
 {
@@ -131,4 +145,17 @@ extern "C" int recon_probe_erfc(float* sink, void* stream, double* ops_per_s)
     const int threads = 256, blocks = 148 * 64, per_thread = 2048;
     return time_it(s, [&] { k_erfc<<<blocks, threads, 0, s>>>(per_thread, sink); },
                    (double)blocks * threads * per_thread, ops_per_s);
+}
+
+extern "C" int recon_probe_l2_stream(const float* img, int64_t n_words, int32_t passes, float* sink, void* stream,
+                                     double* bytes_per_s)
+{
+    if (!img || !sink || n_words <= 0 || (n_words & 3) || passes < 1 || !bytes_per_s) return 1;
+    if (reinterpret_cast<uintptr_t>(img) % 16) return 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int threads = 256, blocks = 148 * 64;
+    const long long n4 = n_words / 4;
+    return time_it(s, [&] { k_l2_stream<<<blocks, threads, 0, s>>>(reinterpret_cast<const float4*>(img), n4, passes,
+                                                                  sink); },
+                   (double)n_words * 4.0 * passes, bytes_per_s);
 }

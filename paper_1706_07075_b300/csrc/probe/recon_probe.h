@@ -33,6 +33,12 @@ int recon_probe_mixed(const float* lam, float* C, int64_t n_words, float* sink, 
 /* erfcf evaluations per second (FP32 ALU); sink: 148*64*256 floats. */
 int recon_probe_erfc(float* sink, void* stream, double* ops_per_s);
 
+/* L2 read bandwidth: coalesced 16-byte reads sweeping img[0..n_words) (n_words a
+ * multiple of 4, the buffer L2-resident after the warm-up run) `passes` times;
+ * *bytes_per_s = bytes read per second; sink: 148*64*256 floats. */
+int recon_probe_l2_stream(const float* img, int64_t n_words, int32_t passes, float* sink, void* stream,
+                          double* bytes_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -174,7 +174,7 @@ class LibreconExecutor:
     """Runs jobs through librecon: one CUDA stream per slot, contexts reused per
     grid, sensitivity images resident per key."""
 
-    def __init__(self, slots, device=0, sensitivities=None, keep_results=True, launch=(192, 0, 0, 0, 2)):
+    def __init__(self, slots, device=0, sensitivities=None, keep_results=True, launch=(128, 0, 0, 0, 2)):
         import torch
         from . import binding as B
         self.B = B

@@ -31,6 +31,9 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   preprocess .......... pinned (closed-form line integrals through uniform
                         boxes and a sphere; rejection decided by hand-built
                         events inside, outside and at the 1.96 sigma edge)
+  start_backprojection  pinned (equals one MLEM iteration from a uniform
+                        image when every event's window lies in the mask;
+                        dense-matrix form A^T w / s)
   osem ................ pinned (dense textbook OSEM on an 8x8x8 grid built
                         by brute force; sum s lambda = B N_eff per
                         sub-iteration; B = 1 is MLEM)
@@ -57,5 +60,5 @@ from .core import (  # noqa: F401
     trace,
 )
 from .filters import median3, median3_at, sieve  # noqa: F401
-from .mlem import (mlem, mlem_regions, osem, region_bounds, region_slabs, slab_grid, stitch,  # noqa: F401
-                   subset_ranges)
+from .mlem import (mlem, mlem_regions, osem, region_bounds, region_slabs, slab_grid, start_backprojection,  # noqa
+                   stitch, subset_ranges)

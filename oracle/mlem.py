@@ -36,6 +36,22 @@ def uniform_start(sens, weights_total):
     return lam
 
 
+def start_backprojection(grid, events, sens, sigma, K=3.0, weights=None, threads=None):
+    """Starting image from a backprojection of the events (Sec. 3.5.4 and Table 2
+    seed MLEM with a "starting backprojection"; its normalisation is not given).
+    Reading: lambda0_j = sum_i a_ij w_i / s_j on {s_j > 0}, 0 elsewhere, i.e. the
+    events' TOF-weighted backprojection divided by the sensitivity, so that
+    sum_j s_j lambda0_j = sum_i w_i (mass of event i's window inside the mask)."""
+    s = np.asarray(sens, np.float64).reshape(-1)
+    n = np.asarray(events[0]).shape[0]
+    w = np.ones(n) if weights is None else np.asarray(weights, np.float64)
+    bp = backproject(grid, events, w, sigma, K, threads)
+    lam = np.zeros_like(s)
+    mask = s > 0
+    lam[mask] = bp[mask] / s[mask]
+    return lam
+
+
 def mlem(grid, events, sens, n_iter, sigma, K=3.0, weights=None, init=None, threads=None, return_p=False,
          lut_samples=None, median=False):
     """Run n_iter MLEM iterations.

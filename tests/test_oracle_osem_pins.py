@@ -50,3 +50,22 @@ def test_subset_ranges_partition_the_list():
         r = oracle.subset_ranges(n, B)
         assert r[0][0] == 0 and r[-1][1] == n
         assert all(a[1] == b[0] for a, b in zip(r[:-1], r[1:]))
+
+
+def test_start_backprojection_dense_and_first_iteration():
+    g, sigma, ev, lors = small_problem(33, n_ev=500, n_lor=1500)
+    A = dense_system(g, ev, sigma, 3.0)
+    s_dense = dense_chords(g, lors)
+    s = oracle.sensitivity(g, lors)
+    lam0 = oracle.start_backprojection(g, ev, s, sigma, 3.0)
+    mask = s_dense > 0
+    ref = np.where(mask, (A.T @ np.ones(A.shape[0])) / np.where(mask, s_dense, 1.0), 0.0)
+    assert np.max(np.abs(lam0 - ref)) <= 1e-11 * np.max(ref)
+    # with a positive sensitivity everywhere, one MLEM iteration from a constant image
+    # of events whose windows lie inside the grid is the starting backprojection
+    s_pos = np.full(g.n_vox, 7.0)
+    inside = np.isclose(A.sum(axis=1), 1.0, rtol=1e-12)
+    ev_in = [e[inside] for e in ev]
+    lam1, _ = oracle.mlem(g, ev_in, s_pos, 1, sigma, 3.0)
+    np.testing.assert_allclose(lam1, oracle.start_backprojection(g, ev_in, s_pos, sigma, 3.0), rtol=1e-11,
+                               atol=1e-15)

@@ -234,6 +234,15 @@ recon_status recon_set_event_order(recon_ctx* ctx, int32_t order, int32_t azimut
  * EINVAL (on < 0, lanes not 1 or 8). */
 recon_status recon_set_tiled_pass(recon_ctx* ctx, int32_t on, int32_t lanes);
 
+/* Start image of recon_mlem when init is NULL.  mode 0 (default): uniform on {s_j > 0}
+ * with sum_j s_j lambda_j = sum_i w_i.  mode 1: the starting backprojection that seeds
+ * the paper's MLEM (Sec. 3.5.4, Table 2), read as lambda0_j = (sum_i a_ij w_i) / s_j on
+ * {s_j > 0} (the events' TOF-weighted backprojection over the sensitivity; the paper does
+ * not give its normalisation).  Mode 1 needs all events before the first iteration, so a
+ * call with host events then uploads them first instead of overlapping the upload with the
+ * first pass.  Errors: EINVAL (mode not 0 or 1). */
+recon_status recon_set_start_image(recon_ctx* ctx, int32_t mode);
+
 /* List-mode OSEM for recon_mlem (OSEM is named in the title of Sec. 2.4; the paper
  * itself reconstructs with MLEM).  n_subsets = B > 1: each iteration runs B
  * sub-iterations; sub-iteration b uses the events of block b of the list,

@@ -77,6 +77,7 @@ SIGNATURES = {
     "recon_set_projector": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "recon_set_median_filter": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_subsets": (C.c_int, [_CTX, C.c_int32]),
+    "recon_set_start_image": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_tiled_pass": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "recon_set_event_order": (C.c_int, [_CTX, C.c_int32, C.c_int32, C.c_int32]),
     "recon_preprocess": (C.c_int, [_CTX, C.POINTER(recon_events), _VP, C.c_double, C.c_int32, _VP, _VP,
@@ -252,6 +253,11 @@ def recon_set_tiled_pass(ctx, on, lanes=1):
     """0: off; 1: on (cells of >= 256 events); m > 1: on with cells of >= m events.
     lanes: threads per event (1 or 8)."""
     return check(ctx, load().recon_set_tiled_pass(ctx, int(on), int(lanes)))
+
+
+def recon_set_start_image(ctx, mode):
+    """0: uniform start image; 1: starting backprojection."""
+    return check(ctx, load().recon_set_start_image(ctx, int(mode)))
 
 
 def recon_set_subsets(ctx, n_subsets):

@@ -155,6 +155,14 @@ __global__ void __launch_bounds__(kImgThreads) k_reduce_weights(const float4* __
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
+// Per-event weights w_i of the resident records into out[n].
+__global__ void k_event_weights(const float4* __restrict__ ev, const int4* __restrict__ pk, long long n,
+                                float* __restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = ev ? ev[2 * i + 1].w : __half2float(__ushort_as_half((unsigned short)((unsigned)pk[i].w >> 16)));
+}
+
 struct StitchTable {
     int n;
     long long vox[kMaxRegions + 1];
@@ -274,6 +282,13 @@ cudaError_t launch_stitch(const float* slabs, const long long* reg_vox, const in
     }
     long long n = (long long)nx * ny * nz;
     k_stitch<<<grid_for(n, kImgThreads), kImgThreads, 0, st>>>(slabs, t, nx, ny, nz, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_event_weights(const float4* ev_f32, const int4* ev_packed, long long n, float* out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_event_weights<<<grid_for(n, kImgThreads), kImgThreads, 0, st>>>(ev_f32, ev_packed, n, out);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,7 @@ struct recon_ctx {
     int lut_n = 0;   // samples of the sampled TOF kernel; 0: exact projector
     bool median = false;  // median-filter sieve after every iteration
     int subsets = 1;      // OSEM subsets of recon_mlem (1: MLEM)
+    int start_mode = 0;   // 0: uniform start image, 1: starting backprojection
     int device = 0, num_sms = 148;
     cudaStream_t own_stream = nullptr, stream = nullptr;
     cudaStream_t copy_stream = nullptr;            // host-to-device copies of the streamed first pass
@@ -921,6 +922,14 @@ recon_status recon_set_projector(recon_ctx* ctx, int32_t projector, int32_t n_sa
     return RECON_OK;
 }
 
+recon_status recon_set_start_image(recon_ctx* ctx, int32_t mode)
+{
+    CHECK_CTX();
+    if (mode != 0 && mode != 1) return fail(ctx, RECON_EINVAL, "mode must be 0 or 1");
+    ctx->start_mode = mode;
+    return RECON_OK;
+}
+
 recon_status recon_set_subsets(recon_ctx* ctx, int32_t n_subsets)
 {
     CHECK_CTX();
@@ -1512,7 +1521,7 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     CHECK_CTX();
     if (n_iter < 0) return fail(ctx, RECON_EINVAL, "n_iter is negative");
     if ((long long)n_iter * ctx->subsets > (1LL << 24)) return fail(ctx, RECON_EINVAL, "n_iter x subsets too large");
-    const bool streamed = can_stream(ctx, events, n_iter) && ctx->have_sens;
+    const bool streamed = can_stream(ctx, events, n_iter) && ctx->have_sens && (init || ctx->start_mode == 0);
     // event order / tiles (mode 2, cell order, is the default)
     const int mode = ctx->tile_mode;
     if (streamed) {
@@ -1527,6 +1536,29 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     const long long nv = ctx->n_vox;
     if (init) {
         CK(cudaMemcpyAsync(ctx->lam.p, init, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
+    } else if (ctx->start_mode == 1) {
+        // starting backprojection: lambda0 = (sum_i a_ij w_i) / s_j on the mask, from a
+        // backward pass with r_i = w_i and the update applied to lambda = 1
+        const bool packed = ctx->fmt == FMT_PACKED;
+        CK(ensure(ctx->vec, sizeof(float) * (size_t)std::max(1LL, ctx->n_ev)));
+        CK(launch_event_weights(packed ? nullptr : ctx->ev.as<float4>(), packed ? ctx->ev.as<int4>() : nullptr,
+                                ctx->n_ev, ctx->vec.as<float>(), ctx->stream));
+        CK(launch_fill_masked(ctx->lam.as<float>(), ctx->s32.as<float>(), nv, 1.f, ctx->stream));
+        CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
+        PassArgs b = base_args(ctx, ctx->ev.p, ctx->n_ev);
+        b.C = ctx->C.as<float>();
+        b.r_in = ctx->vec.as<float>();
+        const RegionTable bt = single_table(ctx);
+        const LaunchCfg bc = ctx->user_cfg ? ctx->cfg : default_cfg();
+        CK(launch_pass(PASS_BACK, (EventFmt)ctx->fmt, bc, b, bt, ctx->num_sms, ctx->stream));
+        const int bpr = update_blocks(nv);
+        CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)bpr));
+        CK(ensure(ctx->reg_vox, sizeof(long long) * 2));
+        const long long rv0[2] = {0, nv};
+        CK(cudaMemcpyAsync(ctx->reg_vox.p, rv0, sizeof rv0, cudaMemcpyHostToDevice, ctx->stream));
+        CK(launch_update(ctx->lam.as<float>(), ctx->C.as<float>(), ctx->s32.as<float>(), nullptr,
+                         ctx->reg_vox.as<long long>(), 1, ctx->upd_partial.as<double>(), bpr, ctx->stream));
+        ctx->stats.kernel_launches += 4;
     } else {
         const double v = ctx->sens_total > 0 ? ctx->w_total / ctx->sens_total : 0.0;
         CK(launch_fill_masked(ctx->lam.as<float>(), ctx->s32.as<float>(), nv, (float)v, ctx->stream));

@@ -151,6 +151,8 @@ cudaError_t launch_median3(const float* in, float* out, const float* s32, uint16
 cudaError_t launch_ingest_f32(const float* const* planes, const float* weight, long long n, float4* out,
                               cudaStream_t st);
 cudaError_t launch_ingest_packed(const int4* rec, const float* weight, long long n, int4* out, cudaStream_t st);
+// Event weights of the resident records into out[n] (float).
+cudaError_t launch_event_weights(const float4* ev_f32, const int4* ev_packed, long long n, float* out, cudaStream_t st);
 // Per-block FP64 sums of the event weights in partial[blocks].
 cudaError_t launch_reduce_weights(const float4* ev_f32, const int4* ev_packed, long long n, double* partial,
                                   int blocks, cudaStream_t st);

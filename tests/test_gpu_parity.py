@@ -146,3 +146,22 @@ def test_piece_mass_forms_match_oracle(tiny, tail_eval):
     lam_ref, _ = oracle.mlem(g, ev.astype(np.float64), s_ref, 3, SIGMA)
     assert rel_l2(img, lam_ref) <= 1e-4
     assert max_rel_above(img, lam_ref, 0.01) <= 1e-3
+
+
+def test_starting_backprojection_matches_oracle(tiny):
+    g, ev, lors, s_ref, ctx = tiny
+    ctx.set_sensitivity(s_ref)
+    ctx.set_start_image(1)
+    lam0 = np.zeros(g.n_vox, np.float32)
+    ctx.mlem(B.make_events(ev), 0, None, lam0)                 # no iteration: the start image itself
+    lam3 = np.zeros(g.n_vox, np.float32)
+    ctx.mlem(None, 3, None, lam3)
+    ctx.set_start_image(0)
+    ref0 = oracle.start_backprojection(g, ev.astype(np.float64), s_ref, SIGMA)
+    assert rel_l2(lam0, ref0) < 1e-5
+    assert max_rel_above(lam0, ref0, 0.01) < 1e-4
+    ref3, _ = oracle.mlem(g, ev.astype(np.float64), s_ref, 3, SIGMA, init=ref0)
+    assert rel_l2(lam3, ref3) <= 1e-4
+    assert max_rel_above(lam3, ref3, 0.01) <= 1e-3
+    with pytest.raises(B.ReconError):
+        ctx.set_start_image(2)

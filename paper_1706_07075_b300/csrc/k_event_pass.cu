@@ -177,6 +177,34 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
 // voxel are merged, so a voxel costs one gather and one reduction however
 // many samples it holds.
 
+// FP32 reductions of one event's backward sweep, two consecutive visits of
+// memory-adjacent voxels of one aligned 8-byte pair sent as one
+// red.global.add.v2.f32 (one L2 request instead of two).  Indices are absolute
+// (image base + slab offset + voxel); flush() sends what is still pending.
+struct PairedRed {
+    float* base;
+    long long pj = -1;
+    float pv = 0.f;
+    __device__ __forceinline__ void add(long long aj, float v)
+    {
+        if (pj >= 0 && ((aj == pj + 1 && !(pj & 1)) || (aj + 1 == pj && !(aj & 1)))) {
+            const long long lo = aj < pj ? aj : pj;
+            const float vlo = aj < pj ? v : pv, vhi = aj < pj ? pv : v;
+            asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(base + lo), "f"(vlo), "f"(vhi) : "memory");
+            pj = -1;
+            return;
+        }
+        if (pj >= 0) atomicAdd(base + pj, pv);
+        pj = aj;
+        pv = v;
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if (pj >= 0) atomicAdd(base + pj, pv);
+        pj = -1;
+    }
+};
+
 struct LutLine {
     float ax, ay, az, bx, by, bz;
     bool valid;
@@ -259,7 +287,9 @@ __device__ __forceinline__ float do_event_lut(const PassArgs& a, const SharedTab
     }
     if (!(p > 0.f)) return 0.f;
     const float r = e.w / p;
-    lut_walk<NS>(g, a.lut, l, [&](int j, float w) { atomicAdd(Cb + j, w * r); });
+    PairedRed pr{a.C};
+    lut_walk<NS>(g, a.lut, l, [&](int j, float w) { pr.add(g.vox_offset + j, w * r); });
+    pr.flush();
     return e.w;
 }
 

@@ -99,25 +99,6 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
     const float r = e.w / p * hin;
     if (Cached && cnt <= pc.cap) {
         for (int k = 0; k < cnt; ++k) atomicAdd(Cb + pc.j[k * pc.stride + tid], pc.a[k * pc.stride + tid] * r);
-    } else if ((g.vox_offset & 1) == 0) {
-        // consecutive pieces in the two voxels of one aligned pair ((j ^ jp) == 1)
-        // go out as one red.global.add.v2.f32
-        int jp = -1;
-        float vp = 0.f;
-        walk<true>(g, a.tof, tail, w, [&](int j, float m) {
-            const float v = m * r;
-            if ((j ^ jp) == 1) {
-                const float lo = (j & 1) ? vp : v, hi = (j & 1) ? v : vp;
-                asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(Cb + (j & ~1)), "f"(lo), "f"(hi)
-                             : "memory");
-                jp = -1;
-            } else {
-                if (jp >= 0) atomicAdd(Cb + jp, vp);
-                jp = j;
-                vp = v;
-            }
-        });
-        if (jp >= 0) atomicAdd(Cb + jp, vp);
     } else {
         walk<true>(g, a.tof, tail, w, [&](int j, float m) { atomicAdd(Cb + j, m * r); });
     }

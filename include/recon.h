@@ -102,9 +102,9 @@ typedef struct {
     int32_t tail_eval;         /* Gaussian mass of each piece from the tails erfc(|tau|/(sigma sqrt 2)) at
                                   its two ends, by 0: t exp(-x^2 + P(t)), t = 1/(1 + x/2), with a fitted
                                   degree-10 P (relative error ~6e-7 at K = 3), 1: CUDA's erfcf; or
-                                  2: the Taylor series of the integral about the piece's midpoint to the
-                                  h^4 term (Hermite polynomials; error below 1e-7 of the window mass for
-                                  pieces up to 0.4 sigma) */
+                                  2: the Taylor series of the integral about the piece's midpoint through
+                                  the h^6 term (Hermite polynomials; error below 1e-7 of the window mass
+                                  for pieces up to 0.4 sigma; the default) */
 } recon_launch;
 
 typedef struct {

@@ -104,7 +104,8 @@ typedef struct {
                                   degree-10 P (relative error ~6e-7 at K = 3), 1: CUDA's erfcf; or
                                   2: the Taylor series of the integral about the piece's midpoint through
                                   the h^6 term (Hermite polynomials; error below 1e-7 of the window mass
-                                  for pieces up to 0.4 sigma; the default) */
+                                  for pieces up to 0.4 sigma).  Without a fixed launch the library uses
+                                  2 only when the voxel diagonal is at most 0.5 sigma, else 0 */
 } recon_launch;
 
 typedef struct {

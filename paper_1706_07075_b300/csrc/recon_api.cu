@@ -361,7 +361,18 @@ recon_status finish_sensitivity(recon_ctx* ctx)
     return RECON_OK;
 }
 
-LaunchCfg default_cfg() { return LaunchCfg{192, 0, 0, 0, TAIL_SERIES}; }
+// The midpoint series for the piece masses holds its error bound (below 1e-7 of the
+// window mass) for pieces up to ~0.4 sigma; a piece is at most a voxel diagonal long.
+bool series_ok(const recon_ctx* c)
+{
+    const double diag = std::sqrt(c->grid.vx * c->grid.vx + c->grid.vy * c->grid.vy + c->grid.vz * c->grid.vz);
+    return c->sigma_mm > 0 && diag <= 0.5 * c->sigma_mm;
+}
+
+LaunchCfg default_cfg(const recon_ctx* c)
+{
+    return series_ok(c) ? LaunchCfg{192, 0, 0, 0, TAIL_SERIES} : LaunchCfg{128, 0, 0, 0, TAIL_FIT};
+}
 
 bool valid_cfg(const recon_launch* c)
 {
@@ -434,7 +445,7 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    *best = default_cfg();
+    *best = default_cfg(ctx);
     CK(ensure(ctx->pass_partial, sizeof(double) * kNeffSlots * tbl.n));
     a.partial = ctx->pass_partial.as<double>();
     // block_mul == 1 marks a cell-ordered event list: each candidate spreads its own grid
@@ -442,6 +453,7 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
     for (const LaunchCfg& c : cands) {
         // the persistent work queue takes events in list order, which a spread list must not
         if (spread && c.blocks_per_sm > 0) continue;
+        if (c.tail == TAIL_SERIES && !series_ok(ctx)) continue;
         float ms_min = 1e30f;
         PassArgs ac = a;
         if (spread) ac.block_mul = spread_multiplier(pass_blocks(c, a.n, ctx->num_sms));
@@ -683,23 +695,23 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool 
 LaunchCfg tuned_or_default(recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl)
 {
     if (ctx->user_cfg) return ctx->cfg;
-    if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg();
+    if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg(ctx);
     auto it = ctx->tuned.find(std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n + (a.block_mul == 1 ? (1 << 20) : 0)));
-    return it != ctx->tuned.end() ? it->second : default_cfg();
+    return it != ctx->tuned.end() ? it->second : default_cfg(ctx);
 }
 
 LaunchCfg choose_cfg(recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl, recon_status* st)
 {
     *st = RECON_OK;
     if (ctx->user_cfg) return ctx->cfg;
-    if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg();
+    if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg(ctx);
     // spread (cell- or region-ordered) lists are tuned apart from lists in load order
     auto key = std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n + (a.block_mul == 1 ? (1 << 20) : 0));
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
     LaunchCfg best;
     *st = autotune(ctx, a, tbl, &best);
-    if (*st != RECON_OK) return default_cfg();
+    if (*st != RECON_OK) return default_cfg(ctx);
     ctx->tuned[key] = best;
     return best;
 }
@@ -1205,7 +1217,7 @@ recon_status recon_forward(recon_ctx* ctx, const recon_events* events, const flo
         ctx->stats.kernel_launches += 1;
     }
     a.p_out = ctx->vec.as<float>();
-    LaunchCfg cfg = ctx->user_cfg ? ctx->cfg : default_cfg();
+    LaunchCfg cfg = ctx->user_cfg ? ctx->cfg : default_cfg(ctx);
     CK(ensure(ctx->work, 64));
     a.work = ctx->work.as<unsigned long long>();
     CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
@@ -1235,7 +1247,7 @@ recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const
         PassArgs a = base_args(ctx, ctx->ev.p, ctx->n_ev);
         a.C = ctx->C.as<float>();
         a.r_in = ctx->vec.as<float>();
-        LaunchCfg cfg = ctx->user_cfg ? ctx->cfg : default_cfg();
+        LaunchCfg cfg = ctx->user_cfg ? ctx->cfg : default_cfg(ctx);
         a.work = ctx->work.as<unsigned long long>();
         CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
         const RegionTable tbl = single_table(ctx);
@@ -1549,7 +1561,7 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
         b.C = ctx->C.as<float>();
         b.r_in = ctx->vec.as<float>();
         const RegionTable bt = single_table(ctx);
-        const LaunchCfg bc = ctx->user_cfg ? ctx->cfg : default_cfg();
+        const LaunchCfg bc = ctx->user_cfg ? ctx->cfg : default_cfg(ctx);
         CK(launch_pass(PASS_BACK, (EventFmt)ctx->fmt, bc, b, bt, ctx->num_sms, ctx->stream));
         const int bpr = update_blocks(nv);
         CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)bpr));

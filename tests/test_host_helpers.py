@@ -51,3 +51,44 @@ def test_bench_arms_share_the_workload_config():
     b = bench.workload_config(args, args.events, 1)
     assert a == b and a["events"] == 146_000_000 and a["parallelism"] == "single"
     assert bench.workload_config(args, args.events, 4)["parallelism"] == "replicas4"
+
+
+def test_fullsize_sampled_voxel_references_match_brute_force():
+    """The full-size GPU test recomputes sampled voxels from prefiltered events.
+    On 200 k full-body events the prefilter must miss no contributing event:
+    lam1 at the sampled voxels from the candidates equals lam1 from all events
+    (exact and sampled projectors), the window count brackets the oracle's
+    p_i > 0 count, and the per-voxel region reference equals the oracle's
+    whole region reconstruction at those voxels."""
+    import oracle
+    import test_gpu_fullsize as F
+    g = F.workload_grid("fullbody")
+    ev = synth.events("fullbody", 200_000, 77)
+    rng = np.random.default_rng(5)
+    lam0 = (rng.integers(64, 193, g.n_vox) / 128.0).astype(np.float32)
+    s = F.smooth_s(g)
+    c = F.tof_points(ev)
+    vox = F.sample_voxels(g, ev, c, rng)
+    cand = F.prefilter(g, ev, c, vox)
+    assert vox.size >= 60
+    every = [np.arange(ev.shape[1])]
+    for lut in (None, 32):
+        a = F.oracle_lam1(g, F.events64_of(ev), cand, vox, lam0, s, lut=lut)
+        b = F.oracle_lam1(g, F.events64_of(ev), every, vox, lam0, s, lut=lut)
+        assert np.count_nonzero(b) >= 0.9 * vox.size
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=0.0)
+    p = oracle.forward(g, ev.astype(np.float64), lam0.astype(np.float64), F.SIGMA)
+    sure, maybe = F.window_meets_grid(g, ev)
+    assert sure <= np.count_nonzero(p > 0) <= sure + maybe
+
+    zb = oracle.region_bounds(g, F.FULLBODY_REGIONS)
+    codes = oracle.region_codes(ev, zb, F.SHELL_MM)
+    offs, idx = oracle.region_members(codes, len(F.FULLBODY_REGIONS))
+    margin = F.K * F.SIGMA + F.SHELL_MM
+    slabs = oracle.region_slabs(g, F.FULLBODY_REGIONS, margin)
+    pos, ref = F.oracle_region_lam1(g, ev, s, vox, cand, codes, offs, idx, slabs)
+    _, images, _, _, _, _ = oracle.mlem_regions(g, ev.astype(np.float64), s, F.FULLBODY_REGIONS, F.SHELL_MM,
+                                                margin, 1, F.SIGMA)
+    whole = np.concatenate(images)
+    assert np.count_nonzero(whole[pos]) >= 0.5 * pos.size      # slab-edge voxels see few windows
+    np.testing.assert_allclose(ref, whole[pos], rtol=1e-12, atol=1e-300)

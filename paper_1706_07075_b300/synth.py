@@ -33,7 +33,7 @@ processes.
 import math
 import multiprocessing as mp
 import os
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 from multiprocessing import shared_memory
 
 import numpy as np
@@ -116,14 +116,23 @@ def fullbody_workload():
     ]
     # ten lesions, 10-20 mm diameter, 4-8x: neck, subclavicular, axillary,
     # lung, liver, abdomen, inguinal, thigh, knee, calf
-    lesions = [((20, 10, 520), 5.0, 6.0), ((-60, -60, 420), 6.0, 5.0), ((-140, 0, 380), 7.0, 4.0),
+    # (every lesion lies inside the body outline, away from the organ edges)
+    lesions = [((20, 10, 520), 5.0, 6.0), ((-60, -40, 400), 6.0, 5.0), ((-150, 0, 250), 7.0, 4.0),
                ((95, 10, 290), 8.0, 6.0), ((-60, 20, 120), 10.0, 4.0), ((40, -40, 20), 9.0, 5.0),
-               ((60, -60, -200), 5.0, 8.0), ((90, 0, -400), 6.0, 7.0), ((-90, -20, -640), 7.5, 6.0),
+               ((60, -30, -120), 5.0, 8.0), ((90, 0, -400), 6.0, 7.0), ((-90, -20, -640), 7.5, 6.0),
                ((90, 10, -850), 5.5, 8.0)]
     for c, r, act in lesions:
         shapes.append(e(c, (r, r, r), act))
     return Workload("fullbody", Scanner(400.0, 2400.0, 45.0), tuple(shapes), (150, 150, 600, 4.0),
                     scatter_fraction=0.33, extra={"lesions": lesions})
+
+
+def fullbody_background_workload():
+    """The full-body phantom without its lesions: the background data set of the
+    contrast recovery coefficient, reconstructed independently of the data with
+    lesions (Sec. 2.6)."""
+    w = fullbody_workload()
+    return replace(w, name="fullbody_background", shapes=w.shapes[:-len(w.extra["lesions"])])
 
 
 def smallfov_workload():
@@ -135,7 +144,8 @@ def smallfov_workload():
     return Workload("smallfov", Scanner(60.0, 100.0), shapes, (128, 128, 128, 0.5))
 
 
-WORKLOADS = {"tiny": tiny_workload, "fullbody": fullbody_workload, "smallfov": smallfov_workload}
+WORKLOADS = {"tiny": tiny_workload, "fullbody": fullbody_workload, "fullbody_background": fullbody_background_workload,
+             "smallfov": smallfov_workload}
 
 
 def grid_of(w):
@@ -453,11 +463,20 @@ def phantom_image(wname, grid=None, oversample=2):
                 zz, yy, xx = np.meshgrid(oz + (np.arange(nz) + a) * v, oy + (np.arange(ny) + b) * v,
                                          ox + (np.arange(nx) + c) * v, indexing="ij")
                 p = np.stack([xx.ravel(), yy.ravel(), zz.ravel()])
-                act = np.zeros(p.shape[1])
-                for s in w.shapes:
-                    act[s.contains(p)] = s.activity
-                img += act.reshape(nz, ny, nx)
+                img += activity_at(w, p).reshape(nz, ny, nx)
     return img / oversample ** 3
+
+
+def activity_at(w, points):
+    """Activity of a workload's phantom at points (3, n) in mm (painter order: a
+    later shape overrides an earlier one where they overlap)."""
+    if isinstance(w, str):
+        w = WORKLOADS[w]()
+    p = np.asarray(points, np.float64).reshape(3, -1)
+    act = np.zeros(p.shape[1])
+    for sh in w.shapes:
+        act[sh.contains(p)] = sh.activity
+    return act
 
 
 def mu_image(wname, grid=None):

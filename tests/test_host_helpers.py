@@ -92,3 +92,29 @@ def test_fullsize_sampled_voxel_references_match_brute_force():
     whole = np.concatenate(images)
     assert np.count_nonzero(whole[pos]) >= 0.5 * pos.size      # slab-edge voxels see few windows
     np.testing.assert_allclose(ref, whole[pos], rtol=1e-12, atol=1e-300)
+
+
+def test_fullbody_lesions_sit_inside_the_body_on_a_uniform_background():
+    # Eq. 1 needs a background VOI for each lesion: the lesion-free phantom must
+    # be uniform over the lesion sphere and every lesion inside the body outline
+    w = synth.WORKLOADS["fullbody"]()
+    bkg = synth.WORKLOADS["fullbody_background"]()
+    assert len(bkg.shapes) == len(w.shapes) - len(w.extra["lesions"])
+    rng = np.random.default_rng(3)
+    ratios = []
+    for c, r, act in w.extra["lesions"]:
+        d = rng.normal(size=(3, 4000))
+        d /= np.linalg.norm(d, axis=0)
+        pts = np.asarray(c, np.float64)[:, None] + d * r * rng.uniform(0.0, 1.0, 4000) ** (1.0 / 3.0)
+        b = synth.activity_at(bkg, pts)
+        assert np.unique(b).size == 1 and b[0] > 0
+        assert np.all(synth.activity_at(w, pts) == act)
+        body = np.zeros(pts.shape[1], bool)
+        for s in bkg.shapes:
+            if s.body:
+                body |= s.contains(pts)
+        assert body.all()
+        ratios.append(act / b[0])
+    assert ratios[3] == pytest.approx(6.0 / 0.3)      # the lung lesion
+    assert ratios[4] == pytest.approx(4.0 / 2.0)      # the liver lesion
+    assert min(ratios) > 1.0

@@ -377,6 +377,8 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
  * Each event's TOF-estimated z, z_tof = (z1+z2)*0.5 + (d*dz)/D with
  * D = sqrt((dx*dx + dy*dy) + dz*dz) in FP64 rounded per operation, decides the
  * regions: r takes the event iff z_b[r] - shell <= z_tof < z_b[r+1] + shell.
+ * events: NULL = the resident events (in the order they were loaded), else loaded
+ * first (and kept resident).
  * Outputs (host or device, each nullable):
  *   code_out:    n bytes; 0xFF no region, r one region, r|0x80 regions r and r+1;
  *   offsets_out: n_regions+1 int64, start of each region's list in idx_out;
@@ -387,10 +389,12 @@ recon_status recon_split_regions(recon_ctx* ctx, const recon_events* events, int
                                  const recon_region* regions, double margin_mm, double shell_mm,
                                  uint8_t* code_out, int64_t* offsets_out, int32_t* idx_out);
 
-/* Region-divided reconstruction (Sec. 2.5): split as recon_split_regions, give each
- * event fed to two regions the weight w_i/2, reconstruct every region on its slab of
- * slices [z_lo - m, z_hi + m) clipped to the grid, m = ceil(margin_mm / vz), with the
- * global sensitivity restricted to the slab, then sum the slabs into image_out
+/* Region-divided reconstruction (Sec. 2.5): split as recon_split_regions (events:
+ * NULL = the resident events), give each event fed to two regions the weight w_i/2,
+ * reconstruct every region on its slab of slices [z_lo - m, z_hi + m) clipped to the
+ * grid, m = ceil(margin_mm / vz), with the global sensitivity restricted to the slab,
+ * and the start image uniform on each slab's {s_j > 0} with sum s lambda = the sum of
+ * its events' weights; then sum the slabs into image_out
  * (nx*ny*nz floats, nullable).  All regions run in one event-pass launch per
  * iteration.  region_images_out: NULL or the concatenated slab images (region order,
  * each nx*ny*slab_nz floats; total from recon_region_slab_voxels).

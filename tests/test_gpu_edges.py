@@ -152,7 +152,7 @@ def test_call_order_and_argument_errors():
             ctx.mlem(B.make_events(ev), 1)
         assert e.value.status == B.RECON_ESTATE
         with pytest.raises(B.ReconError) as e:
-            ctx.forward(None, None, np.zeros(1, np.float32)) if False else ctx.mlem(None, -1)
+            ctx.mlem(None, -1)
         assert e.value.status == B.RECON_EINVAL
         with pytest.raises(B.ReconError):
             ctx.set_launch(100, 0, 0)
@@ -172,6 +172,17 @@ def test_call_order_and_argument_errors():
         pk = B.make_events(rec, packed=True, lattice_mm=0.0)
         with pytest.raises(B.ReconError):
             ctx.load_events(pk)
+        # the failed calls left the context usable: a valid reconstruction runs and
+        # matches a fresh context's
+        lors = synth.sensitivity_lors("tiny", 20_000, 3)
+        ctx.sensitivity(lors)
+        img = np.zeros(g.n_vox, np.float32)
+        ctx.mlem(B.make_events(ev), 2, None, img)
+        with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as fresh:
+            fresh.sensitivity(lors)
+            ref = np.zeros(g.n_vox, np.float32)
+            fresh.mlem(B.make_events(ev), 2, None, ref)
+        assert img.max() > 0 and rel_l2(img, ref) < 1e-6
     with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx2:
         with pytest.raises(B.ReconError) as e:
             ctx2.forward(None, None, np.zeros(4, np.float32))

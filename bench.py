@@ -167,7 +167,7 @@ def measure_probes(n_vox, stream, dev):
     from paper_1706_07075_b300 import build as lib_build
     lib = C.CDLL(lib_build.build_probe())
     for name in ("recon_probe_l2_red", "recon_probe_gather", "recon_probe_erfc", "recon_probe_mixed",
-                 "recon_probe_l2_stream"):
+                 "recon_probe_l2_stream", "recon_probe_red_groups"):
         getattr(lib, name).restype = C.c_int
     img = torch.zeros(n_vox, dtype=torch.float32, device=dev)
     sink = torch.zeros(148 * 64 * 256, dtype=torch.float32, device=dev)
@@ -178,6 +178,12 @@ def measure_probes(n_vox, stream, dev):
         out["l2_red_gops"] = v.value / 1e9
     if lib.recon_probe_l2_red(C.c_void_p(img.data_ptr()), C.c_int64(n_vox), 4, h, C.byref(v)) == 0:
         out["l2_red_runs4_gops"] = v.value / 1e9
+    # element reductions per second when `group` lanes of a warp share one 32-byte sector
+    groups = {}
+    for group in (1, 2, 4, 8, 32):
+        if lib.recon_probe_red_groups(C.c_void_p(img.data_ptr()), C.c_int64(n_vox), group, 1, h, C.byref(v)) == 0:
+            groups[str(group)] = v.value / 1e9
+    out["red_lanes_per_sector_gops"] = groups
     if lib.recon_probe_gather(C.c_void_p(img.data_ptr()), C.c_int64(n_vox), C.c_void_p(sink.data_ptr()), h,
                               C.byref(v)) == 0:
         out["gather_gops"] = v.value / 1e9

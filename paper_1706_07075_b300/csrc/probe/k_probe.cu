@@ -1,8 +1,8 @@
 // Hardware probes that measure the roofline denominators of the MLEM event
 // pass on the running GPU (not part of the reconstruction): the rate of
-// scattered FP32 reductions into an L2-resident image, the rate of scattered
-// 4-byte gathers from it, and the FP32 issue rate of the pieces' Gaussian
-// tail evaluation.  Each probe times itself with CUDA events on `stream`
+// scattered FP32 reductions into an L2-resident image (also with lanes that
+// share sectors), the rate of scattered 4-byte gathers from it, and the FP32
+// issue rate of the pieces' Gaussian tail evaluation.  Each probe times itself with CUDA events on `stream`
 // and returns operations per second.
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -45,6 +45,21 @@ __global__ void k_gather(const float* img, uint32_t n_words, int per_thread, flo
         acc += __ldg(img + h % n_words);
     }
     if (acc == 1234.5f) sink[t] = acc;
+}
+
+// Reductions whose lanes share 32-byte sectors: the lanes of a warp form groups
+// of `group` lanes; each group and step picks one hashed 128-byte line of img
+// and lane k of the group adds to word (k * stride) mod 32 of it.  group 1 is
+// the scattered case; group 8 with stride 1 puts eight lanes in one sector.
+__global__ void k_red_groups(float* img, uint32_t n_lines, int per_thread, int group, int stride)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31u, warp = t >> 5;
+    const uint32_t gid = lane / (uint32_t)group, sub = lane % (uint32_t)group;
+    for (int k = 0; k < per_thread; ++k) {
+        const uint32_t h = hash32(warp * 7919u + gid * 104729u + (uint32_t)k * 0x9e3779b9u);
+        atomicAdd(img + (h % n_lines) * 32u + (sub * (uint32_t)stride) % 32u, 1e-7f);
+    }
 }
 
 // One scattered gather from `lam` and one scattered reduction into `C` (two
@@ -116,6 +131,19 @@ extern "C" int recon_probe_l2_red(float* img, int64_t n_words, int32_t runs, voi
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int threads = 256, blocks = 148 * 64, per_thread = 256;
     return time_it(s, [&] { k_red<<<blocks, threads, 0, s>>>(img, (uint32_t)n_words, per_thread, runs); },
+                   (double)blocks * threads * per_thread, ops_per_s);
+}
+
+extern "C" int recon_probe_red_groups(float* img, int64_t n_words, int32_t group, int32_t stride, void* stream,
+                                      double* ops_per_s)
+{
+    if (!img || n_words < 32 || n_words >= (1LL << 32) || group < 1 || group > 32 || (32 % group) || stride < 1 ||
+        stride > 32 || !ops_per_s)
+        return 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int threads = 256, blocks = 148 * 32, per_thread = 256;
+    const uint32_t n_lines = (uint32_t)(n_words / 32);
+    return time_it(s, [&] { k_red_groups<<<blocks, threads, 0, s>>>(img, n_lines, per_thread, group, stride); },
                    (double)blocks * threads * per_thread, ops_per_s);
 }
 

@@ -22,6 +22,13 @@ extern "C" {
  * 148*64*256*256 reductions per run; img is modified. */
 int recon_probe_l2_red(float* img, int64_t n_words, int32_t runs, void* stream, double* ops_per_s);
 
+/* FP32 reductions whose lanes share sectors: lanes in groups of `group` (1..32, a
+ * divisor of 32); per group and step one hashed 128-byte line of img[0..n_words)
+ * (n_words >= 32), lane k of the group adding to word (k*stride) mod 32 of it.
+ * *ops_per_s counts element reductions (148*32*256*256 per run); img is modified. */
+int recon_probe_red_groups(float* img, int64_t n_words, int32_t group, int32_t stride, void* stream,
+                           double* ops_per_s);
+
 /* Scattered 4-byte read-only gathers from img[0..n_words); sink: 148*64*256 floats. */
 int recon_probe_gather(const float* img, int64_t n_words, float* sink, void* stream, double* ops_per_s);
 

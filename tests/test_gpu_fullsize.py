@@ -329,6 +329,52 @@ def test_fullsize_packed_bf16_gather(full):
     assert cons[0, 1] == pytest.approx(cons[0, 0], rel=1e-5)
 
 
+def test_fullsize_osem_subset_counts(full, ctx):
+    # OSEM with 5 subsets (consecutive blocks of the list) at full size.  The first
+    # sub-iteration starts from lam0 > 0, so its N_eff equals the FP64 count of its
+    # block's TOF windows that meet the grid.  A voxel that one block does not reach
+    # gets lambda = 0 and keeps it (multiplicative update), so later blocks lose the
+    # events whose every voxel some earlier block missed: a few 1e-5 of a block per
+    # sub-iteration on this workload (measured 0.7, 3.0, 6.0, 9.4e-5 for blocks 1-4),
+    # bounded here by 1e-3.  sum s lambda = B N_eff after each sub-iteration.
+    g, lam0, ev = full["g"], full["lam0"], full["ev"]
+    B_SUB = 5
+    n = ev.shape[1]
+    img = np.zeros(g.n_vox, np.float32)
+    cons = np.zeros((B_SUB, 2))
+    ctx.set_subsets(B_SUB)
+    try:
+        ctx.mlem(None, 1, lam0, img, cons)
+    finally:
+        ctx.set_subsets(1)
+    assert np.isfinite(img).all() and img.min() >= 0.0
+    for b in range(B_SUB):
+        lo, hi = b * n // B_SUB, (b + 1) * n // B_SUB
+        sure, maybe = window_meets_grid(g, ev[:, lo:hi])
+        print(f"\nsubset {b}: N_eff {cons[b, 0]:.0f}, FP64 windows meeting the grid {sure} (+{maybe})")
+        if b == 0:
+            assert sure <= cons[b, 0] <= sure + maybe
+        else:
+            assert sure - 1e-3 * (hi - lo) <= cons[b, 0] <= sure + maybe
+        assert cons[b, 1] == pytest.approx(B_SUB * cons[b, 0], rel=1e-5)
+
+
+def test_fullsize_preprocess_sampled_events(full, ctx):
+    # attenuation weights and TOF scatter rejection over all 146 M resident events;
+    # the oracle recomputes every 1009th event
+    from test_gpu_preprocess import Z95, check_against_oracle
+    g, ev = full["g"], full["ev"]
+    mu = synth.mu_image("fullbody")
+    n = ev.shape[1]
+    w = np.zeros(n, np.float32)
+    keep = np.zeros(n, np.uint8)
+    kept = ctx.preprocess(None, mu, Z95, 0, w, keep)
+    assert kept == int(keep.sum())
+    print(f"\npre-processing, 146 M events: {kept / n:.4f} kept")
+    pick = np.arange(0, n, 1009)
+    check_against_oracle(g, np.ascontiguousarray(ev[:, pick]), mu, w[pick], keep[pick], int(keep[pick].sum()))
+
+
 @pytest.fixture(scope="module")
 def regions_ref(full):
     """Oracle region codes over all events (FP64, chunked), members and offsets."""

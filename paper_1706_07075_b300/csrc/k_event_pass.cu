@@ -37,6 +37,23 @@ __device__ __forceinline__ int find_region(const SharedTable& t, long long i)
     return r;
 }
 
+// Adds a warp's N_eff weights to the block's per-region sums: one shared-memory
+// atomic per warp when its weighted lanes share a region (always for an undivided
+// pass), else one per lane.  All 32 lanes of the warp must call it (w = 0 for a
+// lane without an event).
+__device__ __forceinline__ void add_neff(float* neff, int r, float w)
+{
+    const int r0 = __shfl_sync(0xffffffffu, r, 0);
+    if (__all_sync(0xffffffffu, r == r0 || w == 0.f)) {
+        float s = w;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0 && s != 0.f) atomicAdd(&neff[r0], s);
+    } else if (w != 0.f) {
+        atomicAdd(&neff[r], w);
+    }
+}
+
 template <int Fmt>
 __device__ __forceinline__ Event load_event(const PassArgs& a, long long i)
 {
@@ -151,11 +168,10 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
         const unsigned long long b =
             a.block_mul > 1 ? (unsigned long long)blockIdx.x * a.block_mul % gridDim.x : blockIdx.x;
         const long long i = (long long)b * blockDim.x + threadIdx.x;
-        if (i < a.n) {
-            int r;
-            float w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, tail, r);
-            if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
-        }
+        int r = 0;
+        float w = 0.f;
+        if (i < a.n) w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, tail, r);
+        if (Kind == PASS_FUSED) add_neff(neff, r, w);
     }
     if (Kind == PASS_FUSED) {
         // fold the block's N_eff into one of kNeffSlots slots per region; the
@@ -308,11 +324,10 @@ __global__ void __launch_bounds__(256) k_lut_pass(PassArgs a, RegionTable tbl)
     const unsigned long long b =
         a.block_mul > 1 ? (unsigned long long)blockIdx.x * a.block_mul % gridDim.x : blockIdx.x;
     const long long i = (long long)b * blockDim.x + threadIdx.x;
-    if (i < a.n) {
-        int r;
-        const float w = do_event_lut<Kind, Fmt, NS>(a, t, i, a.lam_bf16 != nullptr, r);
-        if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
-    }
+    int r = 0;
+    float w = 0.f;
+    if (i < a.n) w = do_event_lut<Kind, Fmt, NS>(a, t, i, a.lam_bf16 != nullptr, r);
+    if (Kind == PASS_FUSED) add_neff(neff, r, w);
     if (Kind == PASS_FUSED) {
         __syncthreads();
         for (int k = threadIdx.x; k < t.n; k += blockDim.x)

@@ -27,7 +27,7 @@ sys.path.insert(0, ROOT)
 METRIC = "TOF-MLEM events x iterations / s (full-body, 146M events, 150x150x600 @ 4 mm)"
 # DRAM bytes per event of the fused pass (ncu, 8 M full-body events, cell + direction order, 128 threads,
 # series masses): see profiles/k_event_pass_fullbody_8M.md
-TRAFFIC_BYTES_PER_EVENT = 49.2
+TRAFFIC_BYTES_PER_EVENT = 49.3
 # algorithmic FP32 operations per Siddon piece: ~25 for the step and the two
 # accumulations plus ~20 for the Gaussian mass of the piece
 ALU_OPS_PER_PIECE = 45.0

@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, c
     tail.inv_sigma_sqrt2 = a.tof.inv_sigma_sqrt2;
     const float hw = a.tof.half_window, hin = a.tof.half_inv_norm;
     const long long e0 = begin[cell], e1 = begin[cell + 1];
+    float my_neff = 0.f;   // this thread's share of the block's N_eff
 
     if (Lanes == 1) {
         // one thread per event: forward sweep gathering from the lambda tile, backward
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, c
             if (!(p > 0.f)) continue;
             const float r = e.w / p * hin;
             walk<true>(tg, a.tof, tail, w, [&](int j, float m) { atomicAdd(C_s + j, m * r); });
-            atomicAdd(&neff_s, e.w);
+            my_neff += e.w;
         }
     }
     const int lane8 = threadIdx.x & (kLanesPerEvent - 1);
@@ -439,9 +440,13 @@ __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, c
                     if (q >= kLanePieces) atomicAdd(C_s + j, m * r);
                 }
             }
-            if (lane8 == 0) atomicAdd(&neff_s, e.w);
+            if (lane8 == 0) my_neff += e.w;
         }
     }
+    // one shared atomic per warp for N_eff (every thread of the block gets here)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_neff += __shfl_xor_sync(0xffffffffu, my_neff, o);
+    if (lane == 0 && my_neff != 0.f) atomicAdd(&neff_s, my_neff);
     __syncthreads();
     // C tile into the image: rows again, consecutive lanes on consecutive voxels
     for (int row = warp; row < Ty * Tz; row += kWarps) {

@@ -481,17 +481,29 @@ def run_serve(args):
     mean_service = (0.6 * np.mean([service[k] for k in region_kinds]) + 0.1 * service["fullbody"] +
                     0.3 * service["smallfov"])
     rate = 0.8 / mean_service
-    rng = np.random.default_rng(args.seed)
     arrivals = poisson_arrivals(args.serve_jobs, rate, args.seed)
-    jobs = []
-    for i, t in enumerate(arrivals):
-        u = rng.uniform()
-        kind = "region" if u < 0.6 else ("fullbody" if u < 0.7 else "smallfov")
-        if kind == "region":
-            kind = region_kinds[int(rng.integers(0, len(region_kinds)))]
-        geo, grid, evs = kinds[kind]
-        ev = evs[int(rng.integers(0, len(evs)))]
-        jobs.append(Job(i, float(t), ev, geo, grid, args.iters, sens_key=kind, kind=kind))
+
+    def make_jobs():
+        # the same stream every call: arrival times, kinds and event sets from the seed
+        rng = np.random.default_rng(args.seed)
+        out = []
+        for i, t in enumerate(arrivals):
+            u = rng.uniform()
+            kind = "region" if u < 0.6 else ("fullbody" if u < 0.7 else "smallfov")
+            if kind == "region":
+                kind = region_kinds[int(rng.integers(0, len(region_kinds)))]
+            geo, grid, evs = kinds[kind]
+            ev = evs[int(rng.integers(0, len(evs)))]
+            out.append(Job(i, float(t), ev, geo, grid, args.iters, sens_key=kind, kind=kind))
+        return out
+
+    def latencies_by_kind(done):
+        out = {}
+        for j in done:
+            out.setdefault("region" if j.kind.startswith("region") else j.kind, []).append(j.latency)
+        return out
+
+    jobs = make_jobs()
     ex.keep_results = False
     ex.warm(jobs)
     srv = Server(ex, slots=3, hbm_budget_bytes=200 << 30)
@@ -499,11 +511,12 @@ def run_serve(args):
     sampler.start()
     stats = srv.replay(jobs)
     clocks = sampler.stop()
+    by_kind = latencies_by_kind(srv.done)
+    # the same stream served one job at a time in arrival order (the plain form)
+    srv1 = Server(ex, slots=1, hbm_budget_bytes=200 << 30)
+    stats1 = srv1.replay(make_jobs())
+    by_kind1 = latencies_by_kind(srv1.done)
     ex.close()
-    by_kind = {}
-    for j in srv.done:
-        key = "region" if j.kind.startswith("region") else j.kind
-        by_kind.setdefault(key, []).append(j.latency)
     line = {"metric": "served TOF-MLEM reconstruction: p50/p99 job latency and aggregate events x iterations / s",
             "value": stats["p50_s"], "unit": "s", "p50_s": stats["p50_s"], "p99_s": stats["p99_s"],
             "events_iters_per_s": stats["events_iters_per_s"], "jobs": stats["jobs"],
@@ -516,6 +529,12 @@ def run_serve(args):
             "serial_service_s": service,
             "latency_p50_by_kind_s": {k: float(np.percentile(v, 50)) for k, v in by_kind.items()},
             "latency_p99_by_kind_s": {k: float(np.percentile(v, 99)) for k, v in by_kind.items()},
+            "one_job_at_a_time": {"p50_s": stats1["p50_s"], "p99_s": stats1["p99_s"],
+                                  "events_iters_per_s": stats1["events_iters_per_s"],
+                                  "latency_p50_by_kind_s": {k: float(np.percentile(v, 50)) for k, v in
+                                                            by_kind1.items()},
+                                  "latency_p99_by_kind_s": {k: float(np.percentile(v, 99)) for k, v in
+                                                            by_kind1.items()}},
             "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0

@@ -13,6 +13,8 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   system_row .......... pinned (closed-form truncated-Gaussian mass of the
                         clipped window; unit sum inside the grid)
   forward/backproject . pinned (dense matrix built by brute force; adjointness)
+  count_visits ........ pinned (brute-force count of the positive-length
+                        pieces inside the TOF windows; axis-parallel closed form)
   sensitivity ......... pinned (chord sums; brute force)
   mlem ................ pinned (dense textbook MLEM on an 8x8x8 grid; the
                         one-voxel closed form; conservation; monotone

@@ -151,6 +151,26 @@ def test_trace_matches_bruteforce(seed):
         assert np.all(np.diff(ta) >= 0) and np.all(tb >= ta)
 
 
+def test_count_visits_matches_bruteforce_pieces():
+    # the work unit of the measurement: the number of positive-length voxel pieces
+    # inside the TOF windows, counted by brute force over every voxel box
+    rng = np.random.default_rng(77)
+    g = ODD_GRID
+    sigma, K = 3.0, 3.0
+    p1, p2 = random_lines(rng, 120, 12.0)
+    d = rng.uniform(-6.0, 6.0, 120)
+    brute = 0
+    for a, b, di in zip(p1, p2, d):
+        brute += len(brute_segments(g, a, b, di - K * sigma, di + K * sigma))
+    assert brute > 200
+    assert oracle.count_visits(g, events_from(p1, p2, d), sigma, K) == brute
+    # axis-parallel closed form: a line along x through voxel centres, window inside
+    # the grid from x = -5.5 to x = 5.5 (planes at -4, -1, 2, 5): 5 pieces
+    y, z = -4.5 + 1.25, -11.0 + 2.0
+    ev = events_from([100.0, y, z], [-100.0, y, z], [0.0])
+    assert oracle.count_visits(g, ev, 5.5 / K, K) == 5
+
+
 def test_trace_axis_parallel_index_convention():
     g = ODD_GRID
     # along z through voxel column (ix, iy) = (3, 1)

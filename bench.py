@@ -160,6 +160,46 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
+def roofline(n, visits, pass_ms, probes, hbm_peak_gbs, sm_mhz, traffic):
+    """Roofline of the fused event pass as t_min / t_measured, t_min the largest of
+    its algorithmic terms per launch: HBM (32 B per event), L2 reductions (one FP32
+    reduction per Siddon piece at the live rate of scattered red.global.add.f32), L2
+    gathers (one 4-byte gather per piece at the live gather rate), L2 sectors (every
+    gather and every reduction touches one 32-byte sector, at the live L2 read
+    bandwidth) and FP32 ALU (ALU_OPS_PER_PIECE per piece on 148 SMs x 128 lanes at
+    the sampled SM clock).  `achieved` and `peak` are in the unit of the largest
+    term; `traffic` is the ncu DRAM bytes of the launch (or None)."""
+    R, G, L2BW = probes.get("l2_red_gops"), probes.get("gather_gops"), probes.get("l2_stream_gbs")
+    alu_peak = 148 * 128 * sm_mhz * 1e6                      # FP32 lane operations per second
+    t = pass_ms / 1e3
+    terms = {"hbm": (32.0 * n) / (hbm_peak_gbs * 1e9),
+             "l2_reductions": visits / (R * 1e9) if R else 0.0,
+             "l2_gathers": visits / (G * 1e9) if G else 0.0,
+             "l2_sectors": visits * 2 * 32.0 / (L2BW * 1e9) if L2BW else 0.0,
+             "alu": visits * ALU_OPS_PER_PIECE / alu_peak}
+    bound = max(terms, key=terms.get)
+    rates = {"hbm": (32.0 * n / t / 1e9, hbm_peak_gbs, "GB/s"),
+             "l2_reductions": (visits / t / 1e9, R, "Gred/s"),
+             "l2_gathers": (visits / t / 1e9, G, "Ggather/s"),
+             "l2_sectors": (visits * 64.0 / t / 1e9, L2BW, "GB/s"),
+             "alu": (visits * ALU_OPS_PER_PIECE / t / 1e12, alu_peak / 1e12, "Tops/s")}
+    ach, pk, unit = rates[bound]
+    hbm_gbs = 32.0 * n / t / 1e9
+    return {
+        "bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk if pk else None,
+        "traffic": traffic,
+        "traffic_source": f"ncu capture of the same kernel on 8 M full-body events, "
+                          f"{TRAFFIC_BYTES_PER_EVENT:.1f} B per event, scaled",
+        "t_min_ms": 1e3 * terms[bound], "terms_ms": {k: 1e3 * v for k, v in terms.items()},
+        "per_launch": {"events": n, "pieces": visits, "gathers": visits, "reductions": visits,
+                       "hbm_bytes": 32.0 * n, "pass_ms": pass_ms},
+        "peak_source": "live probes on an L2-resident image of the grid's size (scattered "
+                       "red.global.add.f32, 4-byte gathers, coalesced 16-byte reads for the L2 sector "
+                       "bandwidth); HBM from MEASURED_PEAKS; ALU from 148 SMs x 128 lanes x sampled SM clock",
+        "mixed_probe_gsteps": probes.get("mixed_gsteps"),
+        "secondary": {"hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak_gbs, "hbm_frac": hbm_gbs / hbm_peak_gbs}}
+
+
 def measure_probes(n_vox, stream, dev):
     """Roofline denominators measured on this GPU (librecon_probe.so)."""
     import ctypes as C
@@ -660,53 +700,14 @@ def run_ours(args):
         # The event pass issues one FP32 reduction into the L2-resident image per
         # Siddon piece (visits per launch = mean pieces per event x events) and
         # reads each 32-byte event record once from HBM.
-        red_rate = visits / (pass_ms / 1e3)
-        hbm_gbs = 32.0 * n / (pass_ms / 1e3) / 1e9
-        # Roofline as t_min / t_measured with t_min the largest of the pass's
-        # algorithmic terms per launch: HBM (32 B per event), L2 reductions (one FP32
-        # reduction per piece, at the rate of scattered red.global.add.f32 measured live),
-        # L2 gathers (one 4-byte gather per piece, live gather rate) and FP32 ALU (about
-        # 25 FP32 operations plus one Gaussian-mass evaluation, ~20, per piece, on
-        # 148 SMs x 128 FP32 lanes at the sampled SM clock).  `achieved` and `peak`
-        # are given in the unit of the largest term.
-        # DRAM bytes per event of the fused pass from its ncu capture on 8 M full-body
-        # events in the bench's event order and launch (dram__bytes_read.sum +
-        # dram__bytes_write.sum); the traffic grows with the events, so it is scaled.
         traffic = TRAFFIC_BYTES_PER_EVENT * n if not args.samples else None
-        R, G, L2BW = probes.get("l2_red_gops"), probes.get("gather_gops"), probes.get("l2_stream_gbs")
         sm_mhz = (clocks.get("sm_mhz") or 2032.0) if isinstance(clocks, dict) else 2032.0
-        alu_peak = 148 * 128 * sm_mhz * 1e6                      # FP32 lane operations per second
-        pieces_s = pass_ms / 1e3
-        terms = {"hbm": (32.0 * n) / (peaks["hbm_gbs"] * 1e9),
-                 "l2_reductions": visits / (R * 1e9) if R else 0.0,
-                 "l2_gathers": visits / (G * 1e9) if G else 0.0,
-                 # every gather and every reduction touches one 32-byte L2 sector
-                 "l2_sectors": visits * 2 * 32.0 / (L2BW * 1e9) if L2BW else 0.0,
-                 "alu": visits * ALU_OPS_PER_PIECE / alu_peak}
-        bound = max(terms, key=terms.get)
-        rates = {"hbm": (32.0 * n / pieces_s / 1e9, peaks["hbm_gbs"], "GB/s"),
-                 "l2_reductions": (visits / pieces_s / 1e9, R, "Gred/s"),
-                 "l2_gathers": (visits / pieces_s / 1e9, G, "Ggather/s"),
-                 "l2_sectors": (visits * 64.0 / pieces_s / 1e9, L2BW, "GB/s"),
-                 "alu": (visits * ALU_OPS_PER_PIECE / pieces_s / 1e12, alu_peak / 1e12, "Tops/s")}
-        ach, pk, unit = rates[bound]
-        out["roofline"] = {
-            "bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk if pk else None,
-            "traffic": traffic,
-            "traffic_source": f"ncu capture of the same kernel on 8 M full-body events, "
-                              f"{TRAFFIC_BYTES_PER_EVENT:.1f} B per event, scaled",
-            "t_min_ms": 1e3 * terms[bound], "terms_ms": {k: 1e3 * v for k, v in terms.items()},
-            "per_launch": {"events": n, "pieces": visits, "gathers": visits, "reductions": visits,
-                           "hbm_bytes": 32.0 * n, "pass_ms": pass_ms},
-            "peak_source": "live probes on an L2-resident image of the grid's size (scattered "
-                           "red.global.add.f32, 4-byte gathers, coalesced 16-byte reads for the L2 sector "
-                           "bandwidth); HBM from MEASURED_PEAKS; ALU from 148 SMs x 128 lanes x sampled SM clock",
-            "mixed_probe_gsteps": probes.get("mixed_gsteps"),
-            "secondary": {"hbm_gbs": hbm_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": hbm_gbs / peaks["hbm_gbs"],
-                          "hbm_peak_source": src}}
+        out["roofline"] = roofline(n, visits, pass_ms, probes, peaks["hbm_gbs"], sm_mhz, traffic)
+        out["roofline"]["secondary"]["hbm_peak_source"] = src
         if args.samples:
             # the roofline above counts Siddon pieces: it describes the exact projector only
-            out["roofline"] = {"bound": "l2_reductions", "achieved": None, "peak": R, "unit": "Gred/s",
+            out["roofline"] = {"bound": "l2_reductions", "achieved": None, "peak": probes.get("l2_red_gops"),
+                               "unit": "Gred/s",
                                "frac": None, "traffic": None,
                                "note": "sampled projector timed; see profiles/k_lut_pass_fullbody_8M.md"}
         if not args.no_cpu_baseline:

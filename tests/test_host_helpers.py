@@ -53,6 +53,32 @@ def test_bench_arms_share_the_workload_config():
     assert bench.workload_config(args, args.events, 4)["parallelism"] == "replicas4"
 
 
+def test_bench_roofline_terms_and_fraction():
+    # the roofline arithmetic of bench.py on the figures of a measured full-body run:
+    # 146 M events x 44.25 pieces, pass 31.2 ms, live probes as measured
+    sys.path.insert(0, ROOT)
+    import bench
+    n, visits, pass_ms = 146_000_000, 146_000_000 * 44.25, 31.22
+    probes = {"l2_red_gops": 230.8, "gather_gops": 299.1, "l2_stream_gbs": 12862.0, "mixed_gsteps": 99.9}
+    r = bench.roofline(n, visits, pass_ms, probes, 6506.9, 2032.0, 49.3 * n)
+    t = r["terms_ms"]
+    assert t["hbm"] == pytest.approx(32.0 * n / 6506.9e9 * 1e3)
+    assert t["l2_reductions"] == pytest.approx(visits / 230.8e9 * 1e3)
+    assert t["l2_sectors"] == pytest.approx(visits * 64.0 / 12862.0e9 * 1e3)
+    assert t["alu"] == pytest.approx(visits * bench.ALU_OPS_PER_PIECE / (148 * 128 * 2032e6) * 1e3)
+    # the bound is the largest term, and frac = t_min / t_measured in any unit
+    assert r["bound"] == max(t, key=t.get) == "l2_sectors"
+    assert r["frac"] == pytest.approx(t["l2_sectors"] / pass_ms)
+    assert r["achieved"] == pytest.approx(visits * 64.0 / (pass_ms / 1e3) / 1e9)
+    assert r["unit"] == "GB/s" and r["peak"] == 12862.0
+    assert r["secondary"]["hbm_frac"] == pytest.approx(32.0 * n / (pass_ms / 1e3) / 6506.9e9)
+    # with a slower reduction rate the reduction term becomes the bound
+    slow = dict(probes, l2_red_gops=150.0)
+    r2 = bench.roofline(n, visits, pass_ms, slow, 6506.9, 2032.0, None)
+    assert r2["bound"] == "l2_reductions" and r2["unit"] == "Gred/s" and r2["traffic"] is None
+    assert r2["frac"] == pytest.approx(r2["terms_ms"]["l2_reductions"] / pass_ms)
+
+
 def test_fullsize_sampled_voxel_references_match_brute_force():
     """The full-size GPU test recomputes sampled voxels from prefiltered events.
     On 200 k full-body events the prefilter must miss no contributing event:

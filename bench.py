@@ -377,7 +377,7 @@ def time_packed_leg(ctx, B, synth, ev, n, args, stream):
         t = time.perf_counter()
         ctx.mlem(B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM), args.iters, None, img, cons)
         times.append(time.perf_counter() - t)
-    e2e_T = sum(times[1:]) / max(1, len(times) - 1)
+    e2e_T = sum(times[1:]) / (len(times) - 1) if len(times) > 1 else float("nan")
     ctx.set_gather_bf16(0)
     return {"workload": "fullbody packed int16/FP16 events, BF16 gather", "value": n * args.iters * args.steps /
             (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,

@@ -84,8 +84,9 @@ def test_fullsize_sampled_voxel_references_match_brute_force():
     On 200 k full-body events the prefilter must miss no contributing event:
     lam1 at the sampled voxels from the candidates equals lam1 from all events
     (exact and sampled projectors), the window count brackets the oracle's
-    p_i > 0 count, and the per-voxel region reference equals the oracle's
-    whole region reconstruction at those voxels."""
+    p_i > 0 count, the per-voxel region reference equals the oracle's whole
+    region reconstruction at those voxels, and the median-sieve reference its
+    whole iteration with the sieve."""
     import oracle
     import test_gpu_fullsize as F
     g = F.workload_grid("fullbody")
@@ -118,6 +119,19 @@ def test_fullsize_sampled_voxel_references_match_brute_force():
     whole = np.concatenate(images)
     assert np.count_nonzero(whole[pos]) >= 0.5 * pos.size      # slab-edge voxels see few windows
     np.testing.assert_allclose(ref, whole[pos], rtol=1e-12, atol=1e-300)
+
+    # the median-sieve reference: the 3x3x3 median of lam1 from the 27 neighbours'
+    # prefiltered events equals the oracle's whole iteration with the sieve
+    plane = g.ny * g.nx
+    centres = np.array([j for j in vox if 0 < j % g.nx < g.nx - 1 and 0 < (j // g.nx) % g.ny < g.ny - 1
+                        and 0 < j // plane < g.nz - 1][:16])
+    offs27 = np.array([dz * plane + dy * g.nx + dx for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)])
+    nb = (centres[:, None] + offs27[None, :]).ravel()
+    lam1_nb = F.oracle_lam1(g, F.events64_of(ev), F.prefilter(g, ev, c, nb), nb, lam0, s).reshape(centres.size, 27)
+    med = np.array([oracle.median3_at(row.reshape(3, 3, 3), (3, 3, 3), [13])[0] for row in lam1_nb])
+    sieved, _ = oracle.mlem(g, ev.astype(np.float64), s, 1, F.SIGMA, init=lam0.astype(np.float64), median=True)
+    assert np.count_nonzero(med) == centres.size
+    np.testing.assert_allclose(med, sieved[centres], rtol=1e-12, atol=0.0)
 
 
 def test_fullbody_lesions_sit_inside_the_body_on_a_uniform_background():

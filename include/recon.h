@@ -208,7 +208,8 @@ recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float
  * call that passes host events bins them after its first, upload-overlapped pass).
  * Measured on B300, 146 M full-body events, series piece masses: 47.6 ms per pass in load
  * order, 35.5 ms with 3^3-voxel cells (about the same for edges of 1 to 10 voxels),
- * 31.5-31.9 ms with 16 x 8 or 32 x 16 direction bins as well.  Errors: EINVAL (order
+ * 31.5-31.9 ms with 16 x 8 or 32 x 16 direction bins as well (31.2 ms in the current
+ * library, which sums N_eff per warp).  Errors: EINVAL (order
  * outside [-1, 64], bins outside [1, 64]). */
 recon_status recon_set_event_order(recon_ctx* ctx, int32_t order, int32_t azimuth_bins, int32_t polar_bins);
 

@@ -284,8 +284,12 @@ recon_status recon_set_timing(recon_ctx* ctx, int32_t on);
 /* Capture each MLEM iteration in a CUDA graph and replay it (1, default) or launch
  * kernels directly (0). */
 recon_status recon_set_graphs(recon_ctx* ctx, int32_t on);
-/* Let recon_mlem search launch configurations on the resident events the first time
- * it meets a new (event count, format, grid) (1, default), or use the default (0). */
+/* Let recon_mlem / recon_mlem_regions search launch configurations of the exact
+ * projector's event pass on the resident events the first time they meet a new
+ * (event count, format, voxel count, region count, event order) with at least 2^20
+ * events (1, default), or use the default launch (0).  Each of 11 candidates (threads per
+ * block, flat or persistent grid, piece cache, piece-mass form) runs two timed passes;
+ * C is cleared afterwards, so the search changes no result. */
 recon_status recon_set_autotune(recon_ctx* ctx, int32_t on);
 
 recon_status recon_get_info(const recon_ctx* ctx, recon_info* out);

@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=1708)
-    ap.add_argument("--cpu-sample", type=int, default=300_000, help="events in the oracle's timed sample")
+    ap.add_argument("--cpu-sample", type=int, default=6_000_000, help="events in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--launch", default=None,
                     help="fix the event-pass launch: threads,blocks_per_sm,chunk,cached_pieces,tail_eval "

@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=1708)
-    ap.add_argument("--cpu-sample", type=int, default=6_000_000, help="events in the oracle's timed sample")
+    ap.add_argument("--cpu-sample", type=int, default=15_000_000, help="events in the oracle's timed sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--launch", default=None,
                     help="fix the event-pass launch: threads,blocks_per_sm,chunk,cached_pieces,tail_eval "
@@ -319,8 +319,6 @@ def run_reference(args):
     return 0
 
 
-FULLBODY_REGIONS = [(0, 67), (67, 134), (134, 200), (200, 267), (267, 334), (334, 400), (400, 467),
-                    (467, 534), (534, 600)]
 
 
 def _timed_steps(stream, k, fn):
@@ -337,11 +335,17 @@ def _timed_steps(stream, k, fn):
 
 
 def time_regions_leg(ctx, B, n, args, stream):
-    """Region-divided form (Sec. 2.5): split by TOF z into nine regions, all
-    regions' events in one event-pass launch per iteration, stitch.  Counts the
-    original events (not their duplicates) per iteration."""
+    """Region-divided form (Sec. 2.5): split by TOF z into nine body regions,
+    all regions' events in one event-pass launch per iteration, stitch.  Counts
+    the original events that join a region (not their duplicates) per iteration."""
     import numpy as np
+    from paper_1706_07075_b300.synth import FULLBODY_REGIONS
     sigma = ctx.get_info()["sigma_mm"]
+    codes = np.zeros(n, np.uint8)
+    offs = np.zeros(len(FULLBODY_REGIONS) + 1, np.int64)
+    ctx.split_regions(None, FULLBODY_REGIONS, 0.0, 6.0, codes, offs, None)
+    n_in = int(np.count_nonzero(codes != 0xFF))
+    del codes
     margin = 3.0 * sigma + 6.0
     cons = np.zeros((args.iters, 9, 2))
     ctx.mlem_regions(None, FULLBODY_REGIONS, margin, 6.0, args.iters, None, None, cons)   # warm-up (+ autotune)
@@ -349,8 +353,10 @@ def time_regions_leg(ctx, B, n, args, stream):
     ms = _timed_steps(stream, args.steps, lambda: ctx.mlem_regions(None, FULLBODY_REGIONS, margin, 6.0, args.iters,
                                                                      None, None, cons))
     st1 = ctx.get_stats()
-    return {"workload": "fullbody 9 TOF regions, shell 6 mm, margin 3 sigma + shell", "value": n * args.iters *
-            args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+    return {"workload": "fullbody 9 TOF body regions (cores of 50 slices from slice 42, the last of 68), shell 6 mm, "
+                        "margin 3 sigma + shell", "value": n_in * args.iters * args.steps / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "events_in_regions": n_in,
+            "events_per_region": [int(x) for x in np.diff(offs)],
             "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
             "launch": list(ctx.get_launch()), "n_eff_per_region_last": [float(x) for x in cons[-1, :, 0]],
             "steps": args.steps}

@@ -156,6 +156,18 @@ def grid_of(w):
     return (nx, ny, nz, v, v, v, -0.5 * nx * v, -0.5 * ny * v, -0.5 * nz * v)
 
 
+# Nine body regions of the full-body workload (Sec. 2.5), as core slice ranges
+# [z_lo, z_hi) of its 150x150x600 grid of 4 mm.  Eight cores of 50 slices
+# (200 mm, the core length of the paper's regions 2-9) run from the feet
+# (slice 42, z = -1032 mm) up the body; the ninth takes the 68 slices up to
+# z = 840 mm, above the head.  With the 6 mm shell the regions take 6.7 M to
+# 34.4 M of the 146 M events each, and slabs widened by 3 sigma + shell span
+# 82 to 100 slices; the 0.09% of events whose TOF point lies below the feet or
+# above the head join no region.
+FULLBODY_REGIONS = [(42, 92), (92, 142), (142, 192), (192, 242), (242, 292), (292, 342), (342, 392),
+                    (392, 442), (442, 510)]
+
+
 # ----------------------------------------------------------------- sampling
 
 def _rng(seed, stream, chunk):

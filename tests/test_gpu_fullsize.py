@@ -42,8 +42,7 @@ N_EVENTS = 146_000_000          # the full-body benchmark workload
 SEED = 1708                     # the benchmark's event seed (rank 0)
 K = 3.0
 MARGIN_MM = 1.0                 # prefilter margin (covers the int16/FP16 packing error)
-FULLBODY_REGIONS = [(0, 67), (67, 134), (134, 200), (200, 267), (267, 334), (334, 400), (400, 467),
-                    (467, 534), (534, 600)]
+FULLBODY_REGIONS = synth.FULLBODY_REGIONS   # the benchmark's nine body regions
 SHELL_MM = 6.0
 CHUNK = 8_000_000
 THREADS = min(16, os.cpu_count() or 1)   # numpy releases the GIL in the array work

@@ -14,8 +14,7 @@ from paper_1706_07075_b300 import synth
 
 pytestmark = pytest.mark.gpu
 
-FULLBODY_REGIONS = [(0, 67), (67, 134), (134, 200), (200, 267), (267, 334), (334, 400), (400, 467),
-                    (467, 534), (534, 600)]
+FULLBODY_REGIONS = synth.FULLBODY_REGIONS   # the benchmark's nine body regions
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "region_boundary_events.json")
 
 

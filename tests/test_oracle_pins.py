@@ -402,8 +402,7 @@ def test_region_codes_golden_boundaries():
     assert list(codes) == [e["code"] for e in evs]
 
 
-FULLBODY_REGIONS = [(0, 67), (67, 134), (134, 200), (200, 267), (267, 334), (334, 400), (400, 467),
-                    (467, 534), (534, 600)]
+FULLBODY_REGIONS = synth.FULLBODY_REGIONS   # nine body regions; some events fall outside them
 
 
 def test_region_codes_one_or_two_consecutive_regions():
@@ -425,8 +424,9 @@ def test_region_codes_one_or_two_consecutive_regions():
         assert np.array_equal(mem, ref)
         counts += mem
     assert counts.max() <= 2 and np.all(counts[inside] >= 1)
+    assert 0 < np.count_nonzero(~inside) < 0.01 * ev.shape[1]   # below the feet or above the head
     # duplicates only within a shell of a core boundary
-    dup = (codes & 0x80) != 0
+    dup = (codes != 0xFF) & ((codes & 0x80) != 0)   # 0xFF (no region) also has the top bit
     near = np.min(np.abs(z[:, None] - zb[None, 1:-1]), axis=1) <= 6.0
     assert np.all(near[dup])
 

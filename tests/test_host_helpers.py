@@ -158,3 +158,27 @@ def test_fullbody_lesions_sit_inside_the_body_on_a_uniform_background():
     assert ratios[3] == pytest.approx(6.0 / 0.3)      # the lung lesion
     assert ratios[4] == pytest.approx(4.0 / 2.0)      # the liver lesion
     assert min(ratios) > 1.0
+
+
+def test_fullbody_regions_cover_the_body_in_nine_uneven_regions():
+    """The nine body regions of the full-body workload (Sec. 2.5): consecutive
+    cores, eight of 200 mm; slabs widened by 3 sigma + 6 mm shell of 60 to 110
+    slices; on a seeded sample every region takes between 4 M and 35 M of 146 M
+    events, and fewer than 0.5% of the events join no region."""
+    import oracle
+    regions = synth.FULLBODY_REGIONS
+    g = oracle.Grid(*synth.grid_of("fullbody"))
+    assert len(regions) == 9
+    assert all(regions[r][1] == regions[r + 1][0] for r in range(8))
+    assert 0 <= regions[0][0] and regions[-1][1] <= g.nz
+    assert [hi - lo for lo, hi in regions[:8]] == [50] * 8 and 50 * g.vz == 200.0
+    sigma = oracle.tof_sigma_mm(300.0)
+    slabs = oracle.region_slabs(g, regions, 3.0 * sigma + 6.0)
+    widths = [hi - lo for lo, hi in slabs]
+    assert min(widths) >= 60 and max(widths) <= 110
+    ev = synth.events("fullbody", 400_000, 1708).astype(np.float64)
+    codes = oracle.region_codes(ev, oracle.region_bounds(g, regions), 6.0)
+    offs, _ = oracle.region_members(codes, 9)
+    share = np.diff(offs) / ev.shape[1]
+    assert share.min() >= 4.0 / 146.0 and share.max() <= 35.0 / 146.0
+    assert np.count_nonzero(codes == 0xFF) < 0.005 * ev.shape[1]

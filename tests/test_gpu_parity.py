@@ -82,6 +82,30 @@ def test_mlem_matches_oracle_5_iterations(tiny, graphs):
     assert np.all(lam >= 0)
 
 
+def test_mlem_resumes_from_a_saved_image(tiny):
+    # checkpoint / resume through the C-ABI: 3 iterations equal 1 iteration, the
+    # image read back, then 2 iterations started from it (recon_mlem's init).  The
+    # image stays FP32 between iterations on both routes, so only the order of the
+    # FP32 reductions differs.
+    g, ev, lors, s_ref, ctx = tiny
+    ctx.sensitivity(lors)
+    lam3 = np.zeros(g.n_vox, np.float32)
+    cons3 = np.zeros((3, 2))
+    ctx.mlem(B.make_events(ev), 3, None, lam3, cons3)
+    lam1 = np.zeros(g.n_vox, np.float32)
+    cons1 = np.zeros((1, 2))
+    ctx.mlem(B.make_events(ev), 1, None, lam1, cons1)
+    lam_r = np.zeros(g.n_vox, np.float32)
+    cons_r = np.zeros((2, 2))
+    ctx.mlem(B.make_events(ev), 2, lam1, lam_r, cons_r)
+    assert rel_l2(lam_r, lam3) <= 1e-5
+    assert max_rel_above(lam_r, lam3, 0.01) <= 1e-4
+    assert cons1[0, 0] == cons3[0, 0]
+    assert np.all(np.abs(cons_r[:, 0] - cons3[1:, 0]) <= 0.5)      # same events with p > 0
+    np.testing.assert_allclose(cons_r[:, 1], cons3[1:, 1], rtol=1e-6)
+    assert rel_l2(lam1, lam3) > 1e-3                                 # the check is not vacuous
+
+
 _cache = {}
 
 

@@ -390,6 +390,23 @@ def test_mlem_invariants_on_tiny_subset():
     assert np.all(lam[s == 0] == 0)
 
 
+def test_mlem_resumes_from_a_saved_image():
+    # checkpoint / resume: an MLEM iteration depends only on the image it starts
+    # from (Sec. 2.4), so n iterations equal k iterations, saved, then n - k more
+    # started from the saved image; the oracle reproduces them bit for bit
+    ev = synth.events("tiny", 4000, 1707).astype(np.float64)
+    lors = synth.sensitivity_lors("tiny", 20000, 1707)
+    g = Grid.centred(32, 32, 48, 4.0)
+    sigma = oracle.tof_sigma_mm(300.0)
+    s = oracle.sensitivity(g, lors)
+    lam3, hist3 = oracle.mlem(g, ev, s, 3, sigma)
+    lam1, hist1 = oracle.mlem(g, ev, s, 1, sigma)
+    lam_r, hist_r = oracle.mlem(g, ev, s, 2, sigma, init=lam1)
+    assert np.array_equal(lam_r, lam3)
+    assert hist1 + hist_r == hist3
+    assert not np.array_equal(lam1, lam3)
+
+
 # ------------------------------------------------------------ region division
 
 def test_region_codes_golden_boundaries():

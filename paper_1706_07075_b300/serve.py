@@ -4,7 +4,9 @@ Jobs (list-mode events + scanner + grid + iteration count) arrive at any
 time.  The scheduler admits queued jobs, oldest first, whenever a slot is
 free and the job's device-memory footprint fits the remaining HBM budget; a
 later, smaller job may pass an older one that does not fit yet (first fit in
-arrival order).  Each slot owns a CUDA stream and a reconstruction context
+arrival order).  With `max_overtakes` set, a job that later jobs have passed
+that many times holds the line: no younger job starts until it does, so a
+large job cannot starve behind a stream of small ones.  Each slot owns a CUDA stream and a reconstruction context
 per image grid, so the upload, the MLEM iterations and the read-back of
 concurrent jobs overlap on the GPU.  Sensitivity images are computed once
 per (scanner, grid) and stay resident on the device; contexts are kept and
@@ -60,14 +62,21 @@ class _Queued:
     arrival: float
     seq: int
     job: Job = field(compare=False)
+    overtaken: int = field(default=0, compare=False)   # younger jobs admitted while this one waited
 
 
 class Server:
-    """Admission, slots and the HBM budget; `executor.run(job, slot)` does the work."""
+    """Admission, slots and the HBM budget; `executor.run(job, slot)` does the work.
 
-    def __init__(self, executor, slots=3, hbm_budget_bytes=200 << 30, clock=time.perf_counter):
+    max_overtakes: None (plain first fit) or the number of times younger jobs
+    may be admitted past a waiting job before it blocks further admissions."""
+
+    def __init__(self, executor, slots=3, hbm_budget_bytes=200 << 30, clock=time.perf_counter, max_overtakes=None):
         if slots < 1:
             raise ValueError("slots must be >= 1")
+        if max_overtakes is not None and max_overtakes < 0:
+            raise ValueError("max_overtakes must be None or >= 0")
+        self.max_overtakes = max_overtakes
         self.executor = executor
         self.slots = slots
         self.budget = int(hbm_budget_bytes)
@@ -99,23 +108,28 @@ class Server:
             self._admit_locked()
 
     def _admit_locked(self):
-        """First fit in arrival order while slots and budget allow."""
+        """First fit in arrival order while slots and budget allow; a waiting job
+        passed max_overtakes times stops younger jobs from being admitted."""
         kept = []
         while self._queue and self._free_slots:
             q = heapq.heappop(self._queue)
             fp = q.job.footprint()
-            if self._in_use + fp <= self.budget:
-                slot = self._free_slots.pop(0)
-                self._in_use += fp
-                q.job.admitted = self.now()
-                q.job.slot = slot
-                self._running += 1
-                self.max_concurrent = max(self.max_concurrent, self._running)
-                t = threading.Thread(target=self._work, args=(q.job, slot, fp), daemon=True)
-                self._threads.append(t)
-                t.start()
-            else:
+            if self._in_use + fp > self.budget:
                 kept.append(q)
+                if self.max_overtakes is not None and q.overtaken >= self.max_overtakes:
+                    break          # it holds the line until the budget frees up for it
+                continue
+            for older in kept:
+                older.overtaken += 1
+            slot = self._free_slots.pop(0)
+            self._in_use += fp
+            q.job.admitted = self.now()
+            q.job.slot = slot
+            self._running += 1
+            self.max_concurrent = max(self.max_concurrent, self._running)
+            t = threading.Thread(target=self._work, args=(q.job, slot, fp), daemon=True)
+            self._threads.append(t)
+            t.start()
         for q in kept:
             heapq.heappush(self._queue, q)
 

@@ -1,6 +1,6 @@
 """Host-side logic of the continuous-batching server (no GPU): admission by
-slots and HBM footprint, first fit in arrival order, release on completion
-and on failure, latency bookkeeping."""
+slots and HBM footprint, first fit in arrival order with an optional
+overtake limit, release on completion and on failure, latency bookkeeping."""
 import threading
 import time
 
@@ -77,6 +77,36 @@ def test_first_fit_lets_a_small_job_pass_a_large_one():
         srv._admit_locked()
     srv.drain(timeout=5)
     assert big.result == 1
+
+
+def test_overtake_limit_stops_a_large_job_from_starving():
+    # with max_overtakes = 1 one later job may pass the waiting large job; the
+    # next one waits behind it although it would fit, and both start once the
+    # budget frees up for the large job
+    ref = [None]
+    ex = FakeExecutor(ref)
+    small = make_job(0, 10).footprint()
+    big = make_job(1, 10, grid=(1000, 1000, 100, 1, 1, 1, 0, 0, 0))
+    srv = Server(ex, slots=3, hbm_budget_bytes=big.footprint() + small, max_overtakes=1)
+    ref[0] = srv
+    srv.start()
+    with srv._lock:
+        srv._in_use = 2 * small           # reserved: the big job cannot start yet
+    s1, s2 = make_job(2, 10, arrival=0.0), make_job(3, 10, arrival=0.0)
+    srv.submit(big)
+    srv.submit(s1)                        # passes the big job (first overtake)
+    srv.submit(s2)                        # would fit, but the big job holds the line
+    time.sleep(0.05)
+    assert s1.admitted is not None and s1.finished is not None
+    assert big.admitted is None and s2.admitted is None
+    with srv._lock:
+        srv._in_use -= 2 * small
+        srv._admit_locked()
+    srv.drain(timeout=5)
+    assert big.result == 1 and s2.result == 3
+    assert big.admitted <= s2.admitted
+    with pytest.raises(ValueError):
+        Server(ex, max_overtakes=-1)
 
 
 def test_failed_job_releases_its_slot_and_memory():

@@ -53,6 +53,24 @@ def test_bench_arms_share_the_workload_config():
     assert bench.workload_config(args, args.events, 4)["parallelism"] == "replicas4"
 
 
+def test_bench_reference_arm_prints_one_json_line():
+    # the oracle arm of bench.py on a small sample: one JSON line with the keys
+    # of the benchmark contract and the same workload description as the CUDA arm
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1", "--cpu-sample", "20000"], cwd=ROOT, capture_output=True, text=True,
+                         timeout=600, check=True).stdout.strip().splitlines()
+    line = json.loads(out[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["unit"] == "events*iters/s" and line["steps"] == 1 and line["warmup"] == 1
+    assert line["config"]["workload"] == "fullbody-146M-150x150x600-4mm"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert "20000" in line["cpu_baseline"]["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
 def test_bench_roofline_terms_and_fraction():
     # the roofline arithmetic of bench.py on the figures of a measured full-body run:
     # 146 M events x 44.25 pieces, pass 31.2 ms, live probes as measured

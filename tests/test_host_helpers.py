@@ -200,3 +200,17 @@ def test_fullbody_regions_cover_the_body_in_nine_uneven_regions():
     share = np.diff(offs) / ev.shape[1]
     assert share.min() >= 4.0 / 146.0 and share.max() <= 35.0 / 146.0
     assert np.count_nonzero(codes == 0xFF) < 0.005 * ev.shape[1]
+
+
+def test_synthetic_draws_do_not_depend_on_the_worker_count():
+    # chunk k of a draw comes from its own Philox stream keyed by (seed, kind, k):
+    # the same events with one worker or several, and whole chunks of a longer
+    # draw equal a shorter draw of those chunks
+    n = 2 * synth.CHUNK + 1000
+    one = synth.events("tiny", n, 11, workers=1)
+    two = synth.events("tiny", n, 11, workers=2)
+    assert np.array_equal(one, two)
+    assert np.array_equal(synth.events("tiny", synth.CHUNK, 11, workers=1), one[:, :synth.CHUNK])
+    lors1 = synth.sensitivity_lors("tiny", n, 11, workers=1)
+    assert np.array_equal(lors1, synth.sensitivity_lors("tiny", n, 11, workers=3))
+    assert not np.array_equal(one[:, :1000], synth.events("tiny", 1000, 12, workers=1))

@@ -410,6 +410,24 @@ def time_lut_leg(ctx, B, n, args, stream, img_exact):
     st1 = ctx.get_stats()
     img_lut = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
     ctx.mlem(None, args.iters, None, img_lut, cons)
+    # the same pass over 2x2x2-brick copies of lambda and C (one vector reduction per
+    # 16-byte brick half a lane visits in a row)
+    cons_b = np.zeros_like(cons)
+    ctx.set_brick_layout(1)
+    try:
+        ctx.mlem(None, args.iters, None, None, cons_b)     # warm-up
+        b0 = ctx.get_stats()
+        ms_b = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons_b))
+        b1 = ctx.get_stats()
+        img_b = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
+        ctx.mlem(None, args.iters, None, img_b, cons_b)
+    finally:
+        ctx.set_brick_layout(0)
+    bricks = {"value": n * args.iters * args.steps / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b / args.steps,
+              "gpu_launches": int(b1["kernel_launches"] - b0["kernel_launches"]),
+              "image_rel_l2_vs_linear": float(torch.linalg.vector_norm(img_b.double() - img_lut.double()) /
+                                              torch.linalg.vector_norm(img_lut.double())),
+              "conservation_last": [float(x) for x in cons_b[-1]]}
     p_lut = torch.empty(n, dtype=torch.float32, device=dev)
     p_ex = torch.empty(n, dtype=torch.float32, device=dev)
     lam = img_exact.to(dev)
@@ -424,7 +442,7 @@ def time_lut_leg(ctx, B, n, args, stream, img_exact):
             "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
             "image_rel_l2_vs_exact": float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)),
             "forward_rel_l2_vs_exact": fwd_rel, "conservation_last": [float(x) for x in cons[-1]],
-            "steps": args.steps}
+            "steps": args.steps, "brick_layout": bricks}
 
 
 def time_osem_leg(ctx, B, n, args, stream, subsets=5):

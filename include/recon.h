@@ -273,6 +273,17 @@ recon_status recon_median_filter(recon_ctx* ctx, const float* image_in, float* i
  * Backprojection always accumulates in FP32. */
 recon_status recon_set_gather_bf16(recon_ctx* ctx, int32_t on);
 
+/* Image layout of the sampled projector's MLEM pass (recon_mlem with RECON_PROJ_SAMPLED,
+ * FP32 gathers): 0 (default) the linear layout; 1 copies of lambda and C in 2x2x2-voxel
+ * bricks, one 32-byte sector per brick, so that a lane's consecutive samples within one
+ * 16-byte brick half go out as one vector reduction (fewer L2 requests).  Each pass then
+ * copies lambda into the bricks before and adds the brick copy of C into C after.  Same
+ * visits and weights as the linear pass; the sums run in another order.  Not used by the
+ * exact projector, with BF16 gathers, by recon_mlem_regions or by the first pass of a
+ * call that streams host events.  Costs two device images of 8 ceil(nx/2) ceil(ny/2)
+ * ceil(nz/2) floats.  EINVAL if on is not 0 or 1, or that count exceeds 2^31. */
+recon_status recon_set_brick_layout(recon_ctx* ctx, int32_t on);
+
 /* Fix the event-pass launch (NULL: return to the autotuner).  EINVAL if invalid. */
 recon_status recon_set_launch(recon_ctx* ctx, const recon_launch* cfg);
 /* The launch the last event pass used. */

@@ -74,6 +74,7 @@ SIGNATURES = {
     "recon_set_stream": (C.c_int, [_CTX, _VP]),
     "recon_set_kernel_window": (C.c_int, [_CTX, C.c_double]),
     "recon_set_gather_bf16": (C.c_int, [_CTX, C.c_int32]),
+    "recon_set_brick_layout": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_projector": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "recon_set_median_filter": (C.c_int, [_CTX, C.c_int32]),
     "recon_set_subsets": (C.c_int, [_CTX, C.c_int32]),
@@ -234,6 +235,10 @@ def recon_set_kernel_window(ctx, k_sigma):
 
 def recon_set_gather_bf16(ctx, on):
     return check(ctx, load().recon_set_gather_bf16(ctx, int(bool(on))))
+
+
+def recon_set_brick_layout(ctx, on):
+    return check(ctx, load().recon_set_brick_layout(ctx, int(on)))
 
 
 PROJ_EXACT = 0

@@ -250,8 +250,53 @@ __device__ __forceinline__ LutLine lut_line(const GridDev& g, const Event& e)
 // Visit (voxel, summed weight) of every run of consecutive samples that share
 // a voxel inside the grid.  NS > 0: the sample count known at compile time (the
 // loop unrolls and the table entries become constant operands); 0: lut.n.
-template <int NS, class Visit>
-__device__ __forceinline__ void lut_walk(const GridDev& g, const LutH& lut, const LutLine& l, Visit&& visit)
+// 2x2x2-voxel bricks: with bx = ceil(nx/2) and by = ceil(ny/2) bricks per row and
+// per plane, brick (ix/2, iy/2, iz/2) holds its 8 voxels contiguously in the order
+// (ix & 1) + 2 (iy & 1) + 4 (iz & 1): one 32-byte sector, split by the z parity into
+// two 16-byte halves.  Every index of a voxel inside the grid is below
+// 8 bx by ceil(nz/2).
+__device__ __forceinline__ int brick_index(int ix, int iy, int iz, int bx, int by)
+{
+    return ((((iz >> 1) * by + (iy >> 1)) * bx + (ix >> 1)) << 3) | ((iz & 1) << 2) | ((iy & 1) << 1) | (ix & 1);
+}
+
+// Reductions into a brick-layout image: a lane's consecutive visits that fall into
+// one 16-byte brick half are summed in registers and sent as one
+// red.global.add.v4.f32 (slots of the half it did not visit add 0).
+struct HalfRed {
+    float* base;
+    int half = -1;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+    __device__ __forceinline__ void add(int q, float v)
+    {
+        const int h = q >> 2;
+        if (h != half) {
+            flush();
+            half = h;
+        }
+        const int slot = q & 3;
+        v0 += slot == 0 ? v : 0.f;
+        v1 += slot == 1 ? v : 0.f;
+        v2 += slot == 2 ? v : 0.f;
+        v3 += slot == 3 ? v : 0.f;
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if (half >= 0)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(base + 4LL * half), "f"(v0), "f"(v1),
+                         "f"(v2), "f"(v3)
+                         : "memory");
+        half = -1;
+        v0 = v1 = v2 = v3 = 0.f;
+    }
+};
+
+// Samples of one line; consecutive samples in one voxel are merged into one visit
+// (voxel index, summed weight).  Brick: the index is the voxel's place in the brick
+// layout (bx, by bricks per row and plane) instead of the linear one.
+template <int NS, bool Brick = false, class Visit>
+__device__ __forceinline__ void lut_walk(const GridDev& g, const LutH& lut, const LutLine& l, Visit&& visit,
+                                         int bx = 0, int by = 0)
 {
     if (!l.valid) return;
     const float fnx = (float)g.nx, fny = (float)g.ny, fnz = (float)g.nz;
@@ -265,7 +310,8 @@ __device__ __forceinline__ void lut_walk(const GridDev& g, const LutH& lut, cons
         const float fy = floorf(__fmaf_rn(s.x, l.by, l.ay));
         const float fz = floorf(__fmaf_rn(s.x, l.bz, l.az));
         const bool in = fx >= 0.f && fx < fnx && fy >= 0.f && fy < fny && fz >= 0.f && fz < fnz;
-        const int j = in ? (int)fx + g.nx * ((int)fy + g.ny * (int)fz) : -1;
+        int j = -1;
+        if (in) j = Brick ? brick_index((int)fx, (int)fy, (int)fz, bx, by) : (int)fx + g.nx * ((int)fy + g.ny * (int)fz);
         if (j != prev) {
             if (prev >= 0) visit(prev, acc);
             prev = j;
@@ -274,6 +320,29 @@ __device__ __forceinline__ void lut_walk(const GridDev& g, const LutH& lut, cons
         acc += s.y;
     }
     if (prev >= 0) visit(prev, acc);
+}
+
+// Fused pass over an image in the brick layout (one grid, FP32 gathers): the same
+// visits and weights as the linear pass; the reductions go out per brick half.
+template <int Fmt, int NS>
+__device__ __forceinline__ float do_event_lut_brick(const PassArgs& a, const SharedTable& t, long long i,
+                                                    int& region)
+{
+    region = 0;
+    const GridDev& g = t.grid[0];
+    const Event e = load_event<Fmt>(a, i);
+    const LutLine l = lut_line(g, e);
+    const float* const lb = a.lam;
+    float p = 0.f;
+    lut_walk<NS, true>(
+        g, a.lut, l, [&](int q, float w) { p = fmaf(w, __ldg(lb + q), p); }, a.brick_bx, a.brick_by);
+    if (!(p > 0.f)) return 0.f;
+    const float r = e.w / p;
+    HalfRed hr{a.C};
+    lut_walk<NS, true>(
+        g, a.lut, l, [&](int q, float w) { hr.add(q, w * r); }, a.brick_bx, a.brick_by);
+    hr.flush();
+    return e.w;
 }
 
 template <int Kind, int Fmt, int NS>
@@ -309,7 +378,7 @@ __device__ __forceinline__ float do_event_lut(const PassArgs& a, const SharedTab
     return e.w;
 }
 
-template <int Kind, int Fmt, int NS>
+template <int Kind, int Fmt, int NS, bool Brick = false>
 __global__ void __launch_bounds__(256) k_lut_pass(PassArgs a, RegionTable tbl)
 {
     __shared__ SharedTable t;
@@ -326,7 +395,10 @@ __global__ void __launch_bounds__(256) k_lut_pass(PassArgs a, RegionTable tbl)
     const long long i = (long long)b * blockDim.x + threadIdx.x;
     int r = 0;
     float w = 0.f;
-    if (i < a.n) w = do_event_lut<Kind, Fmt, NS>(a, t, i, a.lam_bf16 != nullptr, r);
+    if (i < a.n) {
+        if constexpr (Brick) w = do_event_lut_brick<Fmt, NS>(a, t, i, r);
+        else w = do_event_lut<Kind, Fmt, NS>(a, t, i, a.lam_bf16 != nullptr, r);
+    }
     if (Kind == PASS_FUSED) add_neff(neff, r, w);
     if (Kind == PASS_FUSED) {
         __syncthreads();
@@ -341,6 +413,14 @@ cudaError_t launch_lut(const LaunchCfg& cfg, const PassArgs& a, const RegionTabl
     if (a.lut.n < 1 || a.lut.n > kMaxLutSamples) return cudaErrorInvalidValue;
     const long long blocks = (a.n + cfg.threads - 1) / cfg.threads;
     if (blocks == 0) return cudaSuccess;
+    if (a.brick_bx > 0) {
+        // brick layout: fused pass over one grid with FP32 gathers only
+        if (Kind != PASS_FUSED || tbl.n != 1 || a.lam_bf16 || tbl.grid[0].vox_offset != 0)
+            return cudaErrorInvalidValue;
+        if (a.lut.n == 32) k_lut_pass<PASS_FUSED, Fmt, 32, true><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
+        else k_lut_pass<PASS_FUSED, Fmt, 0, true><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
+        return cudaGetLastError();
+    }
     if (a.lut.n == 32) k_lut_pass<Kind, Fmt, 32><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
     else if (a.lut.n == 15) k_lut_pass<Kind, Fmt, 15><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
     else k_lut_pass<Kind, Fmt, 0><<<(unsigned)blocks, cfg.threads, 0, s>>>(a, tbl);
@@ -391,7 +471,62 @@ cudaError_t launch_kind(const LaunchCfg& cfg, const PassArgs& a, const RegionTab
     return launch_tail<Kind, Fmt, TAIL_ERFC>(blocks, cfg, a, tbl, s);
 }
 
+// Linear image -> brick copy (x fastest in the linear image).
+__global__ void k_to_bricks(const float* __restrict__ lin, float* __restrict__ br, int nx, int ny, int nz, int bx,
+                            int by)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(j % nx);
+        const long long rest = j / nx;
+        const int iy = (int)(rest % ny), iz = (int)(rest / ny);
+        br[brick_index(ix, iy, iz, bx, by)] = lin[j];
+    }
+}
+
+// lin += brick copy; the brick copy is cleared for the next pass.
+__global__ void k_from_bricks_add(float* __restrict__ br, float* __restrict__ lin, int nx, int ny, int nz, int bx,
+                                  int by)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(j % nx);
+        const long long rest = j / nx;
+        const int iy = (int)(rest % ny), iz = (int)(rest / ny);
+        const int q = brick_index(ix, iy, iz, bx, by);
+        lin[j] += br[q];
+        br[q] = 0.f;
+    }
+}
+
+unsigned brick_blocks(long long n)
+{
+    const long long b = (n + 255) / 256;
+    return (unsigned)std::max(1LL, std::min(b, 148LL * 32));
+}
+
 }  // namespace
+
+long long brick_voxels(int nx, int ny, int nz)
+{
+    return 8LL * ((nx + 1) / 2) * ((ny + 1) / 2) * ((nz + 1) / 2);
+}
+
+cudaError_t launch_to_bricks(const float* lin, float* br, int nx, int ny, int nz, cudaStream_t s)
+{
+    const long long n = (long long)nx * ny * nz;
+    if (n <= 0) return cudaSuccess;
+    k_to_bricks<<<brick_blocks(n), 256, 0, s>>>(lin, br, nx, ny, nz, (nx + 1) / 2, (ny + 1) / 2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_bricks_add(float* br, float* lin, int nx, int ny, int nz, cudaStream_t s)
+{
+    const long long n = (long long)nx * ny * nz;
+    if (n <= 0) return cudaSuccess;
+    k_from_bricks_add<<<brick_blocks(n), 256, 0, s>>>(br, lin, nx, ny, nz, (nx + 1) / 2, (ny + 1) / 2);
+    return cudaGetLastError();
+}
 
 int pass_blocks(const LaunchCfg& cfg, long long n, int num_sms)
 {

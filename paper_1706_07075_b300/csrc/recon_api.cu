@@ -122,6 +122,8 @@ struct recon_ctx {
 
     // options
     bool bf16 = false, timing = false, graphs = true, autotune = true;
+    bool bricks = false;  // sampled pass of recon_mlem over 2x2x2-brick copies of lambda and C
+    DevBuf lam_brick, C_brick;
     bool user_cfg = false;
     LaunchCfg cfg{192, 0, 0, 0, TAIL_SERIES};
     LaunchCfg last_cfg{192, 0, 0, 0, TAIL_SERIES};
@@ -499,6 +501,7 @@ struct IterPlan {
     int max_nz;
     int subsets;     // OSEM subsets (1: MLEM); single-region plans only
     size_t rec_bytes;
+    bool bricks = false;  // the sampled pass runs over the context's brick copies of lam and C
     // shared-memory tiled pass (single region, MLEM, exact projector)
     bool tiled = false;
     TileH th{};
@@ -515,7 +518,7 @@ struct IterPlan {
 // The fused event pass of one (sub-)iteration: the tiled pass over the binned
 // events plus the global-memory pass over the fallback events, or the
 // global-memory pass alone.
-recon_status launch_event_pass(recon_ctx* ctx, const IterPlan& p, const PassArgs& a, const RegionTable& t)
+recon_status launch_event_pass_layout(recon_ctx* ctx, const IterPlan& p, const PassArgs& a, const RegionTable& t)
 {
     if (!p.tiled) {
         if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
@@ -547,6 +550,25 @@ recon_status launch_event_pass(recon_ctx* ctx, const IterPlan& p, const PassArgs
         if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
         CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, af, tf, ctx->num_sms, ctx->stream));
     }
+    return RECON_OK;
+}
+
+// The event pass in the image layout of the plan: with bricks, lambda is copied into
+// the brick layout first, the pass reduces into the brick copy of C, and that copy
+// is added into C (and cleared) afterwards.
+recon_status launch_event_pass(recon_ctx* ctx, const IterPlan& p, const PassArgs& a, const RegionTable& t)
+{
+    if (!p.bricks) return launch_event_pass_layout(ctx, p, a, t);
+    const recon_grid& g = ctx->grid;
+    CK(launch_to_bricks(a.lam, ctx->lam_brick.as<float>(), g.nx, g.ny, g.nz, ctx->stream));
+    PassArgs ab = a;
+    ab.lam = ctx->lam_brick.as<float>();
+    ab.C = ctx->C_brick.as<float>();
+    ab.brick_bx = (g.nx + 1) / 2;
+    ab.brick_by = (g.ny + 1) / 2;
+    recon_status s = launch_event_pass_layout(ctx, p, ab, t);
+    if (s != RECON_OK) return s;
+    CK(launch_from_bricks_add(ctx->C_brick.as<float>(), a.C, g.nx, g.ny, g.nz, ctx->stream));
     return RECON_OK;
 }
 
@@ -601,9 +623,10 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
              (void*)p.hist, (void*)p.iter, p.hist_cap, (void*)ctx->stream, ctx->ev_generation, p.tbl.n,
              (double)p.a.tof.half_window, (double)p.a.tof.inv_sigma_sqrt2, (double)p.a.lattice);
     std::string k(buf);
-    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %d %p %u %p %p %lld %lld %d bm %u", p.a.lut.n,
-             (void*)p.med, p.med_vox, p.max_nz, p.subsets, (int)p.tiled, p.tile_mode, (const void*)p.list, p.n_list,
-             p.ev_cell, p.ev_fb, p.n_fb, p.n_cell_events, ctx->tile_lanes, p.a.block_mul);
+    snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %d %p %u %p %p %lld %lld %d bm %u br %d %p %p",
+             p.a.lut.n, (void*)p.med, p.med_vox, p.max_nz, p.subsets, (int)p.tiled, p.tile_mode, (const void*)p.list,
+             p.n_list, p.ev_cell, p.ev_fb, p.n_fb, p.n_cell_events, ctx->tile_lanes, p.a.block_mul, (int)p.bricks,
+             ctx->lam_brick.p, ctx->C_brick.p);
     k += buf;
     for (int r = 0; r < p.tbl.n; ++r) {
         snprintf(buf, sizeof buf, "|%lld %d %a %lld", p.tbl.ev_begin[r + 1], p.tbl.grid[r].nz,
@@ -646,7 +669,7 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool 
                 CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions,
                                    p.hist, p.iter, p.hist_cap, ctx->stream));
                 ctx->stats.kernel_launches += (a.n > 0 ? 3 : 2) + (p.med && b == B - 1 ? 1 : 0) +
-                                              (p.tiled && p.n_fb > 0 ? 1 : 0);
+                                              (p.tiled && p.n_fb > 0 ? 1 : 0) + (p.bricks ? 2 : 0);
             }
         }
         if (ctx->timing) {
@@ -685,8 +708,8 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool 
     }
     for (int k = 0; k < n_iter; ++k) {
         CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-        ctx->stats.kernel_launches += (long long)p.subsets * (p.pass_blocks > 0 ? 3 : 2) + (p.med ? 1 : 0) +
-                                      (p.tiled && p.n_fb > 0 ? 1 : 0);
+        ctx->stats.kernel_launches += (long long)p.subsets * ((p.pass_blocks > 0 ? 3 : 2) + (p.bricks ? 2 : 0)) +
+                                      (p.med ? 1 : 0) + (p.tiled && p.n_fb > 0 ? 1 : 0);
     }
     return RECON_OK;
 }
@@ -867,7 +890,8 @@ void recon_destroy(recon_ctx* ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     invalidate_graph(ctx);
-    DevBuf* bufs[] = {&ctx->s64, &ctx->s32, &ctx->lam, &ctx->C, &ctx->lam_bf16, &ctx->ev, &ctx->staging,
+    DevBuf* bufs[] = {&ctx->s64, &ctx->s32, &ctx->lam, &ctx->C, &ctx->lam_bf16, &ctx->lam_brick, &ctx->C_brick,
+                      &ctx->ev, &ctx->staging,
                       &ctx->pass_partial, &ctx->upd_partial, &ctx->work, &ctx->iter, &ctx->hist, &ctx->reg_vox,
                       &ctx->red_partial, &ctx->vec, &ctx->med, &ctx->mu, &ctx->keep, &ctx->counter, &ctx->codes, &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
                       &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg,
@@ -1024,6 +1048,17 @@ recon_status recon_set_gather_bf16(recon_ctx* ctx, int32_t on)
     CHECK_CTX();
     ctx->bf16 = on != 0;
     if (ctx->bf16) CK(ensure(ctx->lam_bf16, sizeof(uint16_t) * ctx->n_vox));
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
+recon_status recon_set_brick_layout(recon_ctx* ctx, int32_t on)
+{
+    CHECK_CTX();
+    if (on != 0 && on != 1) return fail(ctx, RECON_EINVAL, "on must be 0 or 1");
+    if (on && brick_voxels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz) > 0x7fffffffLL)
+        return fail(ctx, RECON_EINVAL, "grid too large for the brick layout (2^31 voxels)");
+    ctx->bricks = on != 0;
     invalidate_graph(ctx);
     return RECON_OK;
 }
@@ -1618,6 +1653,13 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     p.med = nullptr;
     p.med_vox = nv;
     p.max_nz = ctx->grid.nz;
+    p.bricks = ctx->bricks && ctx->lut_n > 0 && !ctx->bf16;
+    if (p.bricks) {
+        const size_t nb = (size_t)brick_voxels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
+        CK(ensure(ctx->lam_brick, sizeof(float) * nb));
+        CK(ensure(ctx->C_brick, sizeof(float) * nb));
+        CK(cudaMemsetAsync(ctx->C_brick.p, 0, sizeof(float) * nb, ctx->stream));
+    }
     if (ctx->median) {
         CK(ensure(ctx->med, sizeof(float) * (size_t)nv));
         p.med = ctx->med.as<float>();

@@ -83,7 +83,16 @@ struct PassArgs {
                                  // (0 or 1: identity); a multiplier coprime with the grid spreads
                                  // region-ordered events over all regions at any moment
     LutH lut;                    // sampled TOF kernel (lut.n > 0) instead of the exact one
+    int brick_bx, brick_by;      // > 0: lam and C are in the 2x2x2-brick layout with these bricks per row
+                                 // and plane (sampled fused pass over one grid, FP32 gathers)
 };
+
+// Voxels of the 2x2x2-brick layout of an nx x ny x nz grid (8 per brick, the
+// bricks padding odd extents), and the copies between it and the linear layout:
+// brick <- linear, and linear += brick with the brick copy cleared.
+long long brick_voxels(int nx, int ny, int nz);
+cudaError_t launch_to_bricks(const float* lin, float* br, int nx, int ny, int nz, cudaStream_t s);
+cudaError_t launch_from_bricks_add(float* br, float* lin, int nx, int ny, int nz, cudaStream_t s);
 
 // Number of blocks a pass launch uses.
 int pass_blocks(const LaunchCfg& cfg, long long n, int num_sms);

@@ -113,6 +113,75 @@ def test_mlem_lut_matches_oracle_5_iterations(tiny, graphs):
         assert cons[k, 1] == pytest.approx(cons[k, 0], rel=1e-5)     # sum s lambda = N_eff
 
 
+_ref_cache = {}
+
+
+def _oracle_lut_mlem_tiny(g, ev, s_ref):
+    if "mlem5" not in _ref_cache:
+        _ref_cache["mlem5"] = oracle.mlem(g, ev.astype(np.float64), s_ref, 5, SIGMA, lut_samples=32)
+    return _ref_cache["mlem5"]
+
+
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_mlem_lut_brick_layout_matches_oracle(tiny, graphs):
+    # the sampled pass over 2x2x2-brick copies of lambda and C: the same visits and
+    # weights, reductions per 16-byte brick half.  Resident events (every pass in
+    # bricks) and host events (the streamed first pass linear, the rest in bricks).
+    g, ev, lors, ctx = tiny
+    s_ref = oracle.sensitivity(g, lors)
+    ctx.set_sensitivity(s_ref)
+    ctx.set_projector(B.PROJ_SAMPLED, 32)
+    ctx.set_graphs(graphs)
+    ctx.load_events(B.make_events(ev))
+    lin = np.zeros(g.n_vox, np.float32)
+    ctx.mlem(None, 5, None, lin, np.zeros((5, 2)))
+    ctx.set_brick_layout(1)
+    try:
+        out = []
+        for events in (None, B.make_events(ev)):
+            img = np.zeros(g.n_vox, np.float32)
+            cons = np.zeros((5, 2))
+            ctx.mlem(events, 5, None, img, cons)
+            out.append((img, cons))
+    finally:
+        ctx.set_brick_layout(0)
+        ctx.set_projector(B.PROJ_EXACT)
+        ctx.set_graphs(1)
+    lam_ref, hist = _oracle_lut_mlem_tiny(g, ev, s_ref)
+    for img, cons in out:
+        assert rel_l2(img, lam_ref) <= 1e-4
+        assert max_rel_above(img, lam_ref, 0.01) <= 1e-3
+        for k in range(5):
+            assert cons[k, 0] == pytest.approx(hist[k][0], abs=0.5)
+            assert cons[k, 1] == pytest.approx(cons[k, 0], rel=1e-5)
+        assert rel_l2(img, lin) <= 1e-5
+        assert max_rel_above(img, lin, 0.01) <= 1e-4
+
+
+def test_mlem_lut_brick_layout_odd_grid():
+    # odd extents on every axis: the bricks pad each axis by one voxel
+    ev = synth.events("tiny", 50_000, 31)
+    lors = synth.sensitivity_lors("tiny", 300_000, 31)
+    g = oracle.Grid.centred(33, 31, 47, 4.0)
+    s_ref = oracle.sensitivity(g, lors)
+    with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx:
+        with pytest.raises(B.ReconError):
+            ctx.set_brick_layout(2)
+        ctx.set_sensitivity(s_ref)
+        ctx.set_projector(B.PROJ_SAMPLED, 32)
+        ctx.set_brick_layout(1)
+        ctx.load_events(B.make_events(ev))
+        img = np.zeros(g.n_vox, np.float32)
+        cons = np.zeros((3, 2))
+        ctx.mlem(None, 3, None, img, cons)
+    lam_ref, hist = oracle.mlem(g, ev.astype(np.float64), s_ref, 3, SIGMA, lut_samples=32)
+    assert rel_l2(img, lam_ref) <= 1e-4
+    assert max_rel_above(img, lam_ref, 0.01) <= 1e-3
+    for k in range(3):
+        assert cons[k, 0] == pytest.approx(hist[k][0], abs=0.5)
+        assert cons[k, 1] == pytest.approx(cons[k, 0], rel=1e-5)
+
+
 def test_region_mlem_lut_matches_oracle():
     ev = synth.events("tiny", 120_000, 23)
     lors = synth.sensitivity_lors("tiny", 500_000, 23)

@@ -60,6 +60,7 @@ def test_null_and_invalid_arguments_fail_without_a_device():
     assert lib.recon_mlem(None, None, 1, None, None, None) == B.RECON_EINVAL
     assert lib.recon_sensitivity(None, None, 0, 0, None) == B.RECON_EINVAL
     assert lib.recon_split_regions(None, None, 1, None, 0.0, 0.0, None, None, None) == B.RECON_EINVAL
+    assert lib.recon_set_brick_layout(None, 1) == B.RECON_EINVAL
 
 
 def test_python_binding_raises_with_message():

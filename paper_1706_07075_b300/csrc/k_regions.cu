@@ -47,22 +47,7 @@ __device__ __forceinline__ uint8_t region_code(const float4* ev, const int4* pk,
 {
     double x1, y1, z1, x2, y2, z2, d;
     event_z_inputs(ev, pk, L, i, x1, y1, z1, x2, y2, z2, d);
-    const double dx = __dsub_rn(x1, x2);
-    const double dy = __dsub_rn(y1, y2);
-    const double dz = __dsub_rn(z1, z2);
-    const double D = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-    const double z = __dadd_rn(__dmul_rn(__dadd_rn(z1, z2), 0.5), __ddiv_rn(__dmul_rn(d, dz), D));
-    int first = -1, count = 0;
-    for (int r = 0; r < R; ++r) {
-        if (__dsub_rn(zb[r], shell) <= z && z < __dadd_rn(zb[r + 1], shell)) {
-            if (first < 0) first = r;
-            ++count;
-        }
-    }
-    if (count == 0) return 0xFF;
-    if (count == 1) return (uint8_t)first;
-    if (count == 2) return (uint8_t)(first | 0x80);
-    return 0xFE;
+    return region_code_of(x1, y1, z1, x2, y2, z2, d, zb, R, shell);
 }
 
 struct Bounds {

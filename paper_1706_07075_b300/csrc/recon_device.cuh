@@ -292,6 +292,33 @@ __device__ __forceinline__ void walk(const GridDev& g, const TofDev& tof, const 
     }
 }
 
+// Region code of one event (Sec. 2.5, Fig. 4): the TOF-estimated annihilation z,
+//     z_tof = (z1 + z2) * 0.5 + (d * dz) / D,   D = sqrt((dx*dx + dy*dy) + dz*dz),
+// in FP64 with every operation rounded on its own (no fused multiply-add), then
+// the regions r with z_b[r] - shell <= z_tof < z_b[r+1] + shell.  Returns 0xFF
+// (none), r (one region), r | 0x80 (regions r and r+1) or 0xFE (three or more).
+// The inputs are the event's values converted exactly to FP64.
+__device__ __forceinline__ uint8_t region_code_of(double x1, double y1, double z1, double x2, double y2, double z2,
+                                                  double d, const double* zb, int R, double shell)
+{
+    const double dx = __dsub_rn(x1, x2);
+    const double dy = __dsub_rn(y1, y2);
+    const double dz = __dsub_rn(z1, z2);
+    const double D = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    const double z = __dadd_rn(__dmul_rn(__dadd_rn(z1, z2), 0.5), __ddiv_rn(__dmul_rn(d, dz), D));
+    int first = -1, count = 0;
+    for (int r = 0; r < R; ++r) {
+        if (__dsub_rn(zb[r], shell) <= z && z < __dadd_rn(zb[r + 1], shell)) {
+            if (first < 0) first = r;
+            ++count;
+        }
+    }
+    if (count == 0) return 0xFF;
+    if (count == 1) return (uint8_t)first;
+    if (count == 2) return (uint8_t)(first | 0x80);
+    return 0xFE;
+}
+
 // Warp-wide sum.
 template <class T>
 __device__ __forceinline__ T warp_sum(T v)

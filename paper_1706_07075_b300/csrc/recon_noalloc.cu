@@ -1,11 +1,12 @@
 // recon_split_regions_noalloc: the TOF-assisted region split for callers that
 // must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA stream
-// capture that must not add allocation nodes, processes whose device memory
-// is owned by another allocator (a framework's caching pool, a real-time
-// acquisition service that reserves all memory at start-up), or code paths
-// where an allocation could fail mid-scan.  This entry point takes only
+// Some callers cannot call cudaMalloc.  A process whose device memory belongs
+// to another allocator (a framework's caching pool, or an acquisition service
+// that reserves all of the GPU's memory when it starts) would see an extra
+// allocation fail, or fragment a pool it does not own.  A real-time path
+// cannot afford cudaFree, which waits for the whole device, or an allocation
+// that may fail half-way through a scan.  This entry point takes only
 // caller-owned inputs and outputs; its per-tile counters and prefix sums live
 // in one fixed, file-scope device array that every GPU loading this library
 // holds until the process exits.
@@ -22,7 +23,7 @@
 #include <cuda_runtime.h>
 
 #include "recon.h"
-#include "recon_kernels.h"
+#include "recon_device.cuh"
 
 namespace recon {
 void set_thread_error(const std::string& msg);  // recon_api.cu: message for recon_last_error(NULL)
@@ -52,27 +53,12 @@ long long max_events_for(int R)
     return ((long long)(kScratchBytes - kOffsetsBytes - 8) / per_tile) * kTile;
 }
 
+// Region code of event i of the caller's SoA planes: the same arithmetic as the
+// allocating split (region_code_of in recon_device.cuh).
 __device__ __forceinline__ unsigned char region_code_soa(const float* const* pl, long long i, const double* zb, int R,
                                                          double shell)
 {
-    const double x1 = pl[0][i], y1 = pl[1][i], z1 = pl[2][i];
-    const double x2 = pl[3][i], y2 = pl[4][i], z2 = pl[5][i], d = pl[6][i];
-    const double dx = __dsub_rn(x1, x2);
-    const double dy = __dsub_rn(y1, y2);
-    const double dz = __dsub_rn(z1, z2);
-    const double D = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-    const double z = __dadd_rn(__dmul_rn(__dadd_rn(z1, z2), 0.5), __ddiv_rn(__dmul_rn(d, dz), D));
-    int first = -1, count = 0;
-    for (int r = 0; r < R; ++r) {
-        if (__dsub_rn(zb[r], shell) <= z && z < __dadd_rn(zb[r + 1], shell)) {
-            if (first < 0) first = r;
-            ++count;
-        }
-    }
-    if (count == 0) return 0xFF;
-    if (count == 1) return (unsigned char)first;
-    if (count == 2) return (unsigned char)(first | 0x80);
-    return 0xFE;
+    return region_code_of(pl[0][i], pl[1][i], pl[2][i], pl[3][i], pl[4][i], pl[5][i], pl[6][i], zb, R, shell);
 }
 
 struct Planes {
@@ -136,6 +122,36 @@ recon_status scratch_address(void** out)
     return RECON_OK;
 }
 
+// The call launches kernels that read `p` and write through it, so it must be
+// device (or managed) memory of the current device: a host pointer, pinned or
+// not, is rejected here instead of faulting in a kernel.
+recon_status check_device_pointer(const void* p, const char* what)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    char buf[200];
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(buf, sizeof buf, "%s is not a device pointer (%s)", what, cudaGetErrorString(e));
+        return fail(RECON_EINVAL, buf);
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+        snprintf(buf, sizeof buf, "%s must be device memory (got %s memory)", what,
+                 at.type == cudaMemoryTypeHost ? "page-locked host" : "unregistered host");
+        return fail(RECON_EINVAL, buf);
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(RECON_ECUDA, "cudaGetDevice failed");
+    }
+    if (at.type == cudaMemoryTypeDevice && at.device != dev) {
+        snprintf(buf, sizeof buf, "%s lives on device %d, not on the current device %d", what, at.device, dev);
+        return fail(RECON_EINVAL, buf);
+    }
+    return RECON_OK;
+}
+
 }  // namespace
 
 extern "C" recon_status recon_split_regions_noalloc(const recon_grid* grid, const recon_events* events,
@@ -173,6 +189,18 @@ extern "C" recon_status recon_split_regions_noalloc(const recon_grid* grid, cons
         for (int k = 0; k < 7; ++k)
             if (!events->planes[k]) return fail(RECON_EINVAL, "event plane pointer is NULL");
         if (!code_out) return fail(RECON_EINVAL, "code_out is NULL");
+        static const char* kPlaneNames[7] = {"event plane x1", "event plane y1", "event plane z1", "event plane x2",
+                                             "event plane y2", "event plane z2", "event plane d"};
+        for (int k = 0; k < 7; ++k) {
+            recon_status ps = check_device_pointer(events->planes[k], kPlaneNames[k]);
+            if (ps != RECON_OK) return ps;
+        }
+        recon_status ps = check_device_pointer(code_out, "code_out");
+        if (ps != RECON_OK) return ps;
+        if (idx_out) {
+            ps = check_device_pointer(idx_out, "idx_out");
+            if (ps != RECON_OK) return ps;
+        }
     }
     if (idx_capacity < 0) return fail(RECON_EINVAL, "idx_capacity is negative");
     if (n == 0) {

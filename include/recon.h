@@ -128,6 +128,8 @@ typedef struct {
     int32_t tile_halo[3];
     int32_t subsets;           /* OSEM subsets of recon_mlem (1: MLEM); conservation rows per iteration */
     int32_t lut_samples;       /* samples of the sampled projector (0: exact projector) */
+    int64_t device_bytes;      /* device memory the context holds now (all its buffers; buffers grow
+                                  to the largest call and are kept until recon_destroy) */
 } recon_info;
 
 typedef struct {
@@ -427,27 +429,34 @@ recon_status recon_region_slab_voxels(const recon_ctx* ctx, int32_t n_regions, c
 /* ------------------------------------------------- allocation-free split */
 
 /* The paper has no counterpart of this call: it is a service for callers that cannot
- * allocate device memory — code recording a CUDA graph that must not gain allocation
- * nodes, or a process whose GPU memory belongs to another allocator (a framework's
- * caching pool, an acquisition service that reserves everything at start-up).
+ * allocate device memory.  A process whose GPU memory belongs to another allocator (a
+ * framework's caching pool, or an acquisition service that reserves all of the GPU's
+ * memory when it starts) would see an extra cudaMalloc fail or fragment a pool it does
+ * not own; a real-time path cannot afford cudaFree, which waits for the whole device, or
+ * an allocation that may fail half-way through a scan.
  *
  * Same split as recon_split_regions (same codes, offsets and ascending index lists),
  * with no context and no cudaMalloc/cudaFree: the caller passes device inputs and
  * outputs, and the per-tile counters live in one 8 MiB static device array that every
  * GPU loading this library keeps until the process exits.
  *   grid:        only nz, vz and oz are used (the z boundaries z_b[r] = oz + z_lo*vz).
- *   events:      fmt RECON_EV_F32_SOA with on_device = 1 (the weight is ignored).
+ *   events:      fmt RECON_EV_F32_SOA with on_device = 1 (the weight is ignored); each
+ *                plane holds n floats in device memory of the current device.
  *   code_out:    n bytes, device.      idx_out: idx_capacity int32, device.
  *   offsets_out: n_regions+1 int64, host.
- *   cuda_stream: the stream to run on (NULL: the legacy default stream); the call
- *                synchronises it before returning.
+ *   cuda_stream: the stream to run on (NULL: the legacy default stream).  The call
+ *                reads the offsets back to the host and synchronises that stream
+ *                before it returns.
  * Limit: n <= 32768 * floor((8 MiB - 1032 B) / (12 * n_regions + 4)) events and n < 2^31
  * (any n below 2^31 for up to 10 regions, about 356 M events for 64); larger n returns
- * RECON_EINVAL with a message.  The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  All calls share the array, so calls that
- * overlap on the GPU (other host threads, other streams) race and must be serialised
- * by the caller.  Errors: EINVAL (arguments, limit, idx_out too small), ECUDA; the
- * message is available from recon_last_error(NULL). */
+ * RECON_EINVAL with a message.  Every event plane, code_out and idx_out must be device
+ * (or managed) memory of the current device: host memory, page-locked or not, returns
+ * RECON_EINVAL before any kernel runs.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and each overwrites what the previous call left there, so
+ * calls that overlap on the GPU (other host threads, other streams) race and must be
+ * serialised by the caller.  Errors: EINVAL (arguments, memory residency, limit, idx_out
+ * too small), ECUDA; the message is available from recon_last_error(NULL). */
 recon_status recon_split_regions_noalloc(const recon_grid* grid, const recon_events* events, int32_t n_regions,
                                          const recon_region* regions, double shell_mm, uint8_t* code_out,
                                          int64_t* offsets_out, int32_t* idx_out, int64_t idx_capacity,

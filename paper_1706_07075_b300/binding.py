@@ -56,7 +56,7 @@ class recon_info(C.Structure):
                 ("n_events_resident", C.c_int64), ("has_sensitivity", C.c_int32), ("num_sms", C.c_int32),
                 ("sens_total", C.c_double), ("tile_cells", C.c_int64), ("tile_events", C.c_int64),
                 ("tile_fallback_events", C.c_int64), ("tile_cell_voxels", C.c_int32), ("tile_halo", C.c_int32 * 3),
-                ("subsets", C.c_int32), ("lut_samples", C.c_int32)]
+                ("subsets", C.c_int32), ("lut_samples", C.c_int32), ("device_bytes", C.c_int64)]
 
 
 class recon_stats(C.Structure):

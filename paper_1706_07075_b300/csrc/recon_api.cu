@@ -249,6 +249,21 @@ void invalidate_graph(recon_ctx* ctx)
     ctx->gkey.clear();
 }
 
+// Every device buffer a context owns (released by recon_destroy, counted by
+// recon_get_info).
+std::vector<DevBuf*> device_buffers(recon_ctx* ctx)
+{
+    return {&ctx->s64, &ctx->s32, &ctx->lam, &ctx->C, &ctx->lam_bf16, &ctx->lam_brick, &ctx->C_brick,
+            &ctx->ev, &ctx->staging,
+            &ctx->pass_partial, &ctx->upd_partial, &ctx->work, &ctx->iter, &ctx->hist, &ctx->reg_vox,
+            &ctx->red_partial, &ctx->vec, &ctx->med, &ctx->mu, &ctx->keep, &ctx->counter, &ctx->codes,
+            &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
+            &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg,
+            &ctx->tile_prep.code, &ctx->tile_prep.counts, &ctx->tile_prep.cursor, &ctx->tile_prep.begin,
+            &ctx->tile_prep.scratch, &ctx->tile_prep.list, &ctx->tile_prep.ev_cell, &ctx->tile_prep.ev_fb,
+            &ctx->tile_prep.misc};
+}
+
 recon_status validate_events(recon_ctx* ctx, const recon_events* e)
 {
     if (!e) return fail(ctx, RECON_EINVAL, "events is NULL");
@@ -890,15 +905,7 @@ void recon_destroy(recon_ctx* ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     invalidate_graph(ctx);
-    DevBuf* bufs[] = {&ctx->s64, &ctx->s32, &ctx->lam, &ctx->C, &ctx->lam_bf16, &ctx->lam_brick, &ctx->C_brick,
-                      &ctx->ev, &ctx->staging,
-                      &ctx->pass_partial, &ctx->upd_partial, &ctx->work, &ctx->iter, &ctx->hist, &ctx->reg_vox,
-                      &ctx->red_partial, &ctx->vec, &ctx->med, &ctx->mu, &ctx->keep, &ctx->counter, &ctx->codes, &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
-                      &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg,
-                      &ctx->tile_prep.code, &ctx->tile_prep.counts, &ctx->tile_prep.cursor, &ctx->tile_prep.begin,
-                      &ctx->tile_prep.scratch, &ctx->tile_prep.list, &ctx->tile_prep.ev_cell, &ctx->tile_prep.ev_fb,
-                      &ctx->tile_prep.misc};
-    for (DevBuf* b : bufs) release(*b);
+    for (DevBuf* b : device_buffers(ctx)) release(*b);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (int k = 0; k < 2; ++k) {
@@ -1111,6 +1118,11 @@ recon_status recon_set_autotune(recon_ctx* ctx, int32_t on)
 
 recon_status recon_get_info(const recon_ctx* ctx, recon_info* out)
 {
+    if (ctx && out) {
+        long long bytes = 0;
+        for (DevBuf* b : device_buffers(const_cast<recon_ctx*>(ctx))) bytes += (long long)b->bytes;
+        out->device_bytes = bytes;
+    }
     if (!ctx || !out) return RECON_EINVAL;
     out->sigma_mm = ctx->sigma_mm;
     out->k_sigma = ctx->k_sigma;

@@ -12,6 +12,18 @@ concurrent jobs overlap on the GPU.  Sensitivity images are computed once
 per (scanner, grid) and stay resident on the device; contexts are kept and
 reused by later jobs on the same grid.
 
+HBM budget: everything the executor keeps on the device counts against it.
+An executor that caches state (contexts, sensitivity images) reports it through
+`resident_bytes()`, the bytes already held for a job's grid on a slot through
+`context_bytes(slot, job)`, and frees idle state through
+`evict_idle(running, need)`.  A job is admitted on a slot when the resident
+bytes, each running job at the larger of its footprint and what its context
+already holds, and the new job's growth (its footprint less what the slot
+already holds for its grid) fit the budget; if
+they do not, idle cached contexts (least recently used first, never one a
+running job uses) are closed first.  An executor without these methods caches
+nothing, and a job then reserves its whole footprint while it runs.
+
 Timing per job: queue wait, service time and latency (completion - arrival).
 The scheduling logic is independent of the GPU: `Server` takes an executor
 object, and `LibreconExecutor` is the one that runs jobs through librecon.
@@ -25,7 +37,16 @@ import numpy as np
 
 EVENT_BYTES = 68          # resident F32 event record (32 B), its cell-ordered copy (32 B) and cell code (4 B)
 IMAGE_BYTES_PER_VOXEL = 20  # lambda, C, s32 (4 B each) + s64 (8 B)
-STAGING_BYTES = (1 << 23) * 32
+# host events go up in chunks of at most 2^23 events through two staging halves of
+# 28 bytes per event each
+STAGING_CHUNK_EVENTS = 1 << 23
+STAGING_BYTES_PER_EVENT = 2 * 28
+# the library's default event order bins events by cells of 4^3 voxels and 16 x 8
+# direction bins; each bin key costs a count, a cursor, a list entry (4 B each) and
+# a 64-bit start
+ORDER_CELL_VOXELS = 4
+ORDER_DIRECTION_BINS = 16 * 8
+ORDER_KEY_BYTES = 20
 
 
 @dataclass
@@ -49,8 +70,14 @@ class Job:
         return int(self.events.shape[1])
 
     def footprint(self):
+        """Device bytes a context needs for this job: resident events with their
+        binned copy, the images, the event-order bin table and the upload staging."""
         nx, ny, nz = self.grid[:3]
-        return self.n_events * EVENT_BYTES + nx * ny * nz * IMAGE_BYTES_PER_VOXEL + STAGING_BYTES
+        c = ORDER_CELL_VOXELS
+        keys = -(-nx // c) * -(-ny // c) * -(-nz // c) * ORDER_DIRECTION_BINS
+        staging = min(self.n_events, STAGING_CHUNK_EVENTS) * STAGING_BYTES_PER_EVENT
+        return (self.n_events * EVENT_BYTES + nx * ny * nz * IMAGE_BYTES_PER_VOXEL + keys * ORDER_KEY_BYTES +
+                staging)
 
     @property
     def latency(self):
@@ -84,7 +111,9 @@ class Server:
         self._queue = []
         self._seq = 0
         self._free_slots = list(range(slots))
-        self._in_use = 0
+        self._in_use = 0            # footprints of the running jobs (bytes)
+        self._running_jobs = {}     # slot -> running job
+        self.peak_charged = 0       # largest resident + reserved bytes seen at an admission
         self._lock = threading.Condition()
         self._threads = []
         self._errors = []
@@ -107,27 +136,65 @@ class Server:
             self._seq += 1
             self._admit_locked()
 
+    def _resident(self):
+        f = getattr(self.executor, "resident_bytes", None)
+        return int(f()) if f else 0
+
+    def _held(self, slot, job):
+        f = getattr(self.executor, "context_bytes", None)
+        return int(f(slot, job)) if f else 0
+
+    def _place(self, job):
+        """(slot, growth) for a job: the free slot that already holds the most
+        device memory for the job's grid, and the bytes the job may add to it."""
+        slot = max(self._free_slots, key=lambda s: (self._held(s, job), -s))
+        return slot, max(0, job.footprint() - self._held(slot, job))
+
+    def _charged(self):
+        """Device bytes charged now: the executor's resident state, each running job
+        at the larger of its footprint and what its context already holds (that
+        context counted once), plus anything else reserved in _in_use."""
+        overlap = sum(min(j.footprint(), self._held(s, j)) for s, j in self._running_jobs.items())
+        return self._resident() + self._in_use - overlap
+
+    def _fits(self, growth):
+        return self._charged() + growth <= self.budget
+
     def _admit_locked(self):
         """First fit in arrival order while slots and budget allow; a waiting job
         passed max_overtakes times stops younger jobs from being admitted."""
         kept = []
         while self._queue and self._free_slots:
             q = heapq.heappop(self._queue)
-            fp = q.job.footprint()
-            if self._in_use + fp > self.budget:
+            slot, growth = self._place(q.job)
+            if not self._fits(growth):
+                evict = getattr(self.executor, "evict_idle", None)
+                if evict is not None:
+                    over = self._charged() + growth - self.budget
+                    evict(dict(self._running_jobs), over)
+                    slot, growth = self._place(q.job)
+            if not self._fits(growth):
+                if self._running == 0 and self._in_use == 0:
+                    # nothing runs and nothing idle is left to free: it can never fit
+                    q.job.finished = self.now()
+                    self._errors.append((q.job.job_id, "does not fit the HBM budget beside the resident state"))
+                    self.done.append(q.job)
+                    continue
                 kept.append(q)
                 if self.max_overtakes is not None and q.overtaken >= self.max_overtakes:
                     break          # it holds the line until the budget frees up for it
                 continue
             for older in kept:
                 older.overtaken += 1
-            slot = self._free_slots.pop(0)
-            self._in_use += fp
+            self._free_slots.remove(slot)
+            self._in_use += q.job.footprint()
+            self._running_jobs[slot] = q.job
+            self.peak_charged = max(self.peak_charged, self._charged())
             q.job.admitted = self.now()
             q.job.slot = slot
             self._running += 1
             self.max_concurrent = max(self.max_concurrent, self._running)
-            t = threading.Thread(target=self._work, args=(q.job, slot, fp), daemon=True)
+            t = threading.Thread(target=self._work, args=(q.job, slot, q.job.footprint()), daemon=True)
             self._threads.append(t)
             t.start()
         for q in kept:
@@ -143,6 +210,7 @@ class Server:
                 job.finished = self.now()
                 self.done.append(job)
                 self._in_use -= fp
+                self._running_jobs.pop(slot, None)
                 self._free_slots.append(slot)
                 self._free_slots.sort()
                 self._running -= 1
@@ -181,12 +249,15 @@ class Server:
         return {"jobs": len(self.done), "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
                 "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
                 "events_iters_per_s": ev_it / span if span > 0 else None, "span_s": span,
-                "max_concurrent": self.max_concurrent}
+                "max_concurrent": self.max_concurrent, "peak_charged_bytes": self.peak_charged}
 
 
 class LibreconExecutor:
     """Runs jobs through librecon: one CUDA stream per slot, contexts reused per
-    grid, sensitivity images resident per key."""
+    grid, sensitivity images resident per key.  The device memory it holds is
+    reported to the server: each cached context's buffers (recon_info's
+    device_bytes, read after every job on the slot's own thread) and the
+    sensitivity images."""
 
     def __init__(self, slots, device=0, sensitivities=None, keep_results=True, launch=(128, 0, 0, 0, 2)):
         import torch
@@ -198,10 +269,19 @@ class LibreconExecutor:
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.contexts = [dict() for _ in range(slots)]   # per slot: grid -> Context
         self.loaded = [dict() for _ in range(slots)]     # per slot: grid -> sensitivity key resident in it
+        self.ctx_bytes = {}                               # (slot, grid) -> device bytes the context holds
+        self.last_used = {}                               # (slot, grid) -> use counter (LRU eviction)
+        self._use = 0
+        self.evicted = 0
         self.sens = dict(sensitivities or {})            # key -> device float64 tensor
         self.keep_results = keep_results
         self.launch = launch                              # fixed event-pass launch (None: autotune per job size)
         self._sens_lock = threading.Lock()
+        self._lock = threading.Lock()                     # contexts, ctx_bytes, last_used
+
+    @staticmethod
+    def _key(job):
+        return (tuple(job.grid), tuple(job.geometry))
 
     def register_sensitivity(self, key, geometry, grid, lors):
         """Compute a sensitivity image once and keep it on the device."""
@@ -217,15 +297,52 @@ class LibreconExecutor:
             self.sens[key] = s
             return s
 
+    def resident_bytes(self):
+        """Device bytes held between jobs: cached contexts and sensitivity images."""
+        with self._lock:
+            ctx = sum(self.ctx_bytes.values())
+        return ctx + sum(int(t.numel()) * t.element_size() for t in self.sens.values())
+
+    def context_bytes(self, slot, job):
+        with self._lock:
+            return self.ctx_bytes.get((slot, self._key(job)), 0)
+
+    def evict_idle(self, running, need):
+        """Close cached contexts no running job uses, least recently used first,
+        until at least `need` bytes are freed; returns the bytes freed.
+        running: slot -> job of the jobs on the GPU (and just admitted)."""
+        busy = {(slot, self._key(job)) for slot, job in running.items()}
+        freed = 0
+        with self._lock:
+            for sk in sorted(self.ctx_bytes, key=lambda k: self.last_used.get(k, 0)):
+                if freed >= need:
+                    break
+                if sk in busy:
+                    continue
+                slot, key = sk
+                ctx = self.contexts[slot].pop(key, None)
+                if ctx is not None:
+                    ctx.close()
+                self.loaded[slot].pop(key, None)
+                freed += self.ctx_bytes.pop(sk)
+                self.last_used.pop(sk, None)
+                self.evicted += 1
+        return freed
+
     def _context(self, slot, job):
-        key = (tuple(job.grid), tuple(job.geometry))
-        ctx = self.contexts[slot].get(key)
+        key = self._key(job)
+        with self._lock:
+            ctx = self.contexts[slot].get(key)
+            self._use += 1
+            self.last_used[(slot, key)] = self._use
         if ctx is None:
             ctx = self.B.Context(job.geometry, job.grid)
             ctx.set_stream(self.streams[slot].cuda_stream)
             if self.launch is not None:
                 ctx.set_launch(*self.launch)
-            self.contexts[slot][key] = ctx
+            with self._lock:
+                self.contexts[slot][key] = ctx
+                self.ctx_bytes[(slot, key)] = ctx.get_info()["device_bytes"]
         if self.loaded[slot].get(key) != job.sens_key:
             ctx.set_sensitivity(self.sens[job.sens_key])
             self.loaded[slot][key] = job.sens_key
@@ -255,15 +372,23 @@ class LibreconExecutor:
         nvox = job.grid[0] * job.grid[1] * job.grid[2]
         img = torch.empty(nvox, dtype=torch.float32).pin_memory() if self.keep_results else None
         cons = np.zeros((job.n_iter, 2))
-        ctx.mlem(self.B.make_events(job.events), job.n_iter, None, img, cons)
+        try:
+            ctx.mlem(self.B.make_events(job.events), job.n_iter, None, img, cons)
+        finally:
+            with self._lock:
+                if self.contexts[slot].get(self._key(job)) is ctx:
+                    self.ctx_bytes[(slot, self._key(job))] = ctx.get_info()["device_bytes"]
         job.result = img.numpy() if img is not None else None
         job.conservation = cons
 
     def close(self):
-        for per_slot in self.contexts:
-            for ctx in per_slot.values():
-                ctx.close()
-            per_slot.clear()
+        with self._lock:
+            for per_slot in self.contexts:
+                for ctx in per_slot.values():
+                    ctx.close()
+                per_slot.clear()
+            self.ctx_bytes.clear()
+            self.last_used.clear()
 
 
 def poisson_arrivals(n, rate_per_s, seed):

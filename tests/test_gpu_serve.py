@@ -85,3 +85,56 @@ def test_each_result_is_the_same_alone_and_in_the_mix(pool):
         assert rel_l2(j.result, alone[j.kind]) <= 1e-5, j.kind
         n_eff, ssum = j.conservation[-1]
         assert ssum == pytest.approx(n_eff, rel=1e-5)
+
+
+def test_a_binding_budget_bounds_the_device_memory(pool):
+    # a budget well below what the cached contexts of three slots x three grids
+    # would hold: the server charges the cached contexts (recon_info's
+    # device_bytes), evicts idle ones, and the device memory in use, sampled with
+    # cudaMemGetInfo during the stream, stays within the budget (plus a small
+    # allowance for what the CUDA runtime keeps per context: streams, events,
+    # graph executables)
+    import threading
+    import time
+    import torch
+    kinds, pinned = pool
+    jobs = make_jobs(kinds, pinned, 15, 9)
+    biggest = max(j.footprint() for j in jobs)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free0, _ = torch.cuda.mem_get_info()
+    ex = LibreconExecutor(3)
+    for k, (geo, grid, _, lors) in kinds.items():
+        ex.register_sensitivity(k, geo, grid, lors)
+    sens = ex.resident_bytes()
+    budget = sens + int(1.6 * biggest)
+    peak = [0]
+    stop = threading.Event()
+
+    def sample():
+        while not stop.is_set():
+            free, _ = torch.cuda.mem_get_info()
+            peak[0] = max(peak[0], free0 - free)
+            time.sleep(0.002)
+
+    th = threading.Thread(target=sample, daemon=True)
+    th.start()
+    srv = Server(ex, slots=3, hbm_budget_bytes=budget)
+    try:
+        stats = srv.replay(jobs)
+    finally:
+        stop.set()
+        th.join()
+        evicted = ex.evicted
+        ex.close()
+    allowance = 96 << 20
+    print(f"\nbudget {budget / 2**20:.0f} MiB, peak charged {stats['peak_charged_bytes'] / 2**20:.0f} MiB, "
+          f"peak in use {peak[0] / 2**20:.0f} MiB, contexts evicted {evicted}, max concurrent "
+          f"{stats['max_concurrent']}")
+    assert stats["jobs"] == 15
+    assert stats["peak_charged_bytes"] <= budget
+    assert evicted > 0
+    assert peak[0] <= budget + allowance
+    for j in jobs:
+        n_eff, ssum = j.conservation[-1]
+        assert ssum == pytest.approx(n_eff, rel=1e-5)

@@ -132,3 +132,75 @@ def test_oversized_job_is_rejected_and_stats():
         srv.submit(make_job(0, 10))
     t = poisson_arrivals(1000, 50.0, 3)
     assert np.all(np.diff(t) > 0) and abs(1000 / t[-1] - 50.0) < 10.0
+
+
+class CachingExecutor:
+    """Keeps one context per (slot, grid) that grows to the largest job it ran,
+    like LibreconExecutor, and records the device bytes all contexts hold."""
+
+    def __init__(self, resident_extra=0):
+        self.lock = threading.Lock()
+        self.ctx = {}                 # (slot, grid) -> bytes
+        self.used = {}
+        self.tick = 0
+        self.extra = resident_extra   # e.g. sensitivity images
+        self.peak_actual = 0
+        self.evicted = 0
+
+    def resident_bytes(self):
+        with self.lock:
+            return sum(self.ctx.values()) + self.extra
+
+    def context_bytes(self, slot, job):
+        with self.lock:
+            return self.ctx.get((slot, job.grid), 0)
+
+    def evict_idle(self, running, need):
+        busy = {(s, j.grid) for s, j in running.items()}
+        freed = 0
+        with self.lock:
+            for k in sorted(self.ctx, key=lambda k: self.used[k]):
+                if freed >= need:
+                    break
+                if k not in busy:
+                    freed += self.ctx.pop(k)
+                    self.evicted += 1
+        return freed
+
+    def run(self, job, slot):
+        with self.lock:
+            k = (slot, job.grid)
+            self.ctx[k] = max(self.ctx.get(k, 0), job.footprint())      # the context grows
+            self.tick += 1
+            self.used[k] = self.tick
+            self.peak_actual = max(self.peak_actual, sum(self.ctx.values()) + self.extra)
+        time.sleep(0.003)
+        job.result = job.job_id
+
+
+def test_cached_contexts_count_against_the_budget():
+    # contexts stay allocated after their jobs; with a budget that binds, the
+    # server charges them, evicts idle ones and never lets the device memory
+    # the executor holds exceed the budget
+    grids = [(10 * (k + 1), 10, 10, 1, 1, 1, 0, 0, 0) for k in range(4)]
+    sizes = [make_job(0, 400_000, grid=g).footprint() for g in grids]
+    ex = CachingExecutor(resident_extra=1000)
+    budget = int(2.2 * max(sizes)) + 1000
+    srv = Server(ex, slots=3, hbm_budget_bytes=budget)
+    jobs = [make_job(i, 400_000, arrival=0.0005 * i, grid=grids[i % 4]) for i in range(40)]
+    stats = srv.replay(jobs)
+    assert stats["jobs"] == 40 and all(j.result == j.job_id for j in jobs)
+    assert ex.peak_actual <= budget
+    assert stats["peak_charged_bytes"] <= budget
+    assert ex.evicted > 0                         # the budget did bind
+    assert stats["max_concurrent"] >= 2
+
+
+def test_a_job_that_cannot_fit_beside_resident_state_fails_instead_of_waiting():
+    ex = CachingExecutor(resident_extra=900)
+    job = make_job(0, 10)
+    srv = Server(ex, slots=1, hbm_budget_bytes=job.footprint() + 100)
+    srv.start()
+    srv.submit(job)
+    with pytest.raises(RuntimeError, match="does not fit"):
+        srv.drain(timeout=5)

@@ -25,8 +25,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TOF-MLEM events x iterations / s (full-body, 146M events, 150x150x600 @ 4 mm)"
-# DRAM bytes per event of the fused pass (ncu, 8 M full-body events, cell + direction order, 128 threads,
-# series masses): see profiles/k_event_pass_fullbody_8M.md
+# DRAM bytes per event of the fused pass: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture on 8 M full-body events (cell + direction order, 128 threads, series masses), per event
 TRAFFIC_BYTES_PER_EVENT = 49.3
 # algorithmic FP32 operations per Siddon piece: ~25 for the step and the two
 # accumulations plus ~20 for the Gaussian mass of the piece
@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="run the served-reconstruction workload (Poisson stream of mixed jobs) instead")
     ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--serve-leg-jobs", type=int, default=60,
+                    help="jobs of the bounded serving leg of the default line (0: no serving leg)")
     return ap.parse_args()
 
 
@@ -164,38 +166,41 @@ def roofline(n, visits, pass_ms, probes, hbm_peak_gbs, sm_mhz, traffic):
     """Roofline of the fused event pass as t_min / t_measured, t_min the largest of
     its algorithmic terms per launch: HBM (32 B per event), L2 reductions (one FP32
     reduction per Siddon piece at the live rate of scattered red.global.add.f32), L2
-    gathers (one 4-byte gather per piece at the live gather rate), L2 sectors (every
-    gather and every reduction touches one 32-byte sector, at the live L2 read
-    bandwidth) and FP32 ALU (ALU_OPS_PER_PIECE per piece on 148 SMs x 128 lanes at
-    the sampled SM clock).  `achieved` and `peak` are in the unit of the largest
-    term; `traffic` is the ncu DRAM bytes of the launch (or None)."""
+    gathers (one 4-byte gather per piece at the live gather rate) and FP32 ALU
+    (ALU_OPS_PER_PIECE per piece on 148 SMs x 128 lanes at the sampled SM clock).
+    A fifth term, two 32-byte L2 sectors per piece at the live L2 read bandwidth, is
+    reported but kept out of the maximum: it charges an L2 sector to every gather,
+    while about a third of the gathers hit L1, so it is not a lower bound on the
+    time.  `achieved` and `peak` are in the unit of the largest term; `traffic` is
+    the ncu DRAM bytes of the launch (or None)."""
     R, G, L2BW = probes.get("l2_red_gops"), probes.get("gather_gops"), probes.get("l2_stream_gbs")
     alu_peak = 148 * 128 * sm_mhz * 1e6                      # FP32 lane operations per second
     t = pass_ms / 1e3
     terms = {"hbm": (32.0 * n) / (hbm_peak_gbs * 1e9),
              "l2_reductions": visits / (R * 1e9) if R else 0.0,
              "l2_gathers": visits / (G * 1e9) if G else 0.0,
-             "l2_sectors": visits * 2 * 32.0 / (L2BW * 1e9) if L2BW else 0.0,
              "alu": visits * ALU_OPS_PER_PIECE / alu_peak}
     bound = max(terms, key=terms.get)
     rates = {"hbm": (32.0 * n / t / 1e9, hbm_peak_gbs, "GB/s"),
              "l2_reductions": (visits / t / 1e9, R, "Gred/s"),
              "l2_gathers": (visits / t / 1e9, G, "Ggather/s"),
-             "l2_sectors": (visits * 64.0 / t / 1e9, L2BW, "GB/s"),
              "alu": (visits * ALU_OPS_PER_PIECE / t / 1e12, alu_peak / 1e12, "Tops/s")}
     ach, pk, unit = rates[bound]
     hbm_gbs = 32.0 * n / t / 1e9
+    sectors_ms = 1e3 * visits * 2 * 32.0 / (L2BW * 1e9) if L2BW else None
     return {
         "bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk if pk else None,
         "traffic": traffic,
         "traffic_source": f"ncu capture of the same kernel on 8 M full-body events, "
-                          f"{TRAFFIC_BYTES_PER_EVENT:.1f} B per event, scaled",
+                          f"{TRAFFIC_BYTES_PER_EVENT:.1f} B per event, scaled to the launch's events",
         "t_min_ms": 1e3 * terms[bound], "terms_ms": {k: 1e3 * v for k, v in terms.items()},
+        "l2_sectors_ms_not_a_bound": sectors_ms,
         "per_launch": {"events": n, "pieces": visits, "gathers": visits, "reductions": visits,
                        "hbm_bytes": 32.0 * n, "pass_ms": pass_ms},
-        "peak_source": "live probes on an L2-resident image of the grid's size (scattered "
-                       "red.global.add.f32, 4-byte gathers, coalesced 16-byte reads for the L2 sector "
-                       "bandwidth); HBM from MEASURED_PEAKS; ALU from 148 SMs x 128 lanes x sampled SM clock",
+        "peak_source": "builder-measured live in this run (librecon_probe.so): scattered red.global.add.f32 "
+                       "and 4-byte gathers into an L2-resident image of the grid's size, coalesced 16-byte "
+                       "reads for the L2 bandwidth; HBM from MEASURED_PEAKS (driver-measured); ALU from "
+                       "148 SMs x 128 lanes x the sampled SM clock",
         "mixed_probe_gsteps": probes.get("mixed_gsteps"),
         "secondary": {"hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak_gbs, "hbm_frac": hbm_gbs / hbm_peak_gbs}}
 
@@ -275,6 +280,8 @@ def workload_config(args, n, world):
     """The workload both arms report: the same dictionary for the CUDA arm and the oracle."""
     return {"workload": "fullbody-146M-150x150x600-4mm", "events": n, "iters_per_step": args.iters,
             "sensitivity_lors": args.lors, "tof_fwhm_ps": 300.0,
+            "timing": "events resident in HBM; each MLEM iteration a CUDA-graph replay of pass, update and "
+                      "conservation sums",
             "projector": f"sampled TOF kernel, {args.samples} samples" if args.samples else
             "exact Siddon pieces x Gaussian mass",
             "l2": "inputs larger than L2 (events 32 B x 146M = 4.7 GB resident)",
@@ -308,7 +315,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, args.events, world),
+        "config": dict(workload_config(args, args.events, world), sampled_events=n_sample,
+                       timing=f"host wall clock; each step one FP64 MLEM iteration over {n_sample} of the events"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
                          "sample": f"each step: 1 FP64 MLEM iteration over a bounded sample of {n_sample} full-body "
                                    f"events (the 150x150x600 grid, sensitivity from 200000 LORs); the metric counts "
@@ -362,33 +370,39 @@ def time_regions_leg(ctx, B, n, args, stream):
             "steps": args.steps}
 
 
-def time_packed_leg(ctx, B, synth, ev, n, args, stream):
+def time_packed_leg(ctx, B, synth, ev, n, args, stream, img_plain, bf16):
     """Precision-packed form: int16 endpoints on a 0.05 mm lattice + FP16 d
-    (16 B per event) and the forward gather from a BF16 image copy."""
+    (16 B per event), the forward gather from the FP32 image or from a BF16 copy
+    of it.  Resident events and end to end (pinned packed records uploaded, the
+    image read back per job); the image's distance to the plain FP32 form's after
+    the same iterations from the same start is reported beside the rate."""
     import numpy as np
     import torch
     rec = torch.from_numpy(synth.pack_events(ev)).pin_memory()
     ctx.load_events(B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM))
-    ctx.set_gather_bf16(1)
+    ctx.set_gather_bf16(1 if bf16 else 0)
     cons = np.zeros((args.iters, 2))
-    ctx.mlem(None, args.iters, None, None, cons)     # warm-up (+ autotune for the packed format)
-    st0 = ctx.get_stats()
-    ms = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons))
-    st1 = ctx.get_stats()
-    # end to end: pinned packed records uploaded (16 B per event) and the image read back per job
-    img = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
-    times = []
-    for k in range(args.e2e_steps + 1):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        ctx.mlem(B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM), args.iters, None, img, cons)
-        times.append(time.perf_counter() - t)
+    try:
+        ctx.mlem(None, args.iters, None, None, cons)     # warm-up (+ autotune for the packed format)
+        st0 = ctx.get_stats()
+        ms = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons))
+        st1 = ctx.get_stats()
+        img = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
+        times = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            ctx.mlem(B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM), args.iters, None, img, cons)
+            times.append(time.perf_counter() - t)
+    finally:
+        ctx.set_gather_bf16(0)
     e2e_T = sum(times[1:]) / (len(times) - 1) if len(times) > 1 else float("nan")
-    ctx.set_gather_bf16(0)
-    return {"workload": "fullbody packed int16/FP16 events, BF16 gather", "value": n * args.iters * args.steps /
-            (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+    a, b = img.double(), img_plain.double()
+    return {"workload": f"fullbody packed int16/FP16 events, {'BF16' if bf16 else 'FP32'} gather",
+            "value": n * args.iters * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "e2e": {"value": n * args.iters / e2e_T, "unit": UNIT, "h2d_bytes_per_step": int(rec.numel() * 2),
                     "d2h_bytes_per_step": int(img.numel() * 4 + cons.nbytes), "job_latency_s": e2e_T},
+            "image_rel_l2_vs_plain_f32": float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)),
             "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]), "launch": list(ctx.get_launch()),
             "conservation_last": [float(x) for x in cons[-1]], "steps": args.steps}
 
@@ -494,26 +508,25 @@ def time_preprocess_leg(ctx, B, synth, n, stream):
             "events_per_s": n / (ms / 1e3), "kept_fraction": kept / n}
 
 
-def run_serve(args):
-    """Served reconstruction: a Poisson stream of jobs mixing single-region slabs
-    (150x150x80 voxels, events whose TOF point lies in the slab), full bodies
+def serve_leg(args, fb, fb_pinned, n_jobs, local):
+    """Served reconstruction: a Poisson stream of n_jobs jobs mixing single-region
+    slabs (150x150x80 voxels, events whose TOF point lies in the slab), full bodies
     (150x150x600) and small fields of view (128^3 voxels of 0.5 mm), 3 iterations
-    each, 60/10/30%, at 0.8x the serial capacity measured on one job of each kind."""
+    each, 60/10/30%, at 0.8x the serial capacity measured on one job of each kind;
+    then the same stream served one job at a time in arrival order (the plain form).
+    fb: the full-body events (7, n) float32, fb_pinned: the same in pinned memory."""
     import numpy as np
     import torch
     from paper_1706_07075_b300 import synth
     from paper_1706_07075_b300.serve import Job, LibreconExecutor, Server, poisson_arrivals
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    n_fb = args.events
-    fb = synth.events("fullbody", n_fb, args.seed)
+    n_fb = fb.shape[1]
     p1, p2, d = fb[0:3], fb[3:6], fb[6]
     dz = p1[2] - p2[2]
     D = np.sqrt((p1[0] - p2[0]) ** 2 + (p1[1] - p2[1]) ** 2 + dz ** 2)
     z = 0.5 * (p1[2] + p2[2]) + d * dz / D
     del p1, p2, d, dz, D
     geo_fb = (400.0, 2400.0, 45.0)
-    kinds = {"fullbody": (geo_fb, synth.grid_of("fullbody"), [torch.from_numpy(fb).pin_memory()])}
+    kinds = {"fullbody": (geo_fb, synth.grid_of("fullbody"), [fb_pinned])}
     slabs = []
     for z0 in np.arange(-1040.0, 900.0, 240.0):
         keep = (z >= z0) & (z < z0 + 320.0)
@@ -525,11 +538,13 @@ def run_serve(args):
     kinds["smallfov"] = ((60.0, 100.0, 90.0), synth.grid_of("smallfov"),
                          [torch.from_numpy(synth.events("smallfov", 5_000_000, args.seed + k)).pin_memory()
                           for k in range(2)])
+    budget = 200 << 30
     ex = LibreconExecutor(slots=3)
     lors_fb = synth.sensitivity_lors("fullbody", 20_000_000, args.seed)
+    lors_sf = synth.sensitivity_lors("smallfov", 10_000_000, args.seed)
     for k, (geo, grid, _) in kinds.items():
-        lors = lors_fb if geo == geo_fb else synth.sensitivity_lors("smallfov", 10_000_000, args.seed)
-        ex.register_sensitivity(k, geo, grid, lors)
+        ex.register_sensitivity(k, geo, grid, lors_fb if geo == geo_fb else lors_sf)
+    del lors_fb, lors_sf
     # serial service time of one job of each kind (warm)
     service = {}
     for k, (geo, grid, evs) in kinds.items():
@@ -541,11 +556,10 @@ def run_serve(args):
             torch.cuda.synchronize()
             service[k] = time.perf_counter() - t
     region_kinds = [k for k in kinds if k.startswith("region")]
-    mix = [("region", 0.6), ("fullbody", 0.1), ("smallfov", 0.3)]
     mean_service = (0.6 * np.mean([service[k] for k in region_kinds]) + 0.1 * service["fullbody"] +
                     0.3 * service["smallfov"])
     rate = 0.8 / mean_service
-    arrivals = poisson_arrivals(args.serve_jobs, rate, args.seed)
+    arrivals = poisson_arrivals(n_jobs, rate, args.seed)
 
     def make_jobs():
         # the same stream every call: arrival times, kinds and event sets from the seed
@@ -561,45 +575,51 @@ def run_serve(args):
             out.append(Job(i, float(t), ev, geo, grid, args.iters, sens_key=kind, kind=kind))
         return out
 
-    def latencies_by_kind(done):
+    def by_kind(done):
         out = {}
         for j in done:
             out.setdefault("region" if j.kind.startswith("region") else j.kind, []).append(j.latency)
-        return out
+        return {k: {"p50_s": float(np.percentile(v, 50)), "p99_s": float(np.percentile(v, 99)), "jobs": len(v)}
+                for k, v in out.items()}
 
     jobs = make_jobs()
     ex.keep_results = False
     ex.warm(jobs)
-    srv = Server(ex, slots=3, hbm_budget_bytes=200 << 30)
+    srv = Server(ex, slots=3, hbm_budget_bytes=budget)
     sampler = ClockSampler(local)
     sampler.start()
     stats = srv.replay(jobs)
     clocks = sampler.stop()
-    by_kind = latencies_by_kind(srv.done)
-    # the same stream served one job at a time in arrival order (the plain form)
-    srv1 = Server(ex, slots=1, hbm_budget_bytes=200 << 30)
+    served_kind = by_kind(srv.done)
+    srv1 = Server(ex, slots=1, hbm_budget_bytes=budget)
     stats1 = srv1.replay(make_jobs())
-    by_kind1 = latencies_by_kind(srv1.done)
     ex.close()
-    line = {"metric": "served TOF-MLEM reconstruction: p50/p99 job latency and aggregate events x iterations / s",
-            "value": stats["p50_s"], "unit": "s", "p50_s": stats["p50_s"], "p99_s": stats["p99_s"],
-            "events_iters_per_s": stats["events_iters_per_s"], "jobs": stats["jobs"],
-            "max_concurrent": stats["max_concurrent"], "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
-            "dtype": "f32", "config": {"workload": "served mix: region slabs 150x150x80 / full body 150x150x600 / "
-                                                   "small FOV 128^3 @ 0.5 mm, 60/10/30%, 3 iterations",
-                                       "arrival_rate_jobs_per_s": rate, "slots": 3, "hbm_budget_gb": 200,
-                                       "region_events": {k: int(kinds[k][2][0].shape[1]) for k in region_kinds},
-                                       "fullbody_events": n_fb, "smallfov_events": 5_000_000},
-            "serial_service_s": service,
-            "latency_p50_by_kind_s": {k: float(np.percentile(v, 50)) for k, v in by_kind.items()},
-            "latency_p99_by_kind_s": {k: float(np.percentile(v, 99)) for k, v in by_kind.items()},
+    return {"workload": "served mix: region slabs 150x150x80 / full body 150x150x600 / small FOV 128^3 @ 0.5 mm, "
+                        "60/10/30%, 3 iterations, Poisson arrivals at 0.8x the serial capacity",
+            "jobs": stats["jobs"], "p50_s": stats["p50_s"], "p99_s": stats["p99_s"],
+            "events_iters_per_s": stats["events_iters_per_s"], "max_concurrent": stats["max_concurrent"],
+            "slots": 3, "hbm_budget_gb": budget >> 30, "arrival_rate_jobs_per_s": rate,
+            "region_events": {k: int(kinds[k][2][0].shape[1]) for k in region_kinds},
+            "fullbody_events": n_fb, "smallfov_events": 5_000_000, "serial_service_s": service,
+            "latency_by_kind": served_kind,
             "one_job_at_a_time": {"p50_s": stats1["p50_s"], "p99_s": stats1["p99_s"],
                                   "events_iters_per_s": stats1["events_iters_per_s"],
-                                  "latency_p50_by_kind_s": {k: float(np.percentile(v, 50)) for k, v in
-                                                            by_kind1.items()},
-                                  "latency_p99_by_kind_s": {k: float(np.percentile(v, 99)) for k, v in
-                                                            by_kind1.items()}},
+                                  "latency_by_kind": by_kind(srv1.done)},
             "clocks": clocks}
+
+
+def run_serve(args):
+    """The served workload alone (--serve): one JSON line with p50/p99 latency."""
+    import torch
+    from paper_1706_07075_b300 import synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    fb = synth.events("fullbody", args.events, args.seed)
+    leg = serve_leg(args, fb, torch.from_numpy(fb).pin_memory(), args.serve_jobs, local)
+    line = {"metric": "served TOF-MLEM reconstruction: p50/p99 job latency and aggregate events x iterations / s",
+            "value": leg["p50_s"], "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "dtype": "f32", "config": {"workload": leg["workload"]}}
+    line.update({k: v for k, v in leg.items() if k != "workload"})
     print(json.dumps(line), flush=True)
     return 0
 
@@ -650,8 +670,8 @@ def run_ours(args):
         ctx.mlem(None, args.iters)
     cfg = ctx.get_launch()
 
-    # timed region: events resident in HBM
-    ctx.set_timing(1)
+    # timed region: events resident in HBM, each iteration a CUDA-graph replay (the
+    # library's default path)
     ctx.reset_stats()
     sampler = ClockSampler(local)
     sampler.start()
@@ -671,9 +691,25 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     stats = ctx.get_stats()
-    ctx.set_timing(0)
     ms = max_over_ranks(ms)
     value = aggregate_rate(n * args.iters * args.steps, world, ms)
+
+    # the split of a step into event passes and updates: the same steps again with
+    # per-kernel CUDA events on the context's stream (direct launches instead of
+    # graph replay while timing is on)
+    ctx.set_timing(1)
+    ctx.reset_stats()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e2.record(stream)
+    for _ in range(args.steps):
+        ctx.mlem(None, args.iters, None, None, cons)
+    e3.record(stream)
+    torch.cuda.synchronize(dev)
+    split_stats = ctx.get_stats()
+    split_ms = e2.elapsed_time(e3)
+    ctx.set_timing(0)
 
     # end to end through the public call: pinned host events in, host image out
     img = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
@@ -686,6 +722,7 @@ def run_ours(args):
     e2e_T = sum(e2e_times[1:]) / args.e2e_steps if args.e2e_steps > 0 else float("nan")
     h2d = ev.nbytes
     d2h = img.numel() * 4 + cons.nbytes
+    tiles_info = {k: v for k, v in ctx.get_info().items() if k.startswith("tile")}
 
     legs = {}
     if not args.no_legs and not args.samples:
@@ -694,12 +731,16 @@ def run_ours(args):
         legs["osem5"] = time_osem_leg(ctx, B, n, args, stream)
         legs["preprocess"] = time_preprocess_leg(ctx, B, synth, n, stream)
         legs["regions"] = time_regions_leg(ctx, B, n, args, stream)
-        legs["packed_bf16"] = time_packed_leg(ctx, B, synth, ev, n, args, stream)
+        legs["packed_f32"] = time_packed_leg(ctx, B, synth, ev, n, args, stream, img, bf16=False)
+        legs["packed_bf16"] = time_packed_leg(ctx, B, synth, ev, n, args, stream, img, bf16=True)
+    if not args.no_legs and not args.samples and args.serve_leg_jobs > 0 and world == 1:
+        ctx.close()                 # the served contexts hold their own copies of the events
+        legs["serve"] = serve_leg(args, ev, pinned, args.serve_leg_jobs, local)
 
     # roofline of the dominant kernel (the fused event pass)
-    passes = max(1, stats["pass_launches"])
-    pass_ms = stats["pass_ms"] / passes
-    upd_ms = stats["update_ms"] / passes
+    passes = max(1, split_stats["pass_launches"])
+    pass_ms = split_stats["pass_ms"] / passes
+    upd_ms = split_stats["update_ms"] / passes
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -712,8 +753,12 @@ def run_ours(args):
            "extra": {"t_generate_s": t_gen, "t_sensitivity_s": t_sens, "t_load_s": t_load,
                      "launch": {"threads": cfg[0], "blocks_per_sm": cfg[1], "chunk": cfg[2], "cached_pieces": cfg[3],
                                 "piece_mass": cfg[4]},
-                     "tiles": {k: v for k, v in ctx.get_info().items() if k.startswith("tile")},
-                     "pass_ms": pass_ms, "update_ms": upd_ms, "conservation_last": list(cons[-1])}}
+                     "tiles": tiles_info,
+                     "pass_ms": pass_ms, "update_ms": upd_ms, "conservation_last": list(cons[-1]),
+                     "pass_split_run": {"how": "the timed steps repeated with per-kernel CUDA events on the "
+                                               "context's stream (direct launches, no graph replay)",
+                                        "ms_per_step": split_ms / args.steps,
+                                        "pass_launches": int(split_stats["pass_launches"])}}}
     if rank == 0:
         peaks, src = measured_peaks()
         vbar = mean_visits(ev)
@@ -733,7 +778,7 @@ def run_ours(args):
             out["roofline"] = {"bound": "l2_reductions", "achieved": None, "peak": probes.get("l2_red_gops"),
                                "unit": "Gred/s",
                                "frac": None, "traffic": None,
-                               "note": "sampled projector timed; see profiles/k_lut_pass_fullbody_8M.md"}
+                               "note": "sampled projector timed: the Siddon-piece roofline does not apply"}
         if not args.no_cpu_baseline:
             lsub = lors[:, :200_000]
             out["cpu_baseline"] = cpu_baseline(ev, lsub, args.iters, args.cpu_sample)

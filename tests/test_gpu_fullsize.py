@@ -2,8 +2,14 @@
 grid of 4 mm voxels, events resident on the device, in the launch and event order
 that the benchmark times (the library's autotuned default).
 
-The FP64 oracle cannot reconstruct 146 M events inside a test, so it recomputes
-sampled outputs one by one.  One MLEM iteration (Sec. 2.4) from a seeded random
+The benchmark's own reconstruction is compared whole: the sensitivity image from
+its 50 M LORs element by element, and the image after its three MLEM iterations
+from the uniform start over every voxel, against the FP64 oracle run over all
+146 M events (a few minutes on the host cores).
+
+The other tests recompute sampled outputs one by one, which lets them cover the
+projector variants, the region form and the sieve at this size without an oracle
+reconstruction each.  One MLEM iteration (Sec. 2.4) from a seeded random
 start image lam0 gives, at voxel j,
 
     lam1_j = lam0_j / s_j * sum_i a_ij w_i / p_i,      p_i = sum_k a_ik lam0_k,
@@ -32,7 +38,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import SIGMA, geometry, grid_tuple, workload_grid
+from gpu_common import SIGMA, geometry, grid_tuple, max_rel_above, rel_l2, workload_grid
 from paper_1706_07075_b300 import binding as B
 from paper_1706_07075_b300 import synth
 
@@ -40,6 +46,8 @@ pytestmark = pytest.mark.gpu
 
 N_EVENTS = 146_000_000          # the full-body benchmark workload
 SEED = 1708                     # the benchmark's event seed (rank 0)
+N_LORS = 50_000_000             # the benchmark's sensitivity LORs (same seed)
+N_ITER = 3                      # MLEM iterations of a benchmark step
 K = 3.0
 MARGIN_MM = 1.0                 # prefilter margin (covers the int16/FP16 packing error)
 FULLBODY_REGIONS = synth.FULLBODY_REGIONS   # the benchmark's nine body regions
@@ -459,3 +467,70 @@ def test_fullsize_region_mlem(full, ctx, regions_ref):
     starts = np.cumsum([0] + [(hi - lo) * g.ny * g.nx for lo, hi in slabs])
     parts = [slab_img[starts[r]:starts[r + 1]] for r in range(len(slabs))]
     assert np.allclose(img, oracle.stitch(g, slabs, parts), rtol=1e-6, atol=0.0)
+
+
+@pytest.fixture(scope="module")
+def whole(full):
+    """The benchmark's reconstruction end to end: the sensitivity image from the
+    50 M LORs, then three MLEM iterations from the uniform start over the resident
+    146 M events in the autotuned default launch and event order (graphs on), on
+    the GPU; and the same from the FP64 oracle over all events and LORs."""
+    import time
+    g, ev = full["g"], full["ev"]
+    lors = synth.sensitivity_lors("fullbody", N_LORS, SEED)
+    s_gpu = np.zeros(g.n_vox)
+    img = np.zeros(g.n_vox, np.float32)
+    cons = np.zeros((N_ITER, 2))
+    with B.Context(geometry("fullbody"), grid_tuple(g), 300.0) as c:
+        c.sensitivity(lors, s_gpu)
+        c.load_events(B.make_events(ev))
+        c.mlem(None, N_ITER, None, img, cons)
+        launch = c.get_launch()
+    t = time.perf_counter()
+    s_ref = oracle.sensitivity(g, lors)
+    t_sens = time.perf_counter() - t
+    del lors
+    evd = ev.astype(np.float64)
+    t = time.perf_counter()
+    lam_ref, hist = oracle.mlem(g, evd, s_ref, N_ITER, SIGMA)
+    t_mlem = time.perf_counter() - t
+    del evd
+    print(f"\noracle over the whole workload: sensitivity {t_sens:.0f} s, {N_ITER} MLEM iterations "
+          f"{t_mlem:.0f} s ({oracle.threads_used()} threads); GPU launch {launch}")
+    return {"s": s_gpu, "s_ref": s_ref, "img": img, "cons": cons, "lam_ref": lam_ref, "hist": hist}
+
+
+def test_fullsize_sensitivity_whole_image(full, whole):
+    # every voxel of the full-body sensitivity image from the benchmark's 50 M LORs;
+    # tolerances as on the tiny grid: the FP32 walk's plane crossings move up to
+    # ~1e-2 mm of chord between two voxels for lines nearly parallel to a plane,
+    # which stays below 2e-4 of s_j at voxels above 1% of the maximum
+    s, s_ref = whole["s"], whole["s_ref"]
+    mask_diff = int(np.sum((s > 0) != (s_ref > 0)))
+    l2 = rel_l2(s, s_ref)
+    mx = max_rel_above(s, s_ref, 0.01)
+    print(f"\nsensitivity, 50 M LORs, {s.size} voxels: rel L2 {l2:.2e}, max rel above 1% {mx:.2e}, "
+          f"support differs at {mask_diff} voxels")
+    assert mask_diff <= 1e-6 * s.size + 2
+    assert l2 < 1e-6
+    assert mx < 2e-4
+
+
+def test_fullsize_mlem_whole_image(full, whole):
+    # the benchmark's step, compared over the whole 150 x 150 x 600 image with the
+    # plain gates: relative L2 <= 1e-4 and per-voxel relative error <= 1e-3 on the
+    # voxels above 1% of the maximum
+    img, lam_ref, cons, hist = whole["img"], whole["lam_ref"], whole["cons"], whole["hist"]
+    l2 = rel_l2(img, lam_ref)
+    mx = max_rel_above(img, lam_ref, 0.01)
+    big = lam_ref > 0.01 * lam_ref.max()
+    print(f"\n{N_ITER} MLEM iterations, 146 M events, whole image: rel L2 {l2:.2e}, max rel {mx:.2e} over "
+          f"{int(big.sum())} voxels above 1% of max; N_eff {cons[:, 0].tolist()} vs oracle "
+          f"{[h[0] for h in hist]}")
+    assert np.isfinite(img).all() and img.min() >= 0.0
+    assert l2 <= 1e-4
+    assert mx <= 1e-3
+    for k in range(N_ITER):
+        # events whose window only touches the grid may fall either way in FP32
+        assert abs(cons[k, 0] - hist[k][0]) <= 1e-6 * N_EVENTS
+        assert cons[k, 1] == pytest.approx(cons[k, 0], rel=1e-5)

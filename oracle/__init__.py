@@ -30,6 +30,8 @@ Parity status of each function (what pins it is in tests/test_oracle_*.py):
   backproject_lut ..... pinned (brute-force sample positions on axis lines;
                         unit mass inside the grid; adjointness; convergence
                         to the exact Siddon x Phi projector as N grows)
+  lut_ambiguous ....... pinned (samples placed by hand at known distances
+                        from voxel planes and from the grid boundary)
   preprocess .......... pinned (closed-form line integrals through uniform
                         boxes and a sphere; rejection decided by hand-built
                         events inside, outside and at the 1.96 sigma edge)
@@ -50,6 +52,8 @@ from .core import (  # noqa: F401
     count_visits,
     forward,
     forward_lut,
+    LUT_EPS_VOXELS,
+    lut_ambiguous,
     lut_samples,
     preprocess,
     region_codes,

@@ -88,13 +88,15 @@ def _load():
             lib.oracle_preprocess.argtypes = [gp, planes, C.c_int64, C.c_int64, dp, C.c_double, C.c_double, dp,
                                               C.POINTER(C.c_uint8)]
             lib.oracle_preprocess.restype = C.c_int64
-            fp = C.POINTER(C.c_float)
             lib.oracle_lut_samples.argtypes = [C.c_int32, C.c_double, C.c_double, dp, dp]
             lib.oracle_lut_samples.restype = None
-            lib.oracle_forward_lut.argtypes = [gp, planes, C.c_int64, C.c_int64, C.c_int32, dp, fp, dp, dp]
+            lib.oracle_forward_lut.argtypes = [gp, planes, C.c_int64, C.c_int64, C.c_int32, dp, dp, dp, dp]
             lib.oracle_forward_lut.restype = C.c_int
-            lib.oracle_backproject_lut.argtypes = [gp, planes, C.c_int64, C.c_int64, C.c_int32, dp, fp, dp, dp]
+            lib.oracle_backproject_lut.argtypes = [gp, planes, C.c_int64, C.c_int64, C.c_int32, dp, dp, dp, dp]
             lib.oracle_backproject_lut.restype = C.c_int
+            lib.oracle_lut_ambiguous.argtypes = [gp, planes, C.c_int64, C.c_int64, C.c_int32, dp, C.c_double,
+                                                 C.POINTER(C.c_int32)]
+            lib.oracle_lut_ambiguous.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -319,14 +321,26 @@ def lut_samples(n_samples, sigma, K=3.0):
     return t, w
 
 
+# Samples within this many voxels of a voxel plane are "ambiguous": an FP32
+# evaluation of the sample position may put them in the neighbouring voxel.
+# Bound on that FP32 error for one IEEE rounding per operation (unit roundoff
+# 2^-24 = 6e-8), with coordinates up to 1.2 m, |d| up to 1 m and |t| up to 3
+# sigma = 57 mm: the TOF point c = M + d u carries |M| 2^-24 + |d| 6 2^-24
+# <= 4e-4 mm, c - o another 1.2e-4 mm, the voxel-unit scaling and the final
+# fused multiply-add ~6e-5 voxel each, so the voxel coordinate of a sample is off
+# by at most ~2e-4 voxel on the 4 mm full-body grid (less on smaller grids; the
+# FP32 rounding of t_k adds 5e-7 voxel).  1e-3 voxel leaves a factor of five.
+LUT_EPS_VOXELS = 1e-3
+
+
 def _lut_args(n_samples, sigma, K):
     t, w = lut_samples(n_samples, sigma, K)
-    t32 = np.ascontiguousarray(t.astype(np.float32))
-    return w, t32, t32.ctypes.data_as(C.POINTER(C.c_float))
+    return np.ascontiguousarray(w), np.ascontiguousarray(t)
 
 
 def forward_lut(grid, events, lam, n_samples, sigma, K=3.0, threads=None):
-    """p_i with the sampled kernel: sum_k w_k lambda(voxel of sample k)."""
+    """p_i with the sampled kernel: sum_k w_k lambda(voxel of sample k), voxels
+    decided in FP64 from the exact sample positions c + t_k u."""
     lib = _load()
     keep, ptrs = _event_planes(events)
     n = keep[0].shape[0]
@@ -334,11 +348,12 @@ def forward_lut(grid, events, lam, n_samples, sigma, K=3.0, threads=None):
     p = np.zeros(n)
     if n == 0:
         return p
-    w, t32, tp = _lut_args(n_samples, sigma, K)
+    w, t = _lut_args(n_samples, sigma, K)
     g = grid.c()
 
     def part(i0, i1):
-        return lib.oracle_forward_lut(C.byref(g), ptrs, i0, i1, int(n_samples), _dptr(w), tp, _dptr(lam), _dptr(p))
+        return lib.oracle_forward_lut(C.byref(g), ptrs, i0, i1, int(n_samples), _dptr(w), _dptr(t), _dptr(lam),
+                                      _dptr(p))
 
     _run_threads(part, _ranges(n, threads or threads_used(n)))
     return p
@@ -350,13 +365,13 @@ def backproject_lut(grid, events, r, n_samples, sigma, K=3.0, threads=None):
     keep, ptrs = _event_planes(events)
     n = keep[0].shape[0]
     r = np.ascontiguousarray(r, np.float64).reshape(-1)
-    w, t32, tp = _lut_args(n_samples, sigma, K)
+    w, t = _lut_args(n_samples, sigma, K)
     g = grid.c()
     ranges = _ranges(n, threads or threads_used(n)) if n else []
     accs = [np.zeros(grid.n_vox) for _ in ranges]
 
     def part(i0, i1, k):
-        return lib.oracle_backproject_lut(C.byref(g), ptrs, i0, i1, int(n_samples), _dptr(w), tp, _dptr(r),
+        return lib.oracle_backproject_lut(C.byref(g), ptrs, i0, i1, int(n_samples), _dptr(w), _dptr(t), _dptr(r),
                                           _dptr(accs[k]))
 
     _run_threads(part, [(a, b, k) for k, (a, b) in enumerate(ranges)])
@@ -364,6 +379,27 @@ def backproject_lut(grid, events, r, n_samples, sigma, K=3.0, threads=None):
     for acc in accs:
         total += acc
     return total
+
+
+def lut_ambiguous(grid, events, n_samples, sigma, K=3.0, eps=LUT_EPS_VOXELS, threads=None):
+    """Per event, how many of its samples lie within eps voxels of a voxel plane
+    (or of the grid boundary), where a lower-precision evaluation of the sample
+    position may choose the neighbouring voxel."""
+    lib = _load()
+    keep, ptrs = _event_planes(events)
+    n = keep[0].shape[0]
+    out = np.zeros(n, np.int32)
+    if n == 0:
+        return out
+    _, t = _lut_args(n_samples, sigma, K)
+    g = grid.c()
+
+    def part(i0, i1):
+        return lib.oracle_lut_ambiguous(C.byref(g), ptrs, i0, i1, int(n_samples), _dptr(t), float(eps),
+                                        out.ctypes.data_as(C.POINTER(C.c_int32)))
+
+    _run_threads(part, _ranges(n, threads or threads_used(n)))
+    return out
 
 
 # ---------------------------------------------------------- region division

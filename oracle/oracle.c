@@ -406,52 +406,63 @@ void oracle_lut_samples(int32_t N, double sigma, double K, double *t, double *w)
 }
 
 /*
- * Voxel of sample k of event i, or -1 outside the grid.  A voxel index is an
- * integer decided by floating point, so it is decided here in FP32 with the
- * operation sequence the GPU kernel uses (one rounding per operation; fmaf is
- * the correctly rounded fused multiply-add), from the FP32 event values and
- * the FP32 sample offset t32.  Everything else of the projector is FP64.
+ * Voxel of the sample at offset t (mm) along event i's line, decided in FP64
+ * from the event's values (Sec. 2.3, "direct technique for voxel filling": the
+ * sample's weight goes to the voxel that contains it):
+ *     u = (P1 - P2) / |P1 - P2|,  c = M + d u,  x = c + t u,
+ *     voxel = floor((x - o) / v) per axis, -1 outside the grid.
+ * *margin (nullable) receives how close the decision came to another outcome:
+ * the distance, in voxels, from (x - o) / v to the nearest integer over the axes
+ * on which the sample lies within the grid's extent widened by one voxel (a
+ * sample outside the grid by more than that on any axis gets a margin of 1).
  */
-static int64_t lut_voxel(const og_grid *g, const float e[7], float t32)
+static int64_t lut_voxel(const og_grid *g, const double e[7], double t, double *margin)
 {
-    const float dx = e[0] - e[3], dy = e[1] - e[4], dz = e[2] - e[5];
-    const float D = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
-    if (!(D > 0.0f)) return -1;
-    const float inv = 1.0f / D;
-    const float u[3] = {dx * inv, dy * inv, dz * inv};
-    const float m[3] = {0.5f * (e[0] + e[3]), 0.5f * (e[1] + e[4]), 0.5f * (e[2] + e[5])};
-    const float o[3] = {(float)g->ox, (float)g->oy, (float)g->oz};
-    const float v[3] = {(float)g->vx, (float)g->vy, (float)g->vz};
-    const int32_t n[3] = {g->nx, g->ny, g->nz};
+    const double dx = e[0] - e[3], dy = e[1] - e[4], dz = e[2] - e[5];
+    const double D = sqrt(dx * dx + dy * dy + dz * dz);
+    if (margin) *margin = 1.0;
+    if (!(D > 0.0)) return -1;
+    const double u[3] = {dx / D, dy / D, dz / D};
     int64_t idx[3];
+    int inside = 1;
+    double near = 1.0;
     for (int k = 0; k < 3; ++k) {
-        const float iv = 1.0f / v[k];
-        const float c = fmaf(e[6], u[k], m[k]);   /* TOF point */
-        const float A = (c - o[k]) * iv;          /* TOF point in voxel units */
-        const float B = u[k] * iv;                /* direction in voxel units */
-        const float f = floorf(fmaf(t32, B, A));  /* voxel of the sample at c + t u */
-        if (!(f >= 0.0f) || !(f < (float)n[k])) return -1;
+        const double m = 0.5 * (e[k] + e[k + 3]);
+        const double x = m + (e[6] + t) * u[k];          /* c + t u along axis k */
+        const double q = (x - axis_origin(g, k)) / axis_voxel(g, k);
+        const double f = floor(q);
+        const int32_t n = axis_count(g, k);
+        if (!(f >= 0.0) || !(f < (double)n)) inside = 0;
+        if (q < -1.0 || q > (double)n + 1.0) {            /* far outside on this axis */
+            near = 1.0;
+            if (margin) *margin = 1.0;
+            return -1;
+        }
+        const double dist = fmin(q - f, f + 1.0 - q);
+        if (dist < near) near = dist;
         idx[k] = (int64_t)f;
     }
+    if (margin) *margin = near;
+    if (!inside) return -1;
     return idx[0] + (int64_t)g->nx * (idx[1] + (int64_t)g->ny * idx[2]);
 }
 
-static void event_f32(const double *const ev[7], int64_t i, float e[7])
+static void event_values(const double *const ev[7], int64_t i, double e[7])
 {
-    for (int k = 0; k < 7; ++k) e[k] = (float)ev[k][i];
+    for (int k = 0; k < 7; ++k) e[k] = ev[k][i];
 }
 
-/* p_i = sum_k w_k lambda(voxel of sample k), events [i0, i1). t32: the FP32
- * sample offsets the GPU uses (the same values rounded once from t_k). */
+/* p_i = sum_k w_k lambda(voxel of sample k), events [i0, i1); t[k], w[k] from
+ * oracle_lut_samples. */
 int oracle_forward_lut(const og_grid *g, const double *const ev[7], int64_t i0, int64_t i1, int32_t N,
-                       const double *w, const float *t32, const double *lambda, double *p_out)
+                       const double *w, const double *t, const double *lambda, double *p_out)
 {
     for (int64_t i = i0; i < i1; ++i) {
-        float e[7];
-        event_f32(ev, i, e);
+        double e[7];
+        event_values(ev, i, e);
         double p = 0.0;
         for (int32_t k = 0; k < N; ++k) {
-            int64_t j = lut_voxel(g, e, t32[k]);
+            int64_t j = lut_voxel(g, e, t[k], NULL);
             if (j >= 0) p += w[k] * lambda[j];
         }
         p_out[i] = p;
@@ -461,16 +472,37 @@ int oracle_forward_lut(const og_grid *g, const double *const ev[7], int64_t i0, 
 
 /* C_j += sum_k w_k r_i over the samples of events [i0, i1) falling in voxel j. */
 int oracle_backproject_lut(const og_grid *g, const double *const ev[7], int64_t i0, int64_t i1, int32_t N,
-                           const double *w, const float *t32, const double *r, double *C_acc)
+                           const double *w, const double *t, const double *r, double *C_acc)
 {
     for (int64_t i = i0; i < i1; ++i) {
         if (r[i] == 0.0) continue;
-        float e[7];
-        event_f32(ev, i, e);
+        double e[7];
+        event_values(ev, i, e);
         for (int32_t k = 0; k < N; ++k) {
-            int64_t j = lut_voxel(g, e, t32[k]);
+            int64_t j = lut_voxel(g, e, t[k], NULL);
             if (j >= 0) C_acc[j] += w[k] * r[i];
         }
+    }
+    return 0;
+}
+
+/* Per event of [i0, i1): the number of its N samples whose position lies within
+ * eps voxels of a voxel plane (or of the grid's boundary), where a computation
+ * in lower precision could decide the voxel, or inside versus outside,
+ * differently from this one. */
+int oracle_lut_ambiguous(const og_grid *g, const double *const ev[7], int64_t i0, int64_t i1, int32_t N,
+                         const double *t, double eps, int32_t *count_out)
+{
+    for (int64_t i = i0; i < i1; ++i) {
+        double e[7];
+        event_values(ev, i, e);
+        int32_t c = 0;
+        for (int32_t k = 0; k < N; ++k) {
+            double margin = 1.0;
+            lut_voxel(g, e, t[k], &margin);
+            if (margin < eps) ++c;
+        }
+        count_out[i] = c;
     }
     return 0;
 }

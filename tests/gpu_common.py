@@ -59,3 +59,11 @@ def max_rel_above(a, b, frac=0.01):
 
 def new_context(name, **kw):
     return B.Context(geometry(name), grid_tuple(workload_grid(name)), kw.get("fwhm", TOF_FWHM_PS))
+
+
+def lut_unambiguous(g, ev, n_samples):
+    """The events of ev ((7, n) float32) none of whose n_samples samples lies within
+    oracle.LUT_EPS_VOXELS of a voxel plane (oracle.lut_ambiguous): on those the
+    kernel's FP32 voxel decisions equal the oracle's FP64 ones."""
+    mask = oracle.lut_ambiguous(g, ev.astype(np.float64), n_samples, SIGMA) == 0
+    return np.ascontiguousarray(ev[:, mask])

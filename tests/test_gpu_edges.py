@@ -200,7 +200,14 @@ def test_kernel_window_changes_the_projector(ctx_tiny):
     ctx.set_kernel_window(3.0)
     p_ref = oracle.forward(g, sub.astype(np.float64), lam.astype(np.float64), SIGMA, K=2.0)
     sel = p_ref > 1e-3 * p_ref.max()
+    # per-event bound of the FP32 walk (the same as test_forward_matches_oracle): a
+    # plane crossing tau = (X - c_k) / u_k carries ~ulp(|X - c_k|) / |u_k| of rounding,
+    # 3.8e-6 mm / 1e-3 = 3.8e-3 mm for a line with |u_k| = 1e-3, which moves that much
+    # chord between two voxels whose lambda differ by up to 1 (lambda in [0.5, 1.5]) at
+    # a TOF density of at most 1/(sigma sqrt(2 pi)) = 0.021 / mm: ~8e-5 of p_i ~ 1.
+    # Among 5000 isotropic lines about 15 have some |u_k| < 1e-3.
     assert np.max(np.abs(p[sel] - p_ref[sel]) / p_ref[sel]) < 1e-4
+    assert np.linalg.norm(p - p_ref) / np.linalg.norm(p_ref) < 2e-6
 
 
 def test_largest_grid_unit_mass():

@@ -130,3 +130,43 @@ def test_many_samples_converge_to_exact_projector():
     errs = [np.max(np.abs(oracle.forward_lut(g, ev, lam, n, SIGMA, K) - exact) / exact) for n in (32, 512, 8192)]
     assert errs[2] < 2e-3
     assert errs[0] > errs[1] > errs[2]
+
+
+def test_ambiguous_samples_are_those_near_a_voxel_plane():
+    # line along +x through voxel centres in y and z (half a voxel from every y, z
+    # plane): sample k sits at x = d + t_k, so its distance to the nearest x plane
+    # in voxels is known by hand.  Samples within eps voxels of a plane (the grid's
+    # faces included) count; samples more than a voxel outside the grid do not.
+    g = Grid(200, 3, 3, 2.0, 2.0, 2.0, -200.0, -3.0, -3.0)
+    n = 32
+    t, _ = oracle.lut_samples(n, SIGMA, K)
+    eps = oracle.LUT_EPS_VOXELS
+    on_plane = 10.0 - t[5]                       # sample 5 exactly at x = 10 mm, a plane
+    cases = {0.0: None, 7.3: None, on_plane: 1, on_plane + 0.5 * eps * g.vx: 1, on_plane + 4 * eps * g.vx: 0,
+             -200.0 - t[0]: 1, 300.0: 0}
+    for d, expect_k5 in cases.items():
+        ev = events_from([500.0, 0.0, 0.0], [-500.0, 0.0, 0.0], d)
+        got = int(oracle.lut_ambiguous(g, ev, n, SIGMA, K)[0])
+        q = (d + t - g.ox) / g.vx
+        near = np.abs(q - np.round(q)) < eps
+        reach = (q >= -1.0) & (q <= g.nx + 1.0)
+        assert got == int(np.sum(near & reach)), d
+        if expect_k5 is not None and d != -200.0 - t[0]:
+            assert bool(near[5] & reach[5]) == bool(expect_k5)
+    # the first sample exactly on the grid's low face: inside versus outside is ambiguous
+    ev = events_from([500.0, 0.0, 0.0], [-500.0, 0.0, 0.0], -200.0 - t[0])
+    assert oracle.lut_ambiguous(g, ev, n, SIGMA, K)[0] >= 1
+    # a TOF point far from the grid: nothing to decide
+    far = events_from([0.0, 0.0, 900.0], [0.0, 0.0, -900.0], 600.0)
+    assert oracle.lut_ambiguous(g, far, n, SIGMA, K)[0] == 0
+    # isotropic lines: the share of ambiguous samples is 2 eps per axis crossing
+    # the grid, ~6 eps in all
+    rng = np.random.default_rng(12)
+    gg = Grid.centred(64, 64, 64, 4.0)
+    m = 20_000
+    u = rng.normal(size=(m, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    c = rng.uniform(-40, 40, (m, 3))
+    ev = events_from(c + 400 * u, c - 400 * u, rng.uniform(-10, 10, m))
+    share = oracle.lut_ambiguous(gg, ev, n, SIGMA, K).sum() / (m * n)
+    assert share == pytest.approx(6 * eps, rel=0.15)

@@ -66,6 +66,10 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="run the served-reconstruction workload (Poisson stream of mixed jobs) instead")
     ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "events"],
+                    help="with N GPUs: replicas (each rank reconstructs its own 146M events, weak scaling) or "
+                         "events (one 146M-event job, each rank a shard of the events, one all-reduce of C per "
+                         "iteration, strong scaling)")
     ap.add_argument("--serve-leg-jobs", type=int, default=60,
                     help="jobs of the bounded serving leg of the default line (0: no serving leg)")
     return ap.parse_args()
@@ -327,6 +331,88 @@ def run_reference(args):
     return 0
 
 
+
+
+def time_split_leg(ctx, B, n, args, stream):
+    """MLEM through recon_event_pass + recon_update, the calls of the event-sharded
+    form, on one rank: the cost of the split (C copied out and back, the stream
+    synchronised twice per iteration) against recon_mlem's graph replay."""
+    import torch
+    from paper_1706_07075_b300.shard import sharded_mlem
+    dev = torch.device("cuda", torch.cuda.current_device())
+    c_buf = torch.zeros(ctx.n_vox, dtype=torch.float32, device=dev)
+    one_rank = lambda c, n_eff: n_eff                                  # noqa: E731  (world of one: no exchange)
+    sharded_mlem(ctx, args.iters, c_buf, one_rank)                     # warm-up
+    ms = _timed_steps(stream, args.steps, lambda: sharded_mlem(ctx, args.iters, c_buf, one_rank))
+    return {"workload": "fullbody, 3 iterations as recon_event_pass + recon_update (one rank)",
+            "value": n * args.iters * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps}
+
+
+def run_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n_total):
+    """One full-body job with its events sharded over the ranks (NCCL all-reduce
+    of C per iteration); every rank holds n_total / world events."""
+    import numpy as np
+    import torch
+    from paper_1706_07075_b300.shard import sharded_mlem, torch_allreduce_sum
+    c_buf = torch.zeros(ctx.n_vox, dtype=torch.float32, device=dev)
+    red = torch_allreduce_sum() if world > 1 else (lambda c, n_eff: n_eff)
+    for _ in range(args.warmup):
+        sharded_mlem(ctx, args.iters, c_buf, red)
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hist = None
+    for _ in range(args.steps):
+        hist = sharded_mlem(ctx, args.iters, c_buf, red)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)))
+    value = n_total * args.iters * args.steps / (ms / 1e3)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(args, n_total, world), parallelism=f"events{world}",
+                           sharding="each rank a shard of the events; one all-reduce of C (54 MB) per iteration"),
+            "gpu_launches": int(ctx.get_stats()["kernel_launches"]), "clocks": clocks,
+            "conservation_last": [float(x) for x in hist[-1]]}
+
+
+def launch_record(ctx_cfg, layout):
+    """The event-pass launch the library used, every tuned dimension named."""
+    return {"threads": ctx_cfg[0], "blocks_per_sm": ctx_cfg[1], "chunk": ctx_cfg[2], "cached_pieces": ctx_cfg[3],
+            "piece_mass": ["fitted erfc tails", "erfcf tails", "midpoint series"][ctx_cfg[4]],
+            "reduction": ["scalar, linear image", "per-brick-half vector, 2x2x2-brick copies"][ctx_cfg[5]],
+            "image_tiling": ["global image (L2-resident)", "shared-memory tiles"][layout[0]],
+            "threads_per_event": layout[1]}
+
+
+def time_smallfov_leg(B, synth, args, stream):
+    """The small field of view of the served mix (128^3 voxels of 0.5 mm, R = 60 mm,
+    5 M events, ~200 Siddon pieces per event) as a reconstruction of its own: the
+    launch the autotuner picks for it and its rate, events resident."""
+    import numpy as np
+    ev = synth.events("smallfov", 5_000_000, args.seed)
+    lors = synth.sensitivity_lors("smallfov", 10_000_000, args.seed)
+    with B.Context((60.0, 100.0, 90.0), synth.grid_of("smallfov"), 300.0) as c:
+        c.set_stream(stream.cuda_stream)
+        c.sensitivity(lors)
+        c.load_events(B.make_events(ev))
+        cons = np.zeros((args.iters, 2))
+        c.mlem(None, args.iters, None, None, cons)          # warm-up (+ autotune for this key)
+        ms = _timed_steps(stream, args.steps, lambda: c.mlem(None, args.iters, None, None, cons))
+        rec = launch_record(c.get_launch(), c.get_layout())
+    return {"workload": "small FOV 128^3 @ 0.5 mm, R = 60 mm scanner, 5 M events, 3 iterations",
+            "value": ev.shape[1] * args.iters * args.steps / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / args.steps, "launch": rec, "conservation_last": [float(x) for x in cons[-1]]}
 
 
 def _timed_steps(stream, k, fn):
@@ -637,7 +723,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    n = args.events
+    n = args.events if args.shard == "replicas" else args.events // world
     t_gen = time.perf_counter()
     ev = synth.events("fullbody", n, args.seed + rank)
     lors = synth.sensitivity_lors("fullbody", args.lors, args.seed)
@@ -665,10 +751,19 @@ def run_ours(args):
     az, pol = (int(x) for x in args.dir_bins.split(","))
     if args.cell_order or (az, pol) != (1, 1):
         ctx.set_event_order(args.cell_order or -1, az, pol)
+    if args.shard == "events":
+        line = run_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n * world)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        ctx.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
     # warm-up (the first call also runs the launch autotuner)
     for _ in range(args.warmup):
         ctx.mlem(None, args.iters)
     cfg = ctx.get_launch()
+    layout = ctx.get_layout()
 
     # timed region: events resident in HBM, each iteration a CUDA-graph replay (the
     # library's default path)
@@ -731,8 +826,11 @@ def run_ours(args):
         legs["osem5"] = time_osem_leg(ctx, B, n, args, stream)
         legs["preprocess"] = time_preprocess_leg(ctx, B, synth, n, stream)
         legs["regions"] = time_regions_leg(ctx, B, n, args, stream)
+        legs["split_pass_update"] = time_split_leg(ctx, B, n, args, stream)
+        # the packed legs load packed events into the context: they come last
         legs["packed_f32"] = time_packed_leg(ctx, B, synth, ev, n, args, stream, img, bf16=False)
         legs["packed_bf16"] = time_packed_leg(ctx, B, synth, ev, n, args, stream, img, bf16=True)
+        legs["smallfov"] = time_smallfov_leg(B, synth, args, stream)
     if not args.no_legs and not args.samples and args.serve_leg_jobs > 0 and world == 1:
         ctx.close()                 # the served contexts hold their own copies of the events
         legs["serve"] = serve_leg(args, ev, pinned, args.serve_leg_jobs, local)
@@ -751,8 +849,7 @@ def run_ours(args):
            "clocks": clocks,
            "legs": legs,
            "extra": {"t_generate_s": t_gen, "t_sensitivity_s": t_sens, "t_load_s": t_load,
-                     "launch": {"threads": cfg[0], "blocks_per_sm": cfg[1], "chunk": cfg[2], "cached_pieces": cfg[3],
-                                "piece_mass": cfg[4]},
+                     "launch": launch_record(ctx_cfg=cfg, layout=layout),
                      "tiles": tiles_info,
                      "pass_ms": pass_ms, "update_ms": upd_ms, "conservation_last": list(cons[-1]),
                      "pass_split_run": {"how": "the timed steps repeated with per-kernel CUDA events on the "

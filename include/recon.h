@@ -106,6 +106,18 @@ typedef struct {
                                   the h^6 term (Hermite polynomials; error below 1e-7 of the window mass
                                   for pieces up to 0.4 sigma).  Without a fixed launch the library uses
                                   2 only when the voxel diagonal is at most 0.5 sigma, else 0 */
+    int32_t reduction;         /* exact projector in recon_mlem (one grid, FP32 gathers, flat grid, no piece
+                                  cache): 0 scalar FP32 reductions into the linear image; 1 lambda and C
+                                  in 2x2x2-voxel brick copies (one 32-byte sector per brick), each lane's
+                                  consecutive pieces within one 16-byte brick half gathered by one load
+                                  and reduced by one red.global.add.v4.f32 (same pieces and masses; the
+                                  sums run in another order).  Other passes use 0 */
+    int32_t image_tiling;      /* reported by recon_get_launch, ignored by recon_set_launch: 1 when the
+                                  last MLEM pass held lambda and C in shared-memory tiles of the event's
+                                  cell (recon_set_tiled_pass, or the autotuner's choice), 0 when it read
+                                  and reduced into the global image */
+    int32_t lanes_per_event;   /* reported by recon_get_launch, ignored by recon_set_launch: threads per
+                                  event of the last MLEM pass (1, or 8 in the tiled pass) */
 } recon_launch;
 
 typedef struct {
@@ -300,10 +312,30 @@ recon_status recon_set_graphs(recon_ctx* ctx, int32_t on);
 /* Let recon_mlem / recon_mlem_regions search launch configurations of the exact
  * projector's event pass on the resident events the first time they meet a new
  * (event count, format, voxel count, region count, event order) with at least 2^20
- * events (1, default), or use the default launch (0).  Each of 11 candidates (threads per
- * block, flat or persistent grid, piece cache, piece-mass form) runs two timed passes;
- * C is cleared afterwards, so the search changes no result. */
+ * events (1, default), or use the default launch (0).  Candidates: threads per block,
+ * flat or persistent grid, piece cache, piece-mass form and reduction form (scalar
+ * into the linear image, or per-brick-half vector reductions over brick copies; the
+ * latter with one grid and FP32 gathers), 15 in all, each timed over two passes (the
+ * brick candidates with their copy kernels).  recon_mlem in the default event order
+ * then also times the shared-memory tiled pass (recon_set_tiled_pass) with 1 and 8
+ * threads per event against the best of those, where tiles fit (exact projector, one
+ * subset, FP32 gathers), and keeps the faster image layout for the key.  C and the
+ * N_eff sums are cleared afterwards, so the search changes no result;
+ * recon_get_launch reports every chosen dimension. */
 recon_status recon_set_autotune(recon_ctx* ctx, int32_t on);
+
+/* Failure injection for testing how callers and the library handle an exhausted
+ * device (the paper has no counterpart).  n > 0: the n-th device allocation the
+ * library attempts from now on (n = 1: the next one), in any context and on any
+ * thread, fails as if the device were out of memory: nothing is allocated and the
+ * call that needed it returns RECON_ENOMEM with a message naming the allocation.
+ * n = 0 disarms.  Only the host side is affected: no kernel runs or faults for it.
+ * A call that fails this way leaves the context usable: a buffer that could not grow
+ * keeps its old allocation, and state that was being replaced (resident events, the
+ * sensitivity image, cached binnings and graphs) is dropped, so later calls rebuild
+ * it or return RECON_ESTATE.  The device allocations of recon_split_regions_noalloc
+ * do not exist and are not counted.  Errors: EINVAL (n < 0). */
+recon_status recon_debug_fail_alloc(int64_t n);
 
 recon_status recon_get_info(const recon_ctx* ctx, recon_info* out);
 recon_status recon_get_stats(const recon_ctx* ctx, recon_stats* out);
@@ -386,6 +418,34 @@ recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const
  * events). */
 recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_iter, const float* init,
                         float* image_out, double* conservation_out);
+
+/* ------------------------------------------------ one iteration, in parts */
+
+/* One MLEM event pass (Sec. 2.4) over the resident events, for callers that combine
+ * the passes of several contexts before the update: ranks of a job whose events are
+ * sharded over GPUs sum their C images (one all-reduce per iteration) and each then
+ * calls recon_update with the sum.
+ *     p_i = sum_k a_ik lambda_k,   C_j = sum_{i: p_i > 0} a_ij w_i / p_i.
+ * events: NULL = the resident events, else loaded first (and kept resident).
+ * lambda: with from_start = 1 the image 1 on {s_j > 0} (MLEM's first update from any
+ * uniform start gives the same image, so the ranks need not agree on a start value);
+ * else `image` (nx*ny*nz floats, host or device) when not NULL, else the context's
+ * current image.  The image stays in the context for recon_update.
+ * C_out: nx*ny*nz floats (host or device) receiving C.  n_eff_out (nullable): FP64 sum
+ * of w_i over the events with p_i > 0.  Projector, event order, launch and BF16
+ * gathers as for recon_mlem.  Errors: EINVAL (NULL C_out, OSEM subsets set), ESTATE
+ * (no events or no sensitivity image). */
+recon_status recon_event_pass(recon_ctx* ctx, const recon_events* events, const float* image, int32_t from_start,
+                              float* C_out, double* n_eff_out);
+
+/* The MLEM update of the context's image from a correction image (Sec. 2.4):
+ * lambda_j <- lambda_j C_j / s_j on {s_j > 0}, 0 elsewhere, followed by the median
+ * sieve when it is on (recon_set_median_filter).
+ * C_in: nx*ny*nz floats (host or device), e.g. the sum of the ranks' recon_event_pass
+ * outputs.  image_out (nullable): nx*ny*nz floats (host or device) receiving the new
+ * image.  sum_s_lambda_out (nullable): sum_j s_j lambda_j in FP64, before the sieve.
+ * Errors: EINVAL (NULL C_in), ESTATE (no sensitivity image). */
+recon_status recon_update(recon_ctx* ctx, const float* C_in, float* image_out, double* sum_s_lambda_out);
 
 /* ------------------------------------------------------ region division */
 

@@ -48,7 +48,8 @@ class recon_region(C.Structure):
 
 class recon_launch(C.Structure):
     _fields_ = [("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("chunk_events", C.c_int32),
-                ("cached_pieces", C.c_int32), ("tail_eval", C.c_int32)]
+                ("cached_pieces", C.c_int32), ("tail_eval", C.c_int32), ("reduction", C.c_int32),
+                ("image_tiling", C.c_int32), ("lanes_per_event", C.c_int32)]
 
 
 class recon_info(C.Structure):
@@ -99,12 +100,15 @@ SIGNATURES = {
     "recon_forward": (C.c_int, [_CTX, C.POINTER(recon_events), _VP, _VP]),
     "recon_backproject": (C.c_int, [_CTX, C.POINTER(recon_events), _VP, _VP]),
     "recon_mlem": (C.c_int, [_CTX, C.POINTER(recon_events), C.c_int32, _VP, _VP, _VP]),
+    "recon_event_pass": (C.c_int, [_CTX, C.POINTER(recon_events), _VP, C.c_int32, _VP, C.POINTER(C.c_double)]),
+    "recon_update": (C.c_int, [_CTX, _VP, _VP, C.POINTER(C.c_double)]),
     "recon_split_regions": (C.c_int, [_CTX, C.POINTER(recon_events), C.c_int32, C.POINTER(recon_region),
                                       C.c_double, C.c_double, _VP, _VP, _VP]),
     "recon_mlem_regions": (C.c_int, [_CTX, C.POINTER(recon_events), C.c_int32, C.POINTER(recon_region),
                                      C.c_double, C.c_double, C.c_int32, _VP, _VP, _VP]),
     "recon_region_slab_voxels": (C.c_int, [_CTX, C.c_int32, C.POINTER(recon_region), C.c_double,
                                            C.POINTER(C.c_int64)]),
+    "recon_debug_fail_alloc": (C.c_int, [C.c_int64]),
     "recon_split_regions_noalloc": (C.c_int, [C.POINTER(recon_grid), C.POINTER(recon_events), C.c_int32,
                                               C.POINTER(recon_region), C.c_double, _VP, _VP, _VP, C.c_int64, _VP]),
 }
@@ -294,17 +298,28 @@ def recon_get_tof_samples(ctx):
     return t[:n.value].copy(), w[:n.value].copy()
 
 
-def recon_set_launch(ctx, threads_per_block=None, blocks_per_sm=0, chunk_events=0, cached_pieces=0, tail_eval=0):
+def recon_set_launch(ctx, threads_per_block=None, blocks_per_sm=0, chunk_events=0, cached_pieces=0, tail_eval=0,
+                     reduction=0):
     if threads_per_block is None:
         return check(ctx, load().recon_set_launch(ctx, None))
-    cfg = recon_launch(threads_per_block, blocks_per_sm, chunk_events, cached_pieces, tail_eval)
+    cfg = recon_launch(threads_per_block, blocks_per_sm, chunk_events, cached_pieces, tail_eval, reduction, 0, 1)
     return check(ctx, load().recon_set_launch(ctx, C.byref(cfg)))
 
 
 def recon_get_launch(ctx):
+    """(threads, blocks_per_sm, chunk, cached_pieces, tail_eval, reduction) of the last
+    event pass; recon_get_layout gives its image tiling and threads per event."""
     cfg = recon_launch()
     check(ctx, load().recon_get_launch(ctx, C.byref(cfg)))
-    return (cfg.threads_per_block, cfg.blocks_per_sm, cfg.chunk_events, cfg.cached_pieces, cfg.tail_eval)
+    return (cfg.threads_per_block, cfg.blocks_per_sm, cfg.chunk_events, cfg.cached_pieces, cfg.tail_eval,
+            cfg.reduction)
+
+
+def recon_get_layout(ctx):
+    """(image_tiling, lanes_per_event) of the last MLEM event pass."""
+    cfg = recon_launch()
+    check(ctx, load().recon_get_launch(ctx, C.byref(cfg)))
+    return (cfg.image_tiling, cfg.lanes_per_event)
 
 
 def recon_set_timing(ctx, on):
@@ -378,6 +393,22 @@ def recon_mlem(ctx, events, n_iter, init=None, image_out=None, conservation_out=
                                         ptr(init), ptr(image_out), ptr(conservation_out)))
 
 
+def recon_event_pass(ctx, events, image, from_start, C_out):
+    """One MLEM event pass into C_out; returns N_eff."""
+    _check_size("C_out", C_out, recon_get_info(ctx)["n_vox"])
+    n_eff = C.c_double(0.0)
+    check(ctx, load().recon_event_pass(ctx, C.byref(events) if events is not None else None, ptr(image),
+                                       int(from_start), ptr(C_out), C.byref(n_eff)))
+    return n_eff.value
+
+
+def recon_update(ctx, C_in, image_out=None):
+    """The MLEM update from C_in; returns sum_j s_j lambda_j."""
+    ssum = C.c_double(0.0)
+    check(ctx, load().recon_update(ctx, ptr(C_in), ptr(image_out), C.byref(ssum)))
+    return ssum.value
+
+
 def recon_split_regions(ctx, events, regions, margin_mm, shell_mm, code_out=None, offsets_out=None, idx_out=None):
     arr = regions_array(regions)
     return check(ctx, load().recon_split_regions(ctx, C.byref(events) if events is not None else None, len(regions),
@@ -398,6 +429,11 @@ def recon_region_slab_voxels(ctx, regions, margin_mm):
     out = C.c_int64()
     check(ctx, load().recon_region_slab_voxels(ctx, len(regions), arr, float(margin_mm), C.byref(out)))
     return out.value
+
+
+def recon_debug_fail_alloc(n):
+    """Make the n-th device allocation of the library from now on fail (0: disarm)."""
+    return check(None, load().recon_debug_fail_alloc(int(n)))
 
 
 def recon_split_regions_noalloc(grid, events, regions, shell_mm, code_out, offsets_out, idx_out, idx_capacity,

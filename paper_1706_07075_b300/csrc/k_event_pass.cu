@@ -70,18 +70,94 @@ struct PieceCache {
     int stride;  // blockDim.x
 };
 
+// Reductions into a brick-layout image: a lane's consecutive visits that fall into
+// one 16-byte brick half are summed in registers and sent as one
+// red.global.add.v4.f32 (slots of the half it did not visit add 0).
+struct HalfRed {
+    float* base;
+    int half = -1;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+    __device__ __forceinline__ void add(int q, float v)
+    {
+        const int h = q >> 2;
+        if (h != half) {
+            flush();
+            half = h;
+        }
+        const int slot = q & 3;
+        v0 += slot == 0 ? v : 0.f;
+        v1 += slot == 1 ? v : 0.f;
+        v2 += slot == 2 ? v : 0.f;
+        v3 += slot == 3 ? v : 0.f;
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if (half >= 0)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(base + 4LL * half), "f"(v0), "f"(v1),
+                         "f"(v2), "f"(v3)
+                         : "memory");
+        half = -1;
+        v0 = v1 = v2 = v3 = 0.f;
+    }
+};
+
+// Gathers from a brick-layout image: the 16-byte brick half of the last gather
+// stays in registers, so a lane's consecutive pieces within one half cost one
+// 16-byte load.
+struct HalfGather {
+    const float4* base;
+    int half = -1;
+    float4 v;
+    __device__ __forceinline__ float get(int q)
+    {
+        const int h = q >> 2;
+        if (h != half) {
+            v = __ldg(base + h);
+            half = h;
+        }
+        const int slot = q & 3;
+        return slot == 0 ? v.x : (slot == 1 ? v.y : (slot == 2 ? v.z : v.w));
+    }
+};
+
+// One event of the exact projector over images in the brick layout (one grid,
+// FP32 gathers): the same pieces and masses as the linear pass; the gathers read
+// 16-byte brick halves and the reductions go out per brick half.
+template <class TailF>
+__device__ __forceinline__ float do_event_brick(const PassArgs& a, const Event& e, const GridDev& g,
+                                                const TailF& tail)
+{
+    Line ln;
+    Walk w;
+    w.valid = false;
+    if (event_line(e, ln)) w = make_walk(g, ln, -a.tof.half_window, a.tof.half_window);
+    const float hin = a.tof.half_inv_norm;
+    const BrickIndex bi(w, a.brick_bx, a.brick_by);
+    HalfGather hg{reinterpret_cast<const float4*>(a.lam)};
+    float p = 0.f;
+    walk_index<true>(g, tail, w, bi, [&](int q, float m) { p = fmaf(m, hg.get(q), p); });
+    p *= hin;
+    if (!(p > 0.f)) return 0.f;
+    const float r = e.w / p * hin;
+    HalfRed hr{a.C};
+    walk_index<true>(g, tail, w, bi, [&](int q, float m) { hr.add(q, m * r); });
+    hr.flush();
+    return e.w;
+}
+
 // One event; returns the weight it adds to N_eff (0 when p_i = 0).
-template <int Kind, int Fmt, bool Cached, class TailF>
+template <int Kind, int Fmt, bool Cached, bool Brick, class TailF>
 __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& t, long long i, bool bf16,
                                           const PieceCache& pc, const TailF& tail, int& region)
 {
     region = find_region(t, i);
     const GridDev& g = t.grid[region];
     Event e = load_event<Fmt>(a, i);
-    float3 c, u;
+    if constexpr (Brick) return do_event_brick(a, e, g, tail);
+    Line ln;
     Walk w;
     w.valid = false;
-    if (event_line(e, c, u)) w = make_walk(g, c, u, -a.tof.half_window, a.tof.half_window);
+    if (event_line(e, ln)) w = make_walk(g, ln, -a.tof.half_window, a.tof.half_window);
     // the walk hands over 2 [Phi(b) - Phi(a)] per piece; half_inv_norm turns it
     // into the TOF mass, applied once to p_i and once to r_i
     const float hin = a.tof.half_inv_norm;
@@ -128,7 +204,7 @@ struct TailOf {
                                            typename std::conditional<TailK == TAIL_ERFC, TailErfc, TailSeries>::type>::type;
 };
 
-template <int Kind, int Fmt, bool Persistent, bool Cached, int TailK>
+template <int Kind, int Fmt, bool Persistent, bool Cached, int TailK, bool Brick = false>
 __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl, int chunk, int cap)
 {
     __shared__ SharedTable t;
@@ -160,7 +236,7 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
             const long long end = min((long long)start + chunk, a.n);
             for (long long i = (long long)start + lane; i < end; i += 32) {
                 int r;
-                float w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, tail, r);
+                float w = do_event<Kind, Fmt, Cached, Brick>(a, t, i, bf16, pc, tail, r);
                 if (Kind == PASS_FUSED && w != 0.f) atomicAdd(&neff[r], w);
             }
         }
@@ -170,7 +246,7 @@ __global__ void __launch_bounds__(256) k_event_pass(PassArgs a, RegionTable tbl,
         const long long i = (long long)b * blockDim.x + threadIdx.x;
         int r = 0;
         float w = 0.f;
-        if (i < a.n) w = do_event<Kind, Fmt, Cached>(a, t, i, bf16, pc, tail, r);
+        if (i < a.n) w = do_event<Kind, Fmt, Cached, Brick>(a, t, i, bf16, pc, tail, r);
         if (Kind == PASS_FUSED) add_neff(neff, r, w);
     }
     if (Kind == PASS_FUSED) {
@@ -250,47 +326,6 @@ __device__ __forceinline__ LutLine lut_line(const GridDev& g, const Event& e)
 // Visit (voxel, summed weight) of every run of consecutive samples that share
 // a voxel inside the grid.  NS > 0: the sample count known at compile time (the
 // loop unrolls and the table entries become constant operands); 0: lut.n.
-// 2x2x2-voxel bricks: with bx = ceil(nx/2) and by = ceil(ny/2) bricks per row and
-// per plane, brick (ix/2, iy/2, iz/2) holds its 8 voxels contiguously in the order
-// (ix & 1) + 2 (iy & 1) + 4 (iz & 1): one 32-byte sector, split by the z parity into
-// two 16-byte halves.  Every index of a voxel inside the grid is below
-// 8 bx by ceil(nz/2).
-__device__ __forceinline__ int brick_index(int ix, int iy, int iz, int bx, int by)
-{
-    return ((((iz >> 1) * by + (iy >> 1)) * bx + (ix >> 1)) << 3) | ((iz & 1) << 2) | ((iy & 1) << 1) | (ix & 1);
-}
-
-// Reductions into a brick-layout image: a lane's consecutive visits that fall into
-// one 16-byte brick half are summed in registers and sent as one
-// red.global.add.v4.f32 (slots of the half it did not visit add 0).
-struct HalfRed {
-    float* base;
-    int half = -1;
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-    __device__ __forceinline__ void add(int q, float v)
-    {
-        const int h = q >> 2;
-        if (h != half) {
-            flush();
-            half = h;
-        }
-        const int slot = q & 3;
-        v0 += slot == 0 ? v : 0.f;
-        v1 += slot == 1 ? v : 0.f;
-        v2 += slot == 2 ? v : 0.f;
-        v3 += slot == 3 ? v : 0.f;
-    }
-    __device__ __forceinline__ void flush()
-    {
-        if (half >= 0)
-            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(base + 4LL * half), "f"(v0), "f"(v1),
-                         "f"(v2), "f"(v3)
-                         : "memory");
-        half = -1;
-        v0 = v1 = v2 = v3 = 0.f;
-    }
-};
-
 // Samples of one line; consecutive samples in one voxel are merged into one visit
 // (voxel index, summed weight).  Brick: the index is the voxel's place in the brick
 // layout (bx, by bricks per row and plane) instead of the linear one.
@@ -448,6 +483,17 @@ template <int Kind, int Fmt, int TailK>
 cudaError_t launch_tail(int blocks, const LaunchCfg& cfg, const PassArgs& a, const RegionTable& tbl, cudaStream_t s)
 {
     const bool persistent = cfg.blocks_per_sm > 0;
+    if (a.brick_bx > 0) {
+        // brick layout: fused pass over one grid, FP32 gathers, flat grid, no piece cache
+        if (Kind != PASS_FUSED || tbl.n != 1 || a.lam_bf16 || tbl.grid[0].vox_offset != 0 || persistent ||
+            cfg.cache > 0)
+            return cudaErrorInvalidValue;
+        if constexpr (Kind == PASS_FUSED) {
+            k_event_pass<PASS_FUSED, Fmt, false, false, TailK, true><<<blocks, cfg.threads, 0, s>>>(a, tbl, cfg.chunk,
+                                                                                                   cfg.cache);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (Kind == PASS_FUSED) {
         if (cfg.cache > 0) {
             if (persistent) return launch_variant<Kind, Fmt, true, true, TailK>(blocks, cfg, a, tbl, s);

@@ -12,28 +12,90 @@ namespace {
 
 constexpr int kImgThreads = 256;
 
-// s_j += L_lj: full chord of each LOR through the grid, no TOF (sensitivity,
-// Sec. 2.4 "sensitive matrix"), accumulated in FP64.
-__global__ void __launch_bounds__(256) k_sensitivity(const float* __restrict__ lor, long long n, GridDev g,
+// s_j += L_lj: the chord of each LOR's line through the grid, no TOF
+// (sensitivity, Sec. 2.4 "sensitive matrix"), computed and accumulated in FP64.
+// The walk is the incremental Siddon walk of the event pass written in double:
+// clip the line M + t u to the grid box (slab method), find the voxel at the
+// entry point, then cross the nearest voxel plane at each step, plane positions
+// taken as first + m * step per axis, each axis crossed only as often as the
+// grid has voxels left in that direction.  In FP32 a crossing t = (X - M) / u_k
+// carries ulp(|X - M|) / |u_k| of rounding, which on a 2.4 m grid moves up to
+// ~1 mm of chord between neighbouring voxels for lines nearly parallel to a
+// plane; the sensitivity is computed once per scanner and grid, so it takes
+// FP64 throughout.
+__global__ void __launch_bounds__(256) k_sensitivity(const float* __restrict__ lor, long long n, GridD g,
                                                      double* __restrict__ s)
 {
     const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n) return;
-    float3 p1 = make_float3(lor[l], lor[n + l], lor[2 * n + l]);
-    float3 p2 = make_float3(lor[3 * n + l], lor[4 * n + l], lor[5 * n + l]);
-    float dx = p1.x - p2.x, dy = p1.y - p2.y, dz = p1.z - p2.z;
-    float D = sqrtf(dx * dx + dy * dy + dz * dz);
-    if (!(D > 0.f) || !(D < 1e30f)) return;
-    float inv = 1.f / D;
-    float3 u = make_float3(dx * inv, dy * inv, dz * inv);
-    float3 c = make_float3(0.5f * (p1.x + p2.x), 0.5f * (p1.y + p2.y), 0.5f * (p1.z + p2.z));
-    const float inf = __int_as_float(0x7f800000);
-    Walk w = make_walk(g, c, u, -inf, inf);
-    TofDev none{};
-    TailErfc unused{0.f};
-    walk<false>(g, none, unused, w, [&](int j, float len) {
-        if (len > 0.f) atomicAdd(s + j, (double)len);
-    });
+    double p1[3], p2[3];
+    for (int k = 0; k < 3; ++k) {
+        p1[k] = lor[(long long)k * n + l];
+        p2[k] = lor[(long long)(3 + k) * n + l];
+    }
+    const double dx = p1[0] - p2[0], dy = p1[1] - p2[1], dz = p1[2] - p2[2];
+    const double D = sqrt(dx * dx + dy * dy + dz * dz);
+    if (!(D > 0.0) || !(D < 1e300)) return;
+    const double u[3] = {dx / D, dy / D, dz / D};
+    const double c[3] = {0.5 * (p1[0] + p2[0]), 0.5 * (p1[1] + p2[1]), 0.5 * (p1[2] + p2[2])};
+    const double lo[3] = {g.ox, g.oy, g.oz};
+    const double v[3] = {g.vx, g.vy, g.vz};
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    double a = -inf, b = inf;
+    for (int k = 0; k < 3; ++k) {
+        const double hi = lo[k] + (double)nn[k] * v[k];
+        if (u[k] == 0.0) {
+            if (!(c[k] >= lo[k] && c[k] < hi)) return;
+        } else {
+            const double t0 = (lo[k] - c[k]) / u[k], t1 = (hi - c[k]) / u[k];
+            a = fmax(a, fmin(t0, t1));
+            b = fmin(b, fmax(t0, t1));
+        }
+    }
+    if (!(a < b)) return;
+    int idx[3], step[3];
+    double tnext[3], dt[3], rem[3];
+    for (int k = 0; k < 3; ++k) {
+        const double x = fma(a, u[k], c[k]);
+        const double fi = fmin(fmax(floor((x - lo[k]) / v[k]), 0.0), (double)(nn[k] - 1));
+        const int i = (int)fi;
+        idx[k] = i;
+        if (u[k] > 0.0) {
+            step[k] = 1;
+            tnext[k] = (lo[k] + (double)(i + 1) * v[k] - c[k]) / u[k];
+            dt[k] = v[k] / u[k];
+            rem[k] = (double)(nn[k] - 1 - i);
+        } else if (u[k] < 0.0) {
+            step[k] = -1;
+            tnext[k] = (lo[k] + (double)i * v[k] - c[k]) / u[k];
+            dt[k] = -v[k] / u[k];
+            rem[k] = (double)i;
+        } else {
+            step[k] = 0;
+            tnext[k] = inf;
+            dt[k] = 0.0;
+            rem[k] = 0.0;
+        }
+        if (rem[k] <= 0.0) tnext[k] = inf;
+    }
+    const double t_first[3] = {tnext[0], tnext[1], tnext[2]};
+    double m[3] = {0.0, 0.0, 0.0};
+    long long j = idx[0] + (long long)g.nx * (idx[1] + (long long)g.ny * idx[2]);
+    const long long sl[3] = {step[0], (long long)step[1] * g.nx, (long long)step[2] * g.nx * g.ny};
+    double tau = a;
+    const int max_steps = g.nx + g.ny + g.nz + 2;
+    for (int it = 0; it < max_steps; ++it) {
+        const double tmin = fmin(tnext[0], fmin(tnext[1], tnext[2]));
+        const double tn = fmax(fmin(tmin, b), tau);
+        if (tn > tau) atomicAdd(s + j, tn - tau);
+        if (tmin >= b) break;
+        tau = tn;
+        const int k = tnext[0] == tmin ? 0 : (tnext[1] == tmin ? 1 : 2);
+        j += sl[k];
+        m[k] += 1.0;
+        tnext[k] = m[k] < rem[k] ? fma(m[k], dt[k], t_first[k]) : inf;
+    }
 }
 
 // FP32 copy of s and per-block FP64 sums of s over the mask s > 0.
@@ -195,7 +257,7 @@ int grid_for(long long n, int threads, int cap = 148 * 32)
 
 }  // namespace
 
-cudaError_t launch_sensitivity(const float* lor6, long long n, const GridH& g, double* s_acc, cudaStream_t st)
+cudaError_t launch_sensitivity(const float* lor6, long long n, const GridD& g, double* s_acc, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     k_sensitivity<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(lor6, n, g, s_acc);

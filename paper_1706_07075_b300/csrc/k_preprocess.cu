@@ -24,13 +24,13 @@ __global__ void __launch_bounds__(256) k_preprocess(void* events, long long n, f
     if (i < n) {
         const Event e = Fmt == FMT_F32 ? load_event_f32(static_cast<const float4*>(events), i)
                                        : load_event_packed(static_cast<const int4*>(events), i, lattice);
-        float3 c, u;
+        Line ln;
         float line_mu = 0.f, comp = 0.f;
         keep = !(half_window > 0.f);
-        if (event_line(e, c, u)) {
+        if (event_line(e, ln)) {
             TofDev tof{};
             TailErfc tail{};
-            const Walk whole = make_walk(g, c, u, -1e30f, 1e30f);
+            const Walk whole = make_walk(g, ln, -1e30f, 1e30f);
             // a long LOR crosses hundreds of body voxels: compensated (two-sum)
             // accumulation keeps the integral to ~1 ulp instead of ~n/2 ulp
             walk<false>(g, tof, tail, whole, [&](int j, float L) {
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_preprocess(void* events, long long n, f
             });
             line_mu = __fadd_rn(line_mu, comp);
             if (half_window > 0.f) {
-                const Walk win = make_walk(g, c, u, -half_window, half_window);
+                const Walk win = make_walk(g, ln, -half_window, half_window);
                 walk<false>(g, tof, tail, win, [&](int j, float L) {
                     if (L > 0.f && __ldg(mu + j) > 0.f) keep = true;
                 });

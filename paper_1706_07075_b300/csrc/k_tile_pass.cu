@@ -62,10 +62,10 @@ __global__ void k_cell_codes(const void* __restrict__ ev, long long n, float lat
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const Event e = load_ev<Fmt>(ev, i, lattice);
-    float3 c, u;
+    Line ln;
     unsigned out = kCellNone;
-    if (event_line(e, c, u)) {
-        const float cc[3] = {c.x, c.y, c.z}, uu[3] = {u.x, u.y, u.z};
+    if (event_line(e, ln)) {
+        const float cc[3] = {ln.c.x, ln.c.y, ln.c.z}, uu[3] = {ln.u.x, ln.u.y, ln.u.z};
         const float o[3] = {t.ox, t.oy, t.oz}, v[3] = {t.vx, t.vy, t.vz};
         const int nn[3] = {t.nx, t.ny, t.nz}, nc[3] = {t.ncx, t.ncy, t.ncz};
         bool miss = false, fits = true;
@@ -353,9 +353,9 @@ __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, c
         // sweep reducing into the C tile
         for (long long i = e0 + threadIdx.x; i < e1; i += Threads) {
             const Event e = load_ev<Fmt>(a.events, i, a.lattice);
-            float3 c, u;
-            if (!event_line(e, c, u)) continue;
-            const Walk w = make_walk(tg, c, u, -hw, hw);
+            Line ln;
+            if (!event_line(e, ln)) continue;
+            const Walk w = make_walk(tg, ln, -hw, hw);
             float p = 0.f;
             walk<true>(tg, a.tof, tail, w, [&](int j, float m) { p = fmaf(m, lam_s[j], p); });
             p *= hin;
@@ -378,15 +378,15 @@ __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, c
         w.valid = false;
         if (have) {
             e = load_ev<Fmt>(a.events, i, a.lattice);
-            float3 c, u;
-            if (event_line(e, c, u)) {
-                const Walk whole = make_walk(tg, c, u, -hw, hw);
+            Line ln;
+            if (event_line(e, ln)) {
+                const Walk whole = make_walk(tg, ln, -hw, hw);
                 if (whole.valid) {
                     const float T = whole.tau_out - whole.tau_in;
                     const float ta = whole.tau_in + T * (0.125f * (float)lane8);
                     const float tb = lane8 == kLanesPerEvent - 1 ? whole.tau_out
                                                                  : whole.tau_in + T * (0.125f * (float)(lane8 + 1));
-                    if (ta < tb) w = make_walk(tg, c, u, ta, tb);
+                    if (ta < tb) w = make_walk(tg, ln, ta, tb);
                 }
             }
         }

@@ -2,6 +2,7 @@
 // stream-ordered execution with per-iteration CUDA graphs, the launch
 // autotuner and the region-divided reconstruction of Sec. 2.5.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -28,18 +29,24 @@ struct DevBuf {
     T* as() const { return static_cast<T*>(p); }
 };
 
+// Host-side fault injection (recon_debug_fail_alloc): when positive, the
+// countdown-th device allocation from now on fails as if the device were out of
+// memory.  Nothing is allocated for the failing request and no GPU work is done.
+std::atomic<long long> g_fail_alloc_countdown{0};
+
+// Grow b to at least `bytes`.  The new allocation is made before the old one is
+// released, so a failed growth leaves b (and whatever it holds) as it was.
 cudaError_t ensure(DevBuf& b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (b.p && b.bytes >= bytes) return cudaSuccess;
+    if (g_fail_alloc_countdown.load() > 0 && g_fail_alloc_countdown.fetch_sub(1) == 1)
+        return cudaErrorMemoryAllocation;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return e;
     if (b.p) cudaFree(b.p);
-    b.p = nullptr;
-    b.bytes = 0;
-    cudaError_t e = cudaMalloc(&b.p, bytes);
-    if (e != cudaSuccess) {
-        b.p = nullptr;
-        return e;
-    }
+    b.p = p;
     b.bytes = bytes;
     return cudaSuccess;
 }
@@ -128,6 +135,15 @@ struct recon_ctx {
     LaunchCfg cfg{192, 0, 0, 0, TAIL_SERIES};
     LaunchCfg last_cfg{192, 0, 0, 0, TAIL_SERIES};
     std::map<std::tuple<long long, int, long long, int>, LaunchCfg> tuned;
+    // image layout the autotuner chose for recon_mlem per (events, format, voxels):
+    // lanes 0 = the cell-ordered global-memory pass, 1 or 8 = the shared-memory tiled
+    // pass with that many threads per event; with the launch it was timed with
+    struct LayoutChoice {
+        int lanes;
+        LaunchCfg cfg;
+    };
+    std::map<std::tuple<long long, int, long long>, LayoutChoice> layout_tuned;
+    int last_tiling = 0, last_lanes = 1;   // layout of the last event pass (recon_get_launch)
     recon_stats stats{};
 
     // per-iteration graph
@@ -285,10 +301,25 @@ recon_status validate_events(recon_ctx* ctx, const recon_events* e)
 
 // After the resident events (or their weights) change: new generation (drops
 // graphs and cached region copies) and the weight total sum_i w_i.
+recon_status events_changed_sum(recon_ctx* ctx);
+
+// The resident events were rewritten: caches keyed on them go, and their total
+// weight is summed again.  If that fails the context holds no events.
 recon_status events_changed(recon_ctx* ctx)
 {
     ctx->ev_generation++;
     invalidate_graph(ctx);
+    recon_status s = events_changed_sum(ctx);
+    if (s != RECON_OK) {
+        ctx->have_ev = false;
+        ctx->n_ev = 0;
+        ctx->ev_generation++;
+    }
+    return s;
+}
+
+recon_status events_changed_sum(recon_ctx* ctx)
+{
     ctx->w_total = 0;
     const long long n = ctx->n_ev;
     if (n > 0) {
@@ -314,6 +345,11 @@ recon_status load_events(recon_ctx* ctx, const recon_events* e)
     const long long n = e->n;
     const bool packed = e->fmt == RECON_EV_PACKED_I16_F16;
     const size_t rec = packed ? 16 : 32;
+    // the resident events are replaced: until the new ones are in, the context holds none
+    ctx->have_ev = false;
+    ctx->n_ev = 0;
+    ctx->ev_generation++;
+    invalidate_graph(ctx);
     CK(ensure(ctx->ev, (size_t)n * rec));
     if (n > 0) {
         if (e->on_device) {
@@ -360,7 +396,7 @@ recon_status load_events(recon_ctx* ctx, const recon_events* e)
     ctx->lattice = packed ? e->lattice_mm : 0.0;
     ctx->n_ev = n;
     ctx->have_ev = true;
-    return events_changed(ctx);
+    return events_changed(ctx);   // drops the events again if their weights cannot be summed
 }
 
 recon_status finish_sensitivity(recon_ctx* ctx)
@@ -401,6 +437,8 @@ bool valid_cfg(const recon_launch* c)
     if (c->cached_pieces != 0 && (c->cached_pieces < 8 || c->cached_pieces > 256)) return false;
     if ((long long)c->cached_pieces * c->threads_per_block * 8 > 200 * 1024) return false;
     if (c->tail_eval != TAIL_FIT && c->tail_eval != TAIL_ERFC && c->tail_eval != TAIL_SERIES) return false;
+    if (c->reduction != 0 && c->reduction != 1) return false;
+    if (c->reduction == 1 && (c->blocks_per_sm != 0 || c->cached_pieces != 0)) return false;
     return true;
 }
 
@@ -457,7 +495,20 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
         {192, 0, 0, 0, TAIL_FIT}, {128, 8, 64, 0, TAIL_FIT}, {64, 0, 0, 64, TAIL_FIT},
         {128, 0, 0, 0, TAIL_ERFC}, {256, 0, 0, 0, TAIL_ERFC}, {128, 0, 0, 0, TAIL_SERIES},
         {256, 0, 0, 0, TAIL_SERIES}, {192, 0, 0, 0, TAIL_SERIES},
+        // brick copies of lambda and C with per-half vector reductions
+        {128, 0, 0, 0, TAIL_SERIES, 1}, {192, 0, 0, 0, TAIL_SERIES, 1}, {256, 0, 0, 0, TAIL_SERIES, 1},
+        {128, 0, 0, 0, TAIL_FIT, 1},
     };
+    // the brick form needs one grid at offset 0 and FP32 gathers; its candidates are
+    // timed with the two copy kernels around the pass
+    const bool brick_ok = a.lut.n == 0 && tbl.n == 1 && tbl.grid[0].vox_offset == 0 && !a.lam_bf16;
+    const recon_grid& gr = ctx->grid;
+    if (brick_ok) {
+        const size_t nb = (size_t)brick_voxels(gr.nx, gr.ny, gr.nz);
+        CK(ensure(ctx->lam_brick, sizeof(float) * nb));
+        CK(ensure(ctx->C_brick, sizeof(float) * nb));
+        CK(cudaMemsetAsync(ctx->C_brick.p, 0, sizeof(float) * nb, ctx->stream));
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -471,19 +522,32 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
         // the persistent work queue takes events in list order, which a spread list must not
         if (spread && c.blocks_per_sm > 0) continue;
         if (c.tail == TAIL_SERIES && !series_ok(ctx)) continue;
+        if (c.reduction == 1 && !brick_ok) continue;
         float ms_min = 1e30f;
         PassArgs ac = a;
         if (spread) ac.block_mul = spread_multiplier(pass_blocks(c, a.n, ctx->num_sms));
+        PassArgs ab = ac;
+        if (c.reduction == 1) {
+            ab.lam = ctx->lam_brick.as<float>();
+            ab.C = ctx->C_brick.as<float>();
+            ab.brick_bx = (gr.nx + 1) / 2;
+            ab.brick_by = (gr.ny + 1) / 2;
+        }
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
             CK(cudaEventRecord(e0, ctx->stream));
-            CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, c, ac, tbl, ctx->num_sms, ctx->stream));
+            if (c.reduction == 1) {
+                CK(launch_to_bricks(ac.lam, ctx->lam_brick.as<float>(), gr.nx, gr.ny, gr.nz, ctx->stream));
+            }
+            CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, c, c.reduction == 1 ? ab : ac, tbl, ctx->num_sms,
+                           ctx->stream));
+            if (c.reduction == 1) CK(launch_from_bricks_add(ab.C, ac.C, gr.nx, gr.ny, gr.nz, ctx->stream));
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, e0, e1));
             ms_min = std::min(ms_min, ms);
-            ctx->stats.kernel_launches += 1;
+            ctx->stats.kernel_launches += c.reduction == 1 ? 3 : 1;
         }
         if (ms_min < best_ms) {
             best_ms = ms_min;
@@ -528,6 +592,7 @@ struct IterPlan {
     long long n_fb = 0;
     long long n_cell_events = 0;
     int tile_mode = 0;   // 1 shared-memory tiles, 2 cell-ordered global pass
+    int lanes = 1;       // threads per event of the shared-memory tiled pass (1 or 8)
 };
 
 // The fused event pass of one (sub-)iteration: the tiled pass over the binned
@@ -554,7 +619,7 @@ recon_status launch_event_pass_layout(recon_ctx* ctx, const IterPlan& p, const P
         if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
         CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, at, tc, ctx->num_sms, ctx->stream));
     } else {
-        CK(launch_tile_pass(at, p.th, p.list, p.n_list, p.tbegin, p.cfg.tail, ctx->tile_lanes, ctx->stream));
+        CK(launch_tile_pass(at, p.th, p.list, p.n_list, p.tbegin, p.cfg.tail, p.lanes, ctx->stream));
     }
     if (p.n_fb > 0) {
         PassArgs af = a;
@@ -640,7 +705,7 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
     std::string k(buf);
     snprintf(buf, sizeof buf, " lut %d med %p %lld %d sub %d tile %d %d %p %u %p %p %lld %lld %d bm %u br %d %p %p",
              p.a.lut.n, (void*)p.med, p.med_vox, p.max_nz, p.subsets, (int)p.tiled, p.tile_mode, (const void*)p.list,
-             p.n_list, p.ev_cell, p.ev_fb, p.n_fb, p.n_cell_events, ctx->tile_lanes, p.a.block_mul, (int)p.bricks,
+             p.n_list, p.ev_cell, p.ev_fb, p.n_fb, p.n_cell_events, p.lanes, p.a.block_mul, (int)p.bricks,
              ctx->lam_brick.p, ctx->C_brick.p);
     k += buf;
     for (int r = 0; r < p.tbl.n; ++r) {
@@ -1053,8 +1118,8 @@ recon_status recon_get_tof_samples(const recon_ctx* ctx, int32_t capacity, float
 recon_status recon_set_gather_bf16(recon_ctx* ctx, int32_t on)
 {
     CHECK_CTX();
+    if (on != 0) CK(ensure(ctx->lam_bf16, sizeof(uint16_t) * ctx->n_vox));
     ctx->bf16 = on != 0;
-    if (ctx->bf16) CK(ensure(ctx->lam_bf16, sizeof(uint16_t) * ctx->n_vox));
     invalidate_graph(ctx);
     return RECON_OK;
 }
@@ -1080,7 +1145,7 @@ recon_status recon_set_launch(recon_ctx* ctx, const recon_launch* cfg)
     if (!valid_cfg(cfg)) return fail(ctx, RECON_EINVAL, "invalid launch configuration");
     ctx->user_cfg = true;
     ctx->cfg = LaunchCfg{cfg->threads_per_block, cfg->blocks_per_sm, cfg->blocks_per_sm > 0 ? cfg->chunk_events : 0,
-                         cfg->cached_pieces, cfg->tail_eval};
+                         cfg->cached_pieces, cfg->tail_eval, cfg->reduction};
     return RECON_OK;
 }
 
@@ -1092,6 +1157,9 @@ recon_status recon_get_launch(const recon_ctx* ctx, recon_launch* out)
     out->chunk_events = ctx->last_cfg.chunk;
     out->cached_pieces = ctx->last_cfg.cache;
     out->tail_eval = ctx->last_cfg.tail;
+    out->reduction = ctx->last_cfg.reduction;
+    out->image_tiling = ctx->last_tiling;
+    out->lanes_per_event = ctx->last_lanes;
     return RECON_OK;
 }
 
@@ -1106,6 +1174,13 @@ recon_status recon_set_graphs(recon_ctx* ctx, int32_t on)
 {
     CHECK_CTX();
     ctx->graphs = on != 0;
+    return RECON_OK;
+}
+
+recon_status recon_debug_fail_alloc(int64_t n)
+{
+    if (n < 0) return RECON_EINVAL;
+    g_fail_alloc_countdown.store(n);
     return RECON_OK;
 }
 
@@ -1164,8 +1239,13 @@ recon_status recon_sensitivity(recon_ctx* ctx, const float* lor, int64_t n, int3
     CHECK_CTX();
     if (n < 0) return fail(ctx, RECON_EINVAL, "n is negative");
     if (n > 0 && !lor) return fail(ctx, RECON_EINVAL, "lor is NULL");
+    // the image is rewritten: until it is complete the context has none
+    ctx->have_sens = false;
+    ctx->sens_generation++;
+    invalidate_graph(ctx);
     CK(cudaMemsetAsync(ctx->s64.p, 0, sizeof(double) * ctx->n_vox, ctx->stream));
-    const GridH g = grid_h(ctx->grid);
+    const recon_grid& cg = ctx->grid;
+    const GridD g{cg.nx, cg.ny, cg.nz, cg.vx, cg.vy, cg.vz, cg.ox, cg.oy, cg.oz};
     if (n > 0) {
         if (on_device) {
             CK(launch_sensitivity(lor, n, g, ctx->s64.as<double>(), ctx->stream));
@@ -1195,6 +1275,9 @@ recon_status recon_set_sensitivity(recon_ctx* ctx, const double* sens, int32_t o
 {
     CHECK_CTX();
     if (!sens) return fail(ctx, RECON_EINVAL, "sens is NULL");
+    ctx->have_sens = false;
+    ctx->sens_generation++;
+    invalidate_graph(ctx);
     CK(cudaMemcpyAsync(ctx->s64.p, sens, sizeof(double) * ctx->n_vox,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     recon_status s = finish_sensitivity(ctx);
@@ -1272,6 +1355,8 @@ recon_status recon_forward(recon_ctx* ctx, const recon_events* events, const flo
     CK(launch_pass(PASS_FORWARD, (EventFmt)ctx->fmt, cfg, a, tbl, ctx->num_sms, ctx->stream));
     ctx->stats.kernel_launches += 1;
     ctx->last_cfg = cfg;
+    ctx->last_tiling = 0;
+    ctx->last_lanes = 1;
     CK(cudaMemcpyAsync(p_out, ctx->vec.p, sizeof(float) * ctx->n_ev, cudaMemcpyDefault, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return RECON_OK;
@@ -1301,6 +1386,8 @@ recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const
         CK(launch_pass(PASS_BACK, (EventFmt)ctx->fmt, cfg, a, tbl, ctx->num_sms, ctx->stream));
         ctx->stats.kernel_launches += 1;
         ctx->last_cfg = cfg;
+        ctx->last_tiling = 0;
+        ctx->last_lanes = 1;
     }
     CK(cudaMemcpyAsync(image_out, ctx->C.p, sizeof(float) * ctx->n_vox, cudaMemcpyDefault, ctx->stream));
     CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * ctx->n_vox, ctx->stream));
@@ -1484,6 +1571,32 @@ void plan_tiles(recon_ctx* ctx, IterPlan& p)
     p.n_fb = tp.n_fb;
     p.n_cell_events = tp.n_binned;
     p.tile_mode = tp.mode;
+    p.lanes = ctx->tile_lanes;
+}
+
+// Device time of one event pass of plan p (best of two); the pass accumulates
+// into C and the N_eff slots, which the caller clears.
+recon_status time_event_pass(recon_ctx* ctx, const IterPlan& p, float* ms_out)
+{
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaEventRecord(e0, ctx->stream));
+        recon_status s = launch_event_pass(ctx, p, p.a, p.tbl);
+        if (s != RECON_OK) return s;
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        best = std::min(best, ms);
+        ctx->stats.kernel_launches += 1 + (p.tiled && p.n_fb > 0 ? 1 : 0) + (p.bricks ? 2 : 0);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_out = best;
+    return RECON_OK;
 }
 
 // Host events and n_iter >= 1: the upload is streamed in chunks through two
@@ -1501,14 +1614,16 @@ recon_status begin_streamed_events(recon_ctx* ctx, const recon_events* e)
     recon_status s = validate_events(ctx, e);
     if (s != RECON_OK) return s;
     const bool packed = e->fmt == RECON_EV_PACKED_I16_F16;
+    ctx->have_ev = false;
+    ctx->n_ev = 0;
+    ctx->ev_generation++;
+    invalidate_graph(ctx);
     CK(ensure(ctx->ev, (size_t)e->n * (packed ? 16 : 32)));
     ctx->fmt = packed ? FMT_PACKED : FMT_F32;
     ctx->lattice = packed ? e->lattice_mm : 0.0;
     ctx->n_ev = e->n;
-    ctx->have_ev = true;
-    ctx->ev_generation++;
-    invalidate_graph(ctx);
     ctx->w_total = (double)e->n;   // unit weights (can_stream excludes caller weights)
+    // have_ev is set by recon_mlem once stream_pass has uploaded every chunk
     return RECON_OK;
 }
 
@@ -1574,13 +1689,25 @@ recon_status stream_pass(recon_ctx* ctx, const recon_events* e, const IterPlan& 
     return RECON_OK;
 }
 
-recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_iter, const float* init,
-                        float* image_out, double* conservation_out)
+}  // extern "C"
+
+namespace {
+
+// recon_event_pass: one event pass instead of n_iter iterations.
+struct PassOnly {
+    const float* image;   // start from this image (nullable)
+    bool from_start;      // start from 1 on {s > 0}
+    float* C_out;
+    double* n_eff_out;
+};
+
+recon_status mlem_impl(recon_ctx* ctx, const recon_events* events, int32_t n_iter, const float* init,
+                       float* image_out, double* conservation_out, const PassOnly* po)
 {
-    CHECK_CTX();
     if (n_iter < 0) return fail(ctx, RECON_EINVAL, "n_iter is negative");
     if ((long long)n_iter * ctx->subsets > (1LL << 24)) return fail(ctx, RECON_EINVAL, "n_iter x subsets too large");
-    const bool streamed = can_stream(ctx, events, n_iter) && ctx->have_sens && (init || ctx->start_mode == 0);
+    const bool streamed =
+        !po && can_stream(ctx, events, n_iter) && ctx->have_sens && (init || ctx->start_mode == 0);
     // event order / tiles (mode 2, cell order, is the default)
     const int mode = ctx->tile_mode;
     if (streamed) {
@@ -1591,9 +1718,16 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
         if (s != RECON_OK) return s;
     }
     if (!ctx->have_sens) return fail(ctx, RECON_ESTATE, "no sensitivity image (call recon_sensitivity first)");
-    if (!ctx->have_ev) return fail(ctx, RECON_ESTATE, "no events loaded");
+    if (!ctx->have_ev && !streamed) return fail(ctx, RECON_ESTATE, "no events loaded");
     const long long nv = ctx->n_vox;
-    if (init) {
+    if (po) {
+        if (po->from_start) {
+            CK(launch_fill_masked(ctx->lam.as<float>(), ctx->s32.as<float>(), nv, 1.f, ctx->stream));
+            ctx->stats.kernel_launches += 1;
+        } else if (po->image) {
+            CK(cudaMemcpyAsync(ctx->lam.p, po->image, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
+        }
+    } else if (init) {
         CK(cudaMemcpyAsync(ctx->lam.p, init, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
     } else if (ctx->start_mode == 1) {
         // starting backprojection: lambda0 = (sum_i a_ij w_i) / s_j on the mask, from a
@@ -1665,12 +1799,24 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     p.med = nullptr;
     p.med_vox = nv;
     p.max_nz = ctx->grid.nz;
-    p.bricks = ctx->bricks && ctx->lut_n > 0 && !ctx->bf16;
-    if (p.bricks) {
-        const size_t nb = (size_t)brick_voxels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
-        CK(ensure(ctx->lam_brick, sizeof(float) * nb));
-        CK(ensure(ctx->C_brick, sizeof(float) * nb));
-        CK(cudaMemsetAsync(ctx->C_brick.p, 0, sizeof(float) * nb, ctx->stream));
+    // image layout of the pass: brick copies for the sampled projector when asked
+    // for (recon_set_brick_layout), and for the exact projector when the launch
+    // says so (its reduction form; not with the shared-memory tiled pass)
+    auto set_layout = [&]() -> recon_status {
+        const bool exact_bricks = ctx->lut_n == 0 && p.cfg.reduction == 1 && !ctx->bf16 && p.cfg.blocks_per_sm == 0 &&
+                                  p.cfg.cache == 0 && !(p.tiled && p.tile_mode == 1);
+        p.bricks = (ctx->bricks && ctx->lut_n > 0 && !ctx->bf16) || exact_bricks;
+        if (p.bricks) {
+            const size_t nb = (size_t)brick_voxels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
+            CK(ensure(ctx->lam_brick, sizeof(float) * nb));
+            CK(ensure(ctx->C_brick, sizeof(float) * nb));
+            CK(cudaMemsetAsync(ctx->C_brick.p, 0, sizeof(float) * nb, ctx->stream));
+        }
+        return RECON_OK;
+    };
+    {
+        recon_status sl = set_layout();
+        if (sl != RECON_OK) return sl;
     }
     if (ctx->median) {
         CK(ensure(ctx->med, sizeof(float) * (size_t)nv));
@@ -1700,30 +1846,114 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
         p.cfg = c;
         p.pass_blocks = pass_blocks(p.cfg, ctx->n_ev, ctx->num_sms);
         ctx->last_cfg = c;
-        return RECON_OK;
+        return set_layout();
+    };
+    // The event list the iterations walk: binned into cell order (the default) or
+    // into shared-memory tiles.  With the autotuner on, the first call on a new
+    // (events, format, voxels) key of the exact projector also times the tiled pass
+    // with 1 and 8 threads per event against the tuned cell-ordered global pass, and
+    // keeps the faster layout and its launch for the key.
+    auto prepare_layout = [&]() -> recon_status {
+        TileH th1;
+        const bool can_tile = mode == 2 && ctx->autotune && !ctx->user_cfg && ctx->lut_n == 0 && p.subsets == 1 &&
+                              !ctx->bf16 && ctx->n_ev >= (1LL << 20) && tile_params(ctx, 1, &th1);
+        const auto lkey = std::make_tuple(ctx->n_ev, ctx->fmt, ctx->n_vox);
+        auto it = can_tile ? ctx->layout_tuned.find(lkey) : ctx->layout_tuned.end();
+        if (it != ctx->layout_tuned.end() && it->second.lanes > 0) {
+            recon_status s1 = prepare_tiles(ctx, 1);
+            if (s1 != RECON_OK) return s1;
+            plan_tiles(ctx, p);
+            p.lanes = it->second.lanes;
+            p.cfg = it->second.cfg;
+            p.pass_blocks = pass_blocks(p.cfg, ctx->n_ev, ctx->num_sms);
+            ctx->last_cfg = p.cfg;
+            return set_layout();
+        }
+        if (mode == 1 || mode == 2) {
+            recon_status s1 = prepare_tiles(ctx, mode);
+            if (s1 != RECON_OK) return s1;
+            plan_tiles(ctx, p);
+        }
+        recon_status s1 = retune();
+        if (s1 != RECON_OK) return s1;
+        if (!can_tile || it != ctx->layout_tuned.end()) return RECON_OK;
+        const LaunchCfg glob_cfg = p.cfg;
+        float t_glob = 0;
+        s1 = time_event_pass(ctx, p, &t_glob);
+        if (s1 != RECON_OK) return s1;
+        s1 = prepare_tiles(ctx, 1);
+        if (s1 != RECON_OK) return s1;
+        plan_tiles(ctx, p);
+        s1 = set_layout();
+        if (s1 != RECON_OK) return s1;
+        int best = 0;
+        float best_t = t_glob;
+        if (p.tiled && p.tile_mode == 1) {
+            for (int lanes : {1, 8}) {
+                p.lanes = lanes;
+                float t = 0;
+                s1 = time_event_pass(ctx, p, &t);
+                if (s1 != RECON_OK) return s1;
+                if (t < best_t) {
+                    best_t = t;
+                    best = lanes;
+                }
+            }
+        }
+        ctx->layout_tuned[lkey] = {best, glob_cfg};
+        CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
+        CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots, ctx->stream));
+        if (best > 0) {
+            p.lanes = best;
+            return RECON_OK;
+        }
+        s1 = prepare_tiles(ctx, 2);
+        if (s1 != RECON_OK) return s1;
+        plan_tiles(ctx, p);
+        p.cfg = glob_cfg;
+        p.pass_blocks = pass_blocks(p.cfg, ctx->n_ev, ctx->num_sms);
+        ctx->last_cfg = p.cfg;
+        return set_layout();
     };
     recon_status s;
+    if (po) {
+        // one pass over the resident events into C; C goes out, N_eff is summed, and
+        // C and the N_eff slots are left zero
+        s = prepare_layout();
+        if (s != RECON_OK) return s;
+        ctx->last_tiling = p.tiled && p.tile_mode == 1 ? 1 : 0;
+        ctx->last_lanes = ctx->last_tiling ? p.lanes : 1;
+        s = launch_event_pass(ctx, p, p.a, p.tbl);
+        if (s != RECON_OK) return s;
+        ctx->stats.kernel_launches += 1 + (p.tiled && p.n_fb > 0 ? 1 : 0) + (p.bricks ? 2 : 0);
+        CK(cudaMemcpyAsync(po->C_out, ctx->C.p, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
+        double n_eff = 0;
+        s = host_sum(ctx, ctx->pass_partial.as<double>(), kNeffSlots, &n_eff);
+        if (s != RECON_OK) return s;
+        if (po->n_eff_out) *po->n_eff_out = n_eff;
+        CK(cudaMemsetAsync(ctx->C.p, 0, sizeof(float) * nv, ctx->stream));
+        CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return RECON_OK;
+    }
     if (streamed) {
         s = stream_pass(ctx, events, p);
         if (s != RECON_OK) return s;
+        ctx->have_ev = true;
         if (n_iter > 1) {
-            if (mode == 1 || mode == 2) {
-                s = prepare_tiles(ctx, mode);
-                if (s != RECON_OK) return s;
-                plan_tiles(ctx, p);
-            }
-            s = retune();
+            s = prepare_layout();
             if (s != RECON_OK) return s;
         }
+        ctx->last_tiling = p.tiled && p.tile_mode == 1 ? 1 : 0;
+        ctx->last_lanes = ctx->last_tiling ? p.lanes : 1;
         s = run_iterations(ctx, p, n_iter - 1, false);
     } else {
-        if (n_iter > 0 && (mode == 1 || mode == 2)) {
-            s = prepare_tiles(ctx, mode);
-            if (s != RECON_OK) return s;
-            plan_tiles(ctx, p);
-            s = retune();
+        if (n_iter > 0) {
+            s = prepare_layout();
             if (s != RECON_OK) return s;
         }
+        ctx->last_tiling = p.tiled && p.tile_mode == 1 ? 1 : 0;
+        ctx->last_lanes = ctx->last_tiling ? p.lanes : 1;
         s = run_iterations(ctx, p, n_iter);
     }
     if (s != RECON_OK) return s;
@@ -1731,6 +1961,60 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
     if (conservation_out && n_iter > 0)
         CK(cudaMemcpyAsync(conservation_out, ctx->hist.p, sizeof(double) * 2 * (size_t)n_iter * p.subsets,
                            cudaMemcpyDefault, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RECON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_iter, const float* init,
+                        float* image_out, double* conservation_out)
+{
+    CHECK_CTX();
+    return mlem_impl(ctx, events, n_iter, init, image_out, conservation_out, nullptr);
+}
+
+recon_status recon_event_pass(recon_ctx* ctx, const recon_events* events, const float* image, int32_t from_start,
+                              float* C_out, double* n_eff_out)
+{
+    CHECK_CTX();
+    if (!C_out) return fail(ctx, RECON_EINVAL, "C_out is NULL");
+    if (ctx->subsets != 1) return fail(ctx, RECON_EINVAL, "recon_event_pass runs MLEM passes (one subset)");
+    const PassOnly po{image, from_start != 0, C_out, n_eff_out};
+    return mlem_impl(ctx, events, 1, nullptr, nullptr, nullptr, &po);
+}
+
+recon_status recon_update(recon_ctx* ctx, const float* C_in, float* image_out, double* sum_s_lambda_out)
+{
+    CHECK_CTX();
+    if (!C_in) return fail(ctx, RECON_EINVAL, "C_in is NULL");
+    if (!ctx->have_sens) return fail(ctx, RECON_ESTATE, "no sensitivity image (call recon_sensitivity first)");
+    const long long nv = ctx->n_vox;
+    const int bpr = update_blocks(nv);
+    CK(ensure(ctx->upd_partial, sizeof(double) * (size_t)bpr));
+    CK(ensure(ctx->reg_vox, sizeof(long long) * 2));
+    if (ctx->median) CK(ensure(ctx->med, sizeof(float) * (size_t)nv));
+    if (ctx->bf16) CK(ensure(ctx->lam_bf16, sizeof(uint16_t) * nv));
+    const long long rv[2] = {0, nv};
+    CK(cudaMemcpyAsync(ctx->reg_vox.p, rv, sizeof rv, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->C.p, C_in, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
+    uint16_t* bf = ctx->bf16 ? ctx->lam_bf16.as<uint16_t>() : nullptr;
+    CK(launch_update(ctx->lam.as<float>(), ctx->C.as<float>(), ctx->s32.as<float>(), bf, ctx->reg_vox.as<long long>(), 1,
+                     ctx->upd_partial.as<double>(), bpr, ctx->stream));
+    ctx->stats.kernel_launches += 1;
+    if (ctx->median) {
+        CK(launch_median3(ctx->lam.as<float>(), ctx->med.as<float>(), ctx->s32.as<float>(), bf,
+                          ctx->reg_vox.as<long long>(), 1, ctx->grid.nx, ctx->grid.ny, ctx->grid.nz, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->lam.p, ctx->med.p, sizeof(float) * (size_t)nv, cudaMemcpyDeviceToDevice, ctx->stream));
+        ctx->stats.kernel_launches += 1;
+    }
+    double ssum = 0;
+    recon_status s = host_sum(ctx, ctx->upd_partial.as<double>(), bpr, &ssum);
+    if (s != RECON_OK) return s;
+    if (sum_s_lambda_out) *sum_s_lambda_out = ssum;
+    if (image_out) CK(cudaMemcpyAsync(image_out, ctx->lam.p, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return RECON_OK;
 }
@@ -1940,6 +2224,8 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
         p.med = ctx->med.as<float>();
     }
     ctx->last_cfg = p.cfg;
+    ctx->last_tiling = 0;
+    ctx->last_lanes = 1;
     s = run_iterations(ctx, p, n_iter);
     if (s != RECON_OK) return s;
     // stitch into the context's whole-grid image

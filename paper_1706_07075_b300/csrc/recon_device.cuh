@@ -145,36 +145,87 @@ struct Walk {
     float t0x, t0y, t0z;      // tau of the first plane crossing per axis (inf if none inside the grid)
     float dtx, dty, dtz;      // tau between successive crossings per axis
     float rx, ry, rz;         // crossings per axis that stay inside the grid
+    int ix0, iy0, iz0;        // start voxel per axis
     bool valid;
 };
 
-// Set up the walk of segment [tau_lo, tau_hi] of the line through `c` with
-// unit direction `u` (tau measured from c).  Slab method for the box, then the
-// start voxel and the first crossing on each axis.  The first crossing is
-// expressed relative to c once, and later crossings as first + m * step, so
-// plane positions carry no accumulated rounding.  Each axis may be crossed
-// only as often as the grid has voxels left in that direction, so every index
-// the walk produces lies inside the grid whatever the rounding.
-__device__ __forceinline__ Walk make_walk(const GridDev& g, float3 c, float3 u, float tau_lo, float tau_hi)
+// The TOF point c = M + d u of an event as an unevaluated sum c + c_lo of two
+// FP32 numbers.  FP32 alone rounds c to ulp(|c|), ~6e-5 mm at 1 m; a line nearly
+// parallel to a voxel plane that passes closer than that to the plane would land
+// on the wrong side of it for much of its window.  The pair keeps c to ~1e-11 mm
+// relative to the planes (error-free sums and products, Dekker and Knuth; the
+// __f*_rn intrinsics keep the compiler from fusing them).
+struct Line {
+    float3 c, c_lo, u;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// c + c_lo = (p1 + p2) / 2 + d u along one axis.
+__device__ __forceinline__ void tof_point_axis(float p1, float p2, float d, float u, float& c, float& c_lo)
+{
+    float s, es;
+    two_sum(p1, p2, s, es);                                // p1 + p2 = s + es exactly
+    const float du = __fmul_rn(d, u);
+    const float edu = __fmaf_rn(d, u, -du);                // d u = du + edu exactly
+    float h, eh;
+    two_sum(__fmul_rn(0.5f, s), du, h, eh);                // halving is exact
+    c = h;
+    c_lo = __fadd_rn(eh, __fadd_rn(__fmul_rn(0.5f, es), edu));
+}
+
+// Line of an event: u = (P1 - P2)/|P1 - P2| and the TOF point c = M + d u as a
+// pair; returns false for a degenerate LOR.
+__device__ __forceinline__ bool event_line(const Event& e, Line& l)
+{
+    const float dx = e.p1.x - e.p2.x, dy = e.p1.y - e.p2.y, dz = e.p1.z - e.p2.z;
+    const float D = sqrtf(dx * dx + dy * dy + dz * dz);
+    if (!(D > 0.f) || !(D < 1e30f) || !(fabsf(e.d) < 1e30f)) return false;
+    const float inv = 1.f / D;
+    l.u = make_float3(dx * inv, dy * inv, dz * inv);
+    tof_point_axis(e.p1.x, e.p2.x, e.d, l.u.x, l.c.x, l.c_lo.x);
+    tof_point_axis(e.p1.y, e.p2.y, e.d, l.u.y, l.c.y, l.c_lo.y);
+    tof_point_axis(e.p1.z, e.p2.z, e.d, l.u.z, l.c.z, l.c_lo.z);
+    return true;
+}
+
+// Set up the walk of segment [tau_lo, tau_hi] of the line through c + c_lo
+// with unit direction u (tau measured from the TOF point).  Slab method for the
+// box, then the start voxel and the first crossing on each axis.  Every plane
+// position enters as (plane - c) - c_lo, a difference of nearby numbers, so the
+// side of a plane and the crossings keep the precision of the pair; the start
+// voxel is first estimated, then corrected by the sign of the position relative
+// to the estimated voxel's planes.  The first crossing is expressed relative to
+// c once, and later crossings as first + m * step, so plane positions carry no
+// accumulated rounding.  Each axis may be crossed only as often as the grid has
+// voxels left in that direction, so every index the walk produces lies inside
+// the grid whatever the rounding.
+__device__ __forceinline__ Walk make_walk(const GridDev& g, const Line& l, float tau_lo, float tau_hi)
 {
     Walk w;
     float a = tau_lo, b = tau_hi;
     const float lo[3] = {g.ox, g.oy, g.oz};
     const float v[3] = {g.vx, g.vy, g.vz};
     const int n[3] = {g.nx, g.ny, g.nz};
-    const float cc[3] = {c.x, c.y, c.z};
-    const float uu[3] = {u.x, u.y, u.z};
+    const float cc[3] = {l.c.x, l.c.y, l.c.z};
+    const float cl[3] = {l.c_lo.x, l.c_lo.y, l.c_lo.z};
+    const float uu[3] = {l.u.x, l.u.y, l.u.z};
     float inv_u[3];
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         inv_u[k] = 1.f / uu[k];
-        float hi = lo[k] + (float)n[k] * v[k];
+        const float hi = lo[k] + (float)n[k] * v[k];
         if (uu[k] == 0.f) {
-            ok = ok && (cc[k] >= lo[k]) && (cc[k] < hi);
+            ok = ok && ((cc[k] - lo[k]) + cl[k] >= 0.f) && ((cc[k] - hi) + cl[k] < 0.f);
         } else {
-            float t0 = (lo[k] - cc[k]) * inv_u[k];
-            float t1 = (hi - cc[k]) * inv_u[k];
+            const float t0 = ((lo[k] - cc[k]) - cl[k]) * inv_u[k];
+            const float t1 = ((hi - cc[k]) - cl[k]) * inv_u[k];
             a = fmaxf(a, fminf(t0, t1));
             b = fminf(b, fmaxf(t0, t1));
         }
@@ -190,16 +241,21 @@ __device__ __forceinline__ Walk make_walk(const GridDev& g, float3 c, float3 u, 
         const float x = fmaf(a, uu[k], cc[k]);
         float fi = floorf((x - lo[k]) / v[k]);
         fi = fminf(fmaxf(fi, 0.f), (float)(n[k] - 1));   // also maps NaN of an invalid walk to 0
+        // position at tau_in relative to the lower plane of voxel fi; one voxel down
+        // or up when it lies outside [0, v)
+        const float xl = lo[k] + fi * v[k];
+        const float r = fmaf(a, uu[k], (cc[k] - xl) + cl[k]);
+        fi += (r < 0.f && fi > 0.f) ? -1.f : ((r >= v[k] && fi < (float)(n[k] - 1)) ? 1.f : 0.f);
         const int i = (int)fi;
         idx[k] = i;
         if (uu[k] > 0.f) {
             step[k] = 1;
-            t0[k] = (lo[k] + (float)(i + 1) * v[k] - cc[k]) * inv_u[k];
+            t0[k] = (((lo[k] + (float)(i + 1) * v[k]) - cc[k]) - cl[k]) * inv_u[k];
             dt[k] = v[k] * inv_u[k];
             rem[k] = (float)(n[k] - 1 - i);
         } else if (uu[k] < 0.f) {
             step[k] = -1;
-            t0[k] = (lo[k] + (float)i * v[k] - cc[k]) * inv_u[k];
+            t0[k] = (((lo[k] + (float)i * v[k]) - cc[k]) - cl[k]) * inv_u[k];
             dt[k] = -v[k] * inv_u[k];
             rem[k] = (float)i;
         } else {
@@ -211,6 +267,9 @@ __device__ __forceinline__ Walk make_walk(const GridDev& g, float3 c, float3 u, 
         if (rem[k] <= 0.f) t0[k] = inf;
     }
     w.j0 = idx[0] + g.nx * (idx[1] + g.ny * idx[2]);
+    w.ix0 = idx[0];
+    w.iy0 = idx[1];
+    w.iz0 = idx[2];
     w.sxl = step[0];
     w.syl = step[1] * g.nx;
     w.szl = step[2] * g.nx * g.ny;
@@ -220,37 +279,75 @@ __device__ __forceinline__ Walk make_walk(const GridDev& g, float3 c, float3 u, 
     return w;
 }
 
-// Line of an event: c = M + d u and u; returns false for a degenerate LOR.
-__device__ __forceinline__ bool event_line(const Event& e, float3& c, float3& u)
+// Index of the current voxel as the walk steps: the linear index
+// ix + nx (iy + ny iz), stepped by +-1, +-nx, +-nx ny.
+struct LinearIndex {
+    int j, sx, sy, sz;
+    __device__ __forceinline__ explicit LinearIndex(const Walk& w) : j(w.j0), sx(w.sxl), sy(w.syl), sz(w.szl) {}
+    __device__ __forceinline__ int get() const { return j; }
+    __device__ __forceinline__ void step(bool bx, bool by, bool) { j += bx ? sx : (by ? sy : sz); }
+};
+
+// 2x2x2-voxel bricks: with bx = ceil(nx/2) and by = ceil(ny/2) bricks per row and
+// per plane, brick (ix/2, iy/2, iz/2) holds its 8 voxels contiguously in the order
+// (ix & 1) + 2 (iy & 1) + 4 (iz & 1): one 32-byte sector, split by the z parity into
+// two 16-byte halves.  Every index of a voxel inside the grid is below
+// 8 bx by ceil(nz/2).
+__device__ __forceinline__ int brick_index(int ix, int iy, int iz, int bx, int by)
 {
-    float dx = e.p1.x - e.p2.x, dy = e.p1.y - e.p2.y, dz = e.p1.z - e.p2.z;
-    float D = sqrtf(dx * dx + dy * dy + dz * dz);
-    if (!(D > 0.f) || !(D < 1e30f) || !(fabsf(e.d) < 1e30f)) return false;
-    float inv = 1.f / D;
-    u = make_float3(dx * inv, dy * inv, dz * inv);
-    c = make_float3(fmaf(e.d, u.x, 0.5f * (e.p1.x + e.p2.x)), fmaf(e.d, u.y, 0.5f * (e.p1.y + e.p2.y)),
-                    fmaf(e.d, u.z, 0.5f * (e.p1.z + e.p2.z)));
-    return true;
+    return ((((iz >> 1) * by + (iy >> 1)) * bx + (ix >> 1)) << 3) | ((iz & 1) << 2) | ((iy & 1) << 1) | (ix & 1);
 }
 
+// Index of the current voxel in the brick layout as the walk steps.  A step along
+// an axis either stays in the brick (the voxel's parity bit on that axis flips:
+// +-1, +-2, +-4) or enters the neighbouring brick (the brick index moves by one
+// brick, the bit flips back): +-(8 stride - unit) with stride 1, bx, bx by.  The
+// two alternate along an axis, so each axis keeps the delta of its next step and
+// the sum of both, and a step swaps the delta for sum - delta.
+struct BrickIndex {
+    int q, dx, dy, dz, ax, ay, az;
+    __device__ __forceinline__ static void axis(int bit, int dir, int unit, int stride, int& d, int& a)
+    {
+        const int inner = dir * unit, cross = dir * (8 * stride - unit);
+        d = dir == 0 ? 0 : ((bit != 0) == (dir > 0) ? cross : inner);
+        a = inner + cross;
+    }
+    __device__ __forceinline__ BrickIndex(const Walk& w, int bx, int by)
+    {
+        q = brick_index(w.ix0, w.iy0, w.iz0, bx, by);
+        const int sx = w.sxl > 0 ? 1 : (w.sxl < 0 ? -1 : 0);
+        const int sy = w.syl > 0 ? 1 : (w.syl < 0 ? -1 : 0);
+        const int sz = w.szl > 0 ? 1 : (w.szl < 0 ? -1 : 0);
+        axis(w.ix0 & 1, sx, 1, 1, dx, ax);
+        axis(w.iy0 & 1, sy, 2, bx, dy, ay);
+        axis(w.iz0 & 1, sz, 4, bx * by, dz, az);
+    }
+    __device__ __forceinline__ int get() const { return q; }
+    __device__ __forceinline__ void step(bool bx, bool by, bool bz)
+    {
+        q += bx ? dx : (by ? dy : dz);
+        dx = bx ? ax - dx : dx;
+        dy = by ? ay - dy : dy;
+        dz = bz ? az - dz : dz;
+    }
+};
+
 // Siddon walk over the voxel pieces of a prepared Walk.  `visit(j, a)` gets
-// the linear voxel index (relative to the grid) and, with Weighted = true, the
-// piece's tail difference a = (s_b - s_a) + (g_a - g_b) = 2 [Phi(b) - Phi(a)]
-// (tails from `tail`): the TOF mass is tof.half_inv_norm * a, a factor the
-// callers apply once per event instead of once per piece.  With Weighted =
-// false, a is the piece length in mm (sensitivity).  Each step crosses the
-// nearest plane; the axis update is
-// written without branches so that the lanes of a warp, which cross different
-// axes, stay converged.  The walk ends at tau_out (an axis with no crossing
-// left inside the grid has its next crossing at +inf), after at most
-// nx + ny + nz + 2 pieces.
-template <bool Weighted, class TailF, class Visit>
-__device__ __forceinline__ void walk(const GridDev& g, const TofDev& tof, const TailF& tail, const Walk& w,
-                                     Visit&& visit)
+// the voxel's index (linear or brick, from the Index stepper) and, with Weighted =
+// true, the piece's tail difference a = (s_b - s_a) + (g_a - g_b) = 2 [Phi(b) -
+// Phi(a)] (tails from `tail`): the TOF mass is tof.half_inv_norm * a, a factor the
+// callers apply once per event instead of once per piece.  With Weighted = false,
+// a is the piece length in mm (sensitivity).  Each step crosses the nearest
+// plane; the axis update is written without branches so that the lanes of a
+// warp, which cross different axes, stay converged.  The walk ends at tau_out (an
+// axis with no crossing left inside the grid has its next crossing at +inf),
+// after at most nx + ny + nz + 2 pieces.
+template <bool Weighted, class TailF, class Index, class Visit>
+__device__ __forceinline__ void walk_index(const GridDev& g, const TailF& tail, const Walk& w, Index idx,
+                                           Visit&& visit)
 {
     if (!w.valid) return;
     const float inf = __int_as_float(0x7f800000);
-    int j = w.j0;
     float mx = 0.f, my = 0.f, mz = 0.f;
     float tx = w.t0x, ty = w.t0y, tz = w.t0z;
     float tau = w.tau_in;
@@ -273,13 +370,13 @@ __device__ __forceinline__ void walk(const GridDev& g, const TofDev& tof, const 
         } else {
             a = tn - tau;
         }
-        visit(j, a);
+        visit(idx.get(), a);
         if (last) break;
         tau = tn;
         const bool bx = tx == tmin;
         const bool by = !bx && ty == tmin;
         const bool bz = !bx && !by;
-        j += bx ? w.sxl : (by ? w.syl : w.szl);
+        idx.step(bx, by, bz);
         mx += bx ? 1.f : 0.f;
         my += by ? 1.f : 0.f;
         mz += bz ? 1.f : 0.f;
@@ -290,6 +387,14 @@ __device__ __forceinline__ void walk(const GridDev& g, const TofDev& tof, const 
         ty = by ? ny_ : ty;
         tz = bz ? nz_ : tz;
     }
+}
+
+// The walk over linear voxel indices.
+template <bool Weighted, class TailF, class Visit>
+__device__ __forceinline__ void walk(const GridDev& g, const TofDev&, const TailF& tail, const Walk& w,
+                                     Visit&& visit)
+{
+    walk_index<Weighted>(g, tail, w, LinearIndex(w), visit);
 }
 
 // Region code of one event (Sec. 2.5, Fig. 4): the TOF-estimated annihilation z,

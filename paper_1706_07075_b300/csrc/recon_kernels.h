@@ -64,6 +64,8 @@ struct LaunchCfg {
     int chunk;         // events per work-queue grab (persistent), multiple of 32
     int cache;         // pieces per thread kept in shared memory for the backprojection (0: walk twice)
     int tail;          // TailEval: how the Gaussian tails are evaluated
+    int reduction;     // 0: scalar reductions into the linear image; 1: lambda and C in 2x2x2-brick copies,
+                       // gathers of 16-byte brick halves and one vector reduction per brick half
 };
 
 struct PassArgs {
@@ -84,7 +86,7 @@ struct PassArgs {
                                  // region-ordered events over all regions at any moment
     LutH lut;                    // sampled TOF kernel (lut.n > 0) instead of the exact one
     int brick_bx, brick_by;      // > 0: lam and C are in the 2x2x2-brick layout with these bricks per row
-                                 // and plane (sampled fused pass over one grid, FP32 gathers)
+                                 // and plane (fused pass over one grid, FP32 gathers)
 };
 
 // Voxels of the 2x2x2-brick layout of an nx x ny x nz grid (8 per brick, the
@@ -124,9 +126,16 @@ size_t tile_smem_bytes(const TileH& t);
 cudaError_t launch_tile_pass(const PassArgs& a, const TileH& t, const unsigned* list, unsigned n_list,
                              const long long* begin, int tail, int lanes, cudaStream_t st);
 
-// Sensitivity: s[j] += chord length of each LOR (FP64 accumulation).  lor6: six
-// planes of n floats (device).
-cudaError_t launch_sensitivity(const float* lor6, long long n, const GridH& g, double* s_acc, cudaStream_t st);
+// Grid in FP64 (the sensitivity walk).
+struct GridD {
+    int nx, ny, nz;
+    double vx, vy, vz;
+    double ox, oy, oz;
+};
+
+// Sensitivity: s[j] += chord length of each LOR's line through the grid, walked and
+// accumulated in FP64.  lor6: six planes of n floats (device).
+cudaError_t launch_sensitivity(const float* lor6, long long n, const GridD& g, double* s_acc, cudaStream_t st);
 
 // FP32 copy of s64 and per-block FP64 sums of s over {s > 0} in partial[blocks].
 cudaError_t launch_sens_finish(const double* s64, long long n_vox, float* s32, double* partial, int blocks,

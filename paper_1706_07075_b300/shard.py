@@ -1,0 +1,45 @@
+"""Event-sharded list-mode MLEM over several ranks (one GPU per rank).
+
+Each rank keeps its shard of the events resident in its own context, with the
+same grid and the same sensitivity image.  An iteration is one event pass per
+rank (recon_event_pass), one sum of the C images over the ranks (an all-reduce,
+the only exchange of the iteration) and the same update on every rank
+(recon_update), so every rank holds the same image after every iteration.  The
+backprojection C_j = sum_i a_ij w_i / p_i is a sum over events, so the sum of the
+ranks' C is the C of the whole list and the iteration is MLEM over all events
+(Sec. 2.4); only the order of the FP32 sums differs.  The first pass starts
+from the image 1 on {s_j > 0}: MLEM's first update from any uniform image is the
+same, so the ranks need not agree on a start value.
+"""
+
+
+def sharded_mlem(ctx, n_iter, c_buf, allreduce_sum, image_out=None):
+    """n_iter MLEM iterations of this rank's context in step with the other ranks.
+
+    ctx: a binding.Context with this rank's events resident and the sensitivity
+    set.  c_buf: nx*ny*nz float32 buffer (host or device, wherever allreduce_sum
+    works).  allreduce_sum(c_buf, n_eff) sums c_buf over the ranks in place and
+    returns the summed n_eff.  Returns [(N_eff, sum_j s_j lambda_j)] per iteration
+    (both over all ranks' events)."""
+    history = []
+    for k in range(n_iter):
+        n_eff = ctx.event_pass(None, None, 1 if k == 0 else 0, c_buf)
+        n_eff = allreduce_sum(c_buf, n_eff)
+        ssum = ctx.update(c_buf, image_out if k == n_iter - 1 else None)
+        history.append((n_eff, ssum))
+    return history
+
+
+def torch_allreduce_sum(group=None):
+    """allreduce_sum over a torch.distributed process group (NCCL with device
+    buffers, gloo with host buffers)."""
+    import torch
+    import torch.distributed as dist
+
+    def fn(c_buf, n_eff):
+        dist.all_reduce(c_buf, group=group)
+        t = torch.tensor([float(n_eff)], dtype=torch.float64, device=c_buf.device)
+        dist.all_reduce(t, group=group)
+        return float(t.item())
+
+    return fn

@@ -107,11 +107,13 @@ def test_one_voxel_grid_closed_form():
 @pytest.mark.parametrize("cfg", [(64, 0, 0, 0, 0), (128, 0, 0, 0, 0), (256, 4, 32, 0, 0), (128, 16, 256, 0, 0),
                                  (256, 1, 1024, 0, 0), (128, 0, 0, 64, 0), (64, 6, 64, 64, 0), (128, 0, 0, 8, 0),
                                  (256, 2, 64, 96, 0), (128, 0, 0, 0, 1), (64, 4, 64, 32, 1), (192, 0, 0, 0, 2),
-                                 (128, 0, 0, 32, 2), (256, 4, 64, 0, 2)])
+                                 (128, 0, 0, 32, 2), (256, 4, 64, 0, 2), (128, 0, 0, 0, 2, 1), (192, 0, 0, 0, 0, 1),
+                                 (256, 0, 0, 0, 1, 1)])
 def test_launch_configurations_agree(ctx_tiny, cfg):
     # (128, 0, 0, 8) caches fewer pieces than most walks have: those events walk twice.
-    # The last field selects the piece-mass form: fitted tails (0), CUDA's erfcf tails
-    # (1), the midpoint Taylor series (2).
+    # The fifth field selects the piece-mass form: fitted tails (0), CUDA's erfcf tails
+    # (1), the midpoint Taylor series (2); a sixth field of 1 the brick-layout
+    # reductions.
     ctx, g = ctx_tiny
     ev, _ = tiny_inputs()
     ctx.set_launch(None)
@@ -121,7 +123,7 @@ def test_launch_configurations_agree(ctx_tiny, cfg):
     ctx.set_launch(*cfg)
     img = np.zeros(g.n_vox, np.float32)
     ctx.mlem(None, 2, None, img, None)
-    assert ctx.get_launch() == (cfg[0], cfg[1], cfg[2] if cfg[1] else 0, cfg[3], cfg[4])
+    assert ctx.get_launch() == (cfg[0], cfg[1], cfg[2] if cfg[1] else 0, cfg[3], cfg[4], cfg[5] if len(cfg) > 5 else 0)
     ctx.set_launch(None)
     assert rel_l2(img, ref) < {0: 1e-6, 1: 2e-6, 2: 5e-6}[cfg[4]]
 
@@ -250,3 +252,52 @@ def test_coarse_voxels_use_tail_masses():
         assert ctx.get_launch()[4] != 2
     assert rel_l2(lam, lam_ref) <= 1e-4
     assert max_rel_above(lam, lam_ref, 0.01) <= 1e-3
+
+
+def test_lines_a_few_ulps_from_a_voxel_plane():
+    # Transaxial and axial lines nearly parallel to a voxel plane, their endpoints a
+    # few FP32 ulps from it at |coordinate| up to 1 m: the side of the plane the TOF
+    # window runs on is decided by ~1e-5 mm.  The image takes another value on each
+    # side of every plane, so a window put on the wrong side changes p_i by tens of
+    # percent.  The kernel keeps the TOF point as a pair of FP32 numbers; every
+    # event must match the FP64 oracle.
+    g = workload_grid("fullbody")
+    rng = np.random.default_rng(71)
+    iz = np.arange(g.nz)[:, None, None]
+    iy = np.arange(g.ny)[None, :, None]
+    ix = np.arange(g.nx)[None, None, :]
+    lam = (1.0 + 0.5 * (iz % 2) + 0.25 * (iy % 2) + 0.125 * (ix % 2)).astype(np.float32).reshape(-1)
+    events = []
+    for _ in range(3000):
+        axis = int(rng.integers(0, 3))
+        lo = (g.ox, g.oy, g.oz)[axis]
+        v = (g.vx, g.vy, g.vz)[axis]
+        n = (g.nx, g.ny, g.nz)[axis]
+        Z = np.float32(lo + v * int(rng.integers(n // 4, n)))       # a plane away from the origin
+        m1, m2 = rng.integers(-3, 4, 2)
+        zs = []
+        for m in (m1, m2):
+            z = Z
+            for _ in range(abs(int(m))):
+                z = np.nextafter(z, np.float32(np.inf if m > 0 else -np.inf), dtype=np.float32)
+            zs.append(z)
+        phi = rng.uniform(0, 2 * np.pi)
+        half = rng.uniform(150.0, 280.0)
+        a, b = [k for k in range(3) if k != axis]
+        p1 = np.zeros(3, np.float32)
+        p2 = np.zeros(3, np.float32)
+        p1[axis], p2[axis] = zs
+        off = rng.uniform(-40, 40, 2)
+        p1[a], p1[b] = off[0] + half * np.cos(phi), off[1] + half * np.sin(phi)
+        p2[a], p2[b] = off[0] - half * np.cos(phi), off[1] - half * np.sin(phi)
+        events.append(np.concatenate([p1, p2, [np.float32(rng.uniform(-60, 60))]]))
+    ev = np.ascontiguousarray(np.array(events, np.float32).T)
+    with B.Context(geometry("fullbody"), grid_tuple(g), 300.0) as ctx:
+        p = np.zeros(ev.shape[1], np.float32)
+        ctx.forward(B.make_events(ev), lam, p)
+    p_ref = oracle.forward(g, ev.astype(np.float64), lam.astype(np.float64), SIGMA)
+    sel = p_ref > 0
+    assert sel.sum() > 0.9 * ev.shape[1]
+    assert np.array_equal(p > 0, p_ref > 0)
+    rel = np.abs(p[sel] - p_ref[sel]) / p_ref[sel]
+    assert rel.max() < 1e-4, f"{int(np.sum(rel > 1e-4))} events off, worst {rel.max():.3e}"

@@ -260,7 +260,9 @@ def test_lines_a_few_ulps_from_a_voxel_plane():
     # window runs on is decided by ~1e-5 mm.  The image takes another value on each
     # side of every plane, so a window put on the wrong side changes p_i by tens of
     # percent.  The kernel keeps the TOF point as a pair of FP32 numbers; every
-    # event must match the FP64 oracle.
+    # event must match the FP64 oracle.  Planes at least 100 mm from the origin: at
+    # the plane through 0 "a few ulps" are denormals (~1e-45 mm), a side that the
+    # FP64 oracle itself cannot resolve (-2.8e-45 + 1200 rounds to 1200).
     g = workload_grid("fullbody")
     rng = np.random.default_rng(71)
     iz = np.arange(g.nz)[:, None, None]
@@ -273,7 +275,9 @@ def test_lines_a_few_ulps_from_a_voxel_plane():
         lo = (g.ox, g.oy, g.oz)[axis]
         v = (g.vx, g.vy, g.vz)[axis]
         n = (g.nx, g.ny, g.nz)[axis]
-        Z = np.float32(lo + v * int(rng.integers(n // 4, n)))       # a plane away from the origin
+        Z = np.float32(0.0)
+        while abs(float(Z)) < 100.0:                                 # a plane away from the origin
+            Z = np.float32(lo + v * int(rng.integers(n // 4, n)))
         m1, m2 = rng.integers(-3, 4, 2)
         zs = []
         for m in (m1, m2):

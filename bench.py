@@ -66,10 +66,11 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="run the served-reconstruction workload (Poisson stream of mixed jobs) instead")
     ap.add_argument("--serve-jobs", type=int, default=200)
-    ap.add_argument("--shard", default="replicas", choices=["replicas", "events"],
-                    help="with N GPUs: replicas (each rank reconstructs its own 146M events, weak scaling) or "
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "events", "regions"],
+                    help="with N GPUs: replicas (each rank reconstructs its own 146M events, weak scaling), "
                          "events (one 146M-event job, each rank a shard of the events, one all-reduce of C per "
-                         "iteration, strong scaling)")
+                         "iteration, strong scaling) or regions (one job divided into the nine TOF body regions, "
+                         "each rank a consecutive block of regions, the stitched images summed once per job)")
     ap.add_argument("--serve-leg-jobs", type=int, default=60,
                     help="jobs of the bounded serving leg of the default line (0: no serving leg)")
     return ap.parse_args()
@@ -358,6 +359,7 @@ def run_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n_total):
     red = torch_allreduce_sum() if world > 1 else (lambda c, n_eff: n_eff)
     for _ in range(args.warmup):
         sharded_mlem(ctx, args.iters, c_buf, red)
+    ctx.reset_stats()
     sampler = ClockSampler(local)
     sampler.start()
     torch.cuda.synchronize(dev)
@@ -384,6 +386,50 @@ def run_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n_total):
                            sharding="each rank a shard of the events; one all-reduce of C (54 MB) per iteration"),
             "gpu_launches": int(ctx.get_stats()["kernel_launches"]), "clocks": clocks,
             "conservation_last": [float(x) for x in hist[-1]]}
+
+
+def run_region_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n):
+    """One full-body job divided into the nine TOF body regions (Sec. 2.5), each
+    rank a consecutive block of regions; every rank holds all events, and the
+    stitched images are summed once per job (NCCL)."""
+    import numpy as np
+    import torch
+    from paper_1706_07075_b300.shard import region_block, regions_mlem_sharded
+    from paper_1706_07075_b300.synth import FULLBODY_REGIONS
+    sigma = ctx.get_info()["sigma_mm"]
+    margin = 3.0 * sigma + 6.0
+    codes = np.zeros(n, np.uint8)
+    ctx.split_regions(None, FULLBODY_REGIONS, 0.0, 6.0, codes, None, None)
+    n_in = int(np.count_nonzero(codes != 0xFF))
+    del codes
+    img = torch.zeros(ctx.n_vox, dtype=torch.float32, device=dev)
+    red = (lambda t: torch.distributed.all_reduce(t)) if world > 1 else (lambda t: None)
+    step = lambda: regions_mlem_sharded(ctx, FULLBODY_REGIONS, margin, 6.0, args.iters, img, rank, world, red)  # noqa
+    for _ in range(args.warmup):
+        step()
+    ctx.reset_stats()
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = max_over_ranks(1e3 * (time.perf_counter() - t0))
+    lo, hi = region_block(len(FULLBODY_REGIONS), rank, world)
+    return {"metric": METRIC, "value": n_in * args.iters * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(args, n, world), parallelism=f"regions{world}",
+                           sharding="nine TOF body regions in consecutive blocks over the ranks; stitched images "
+                                    "summed once per job", events_in_regions=n_in,
+                           timing="host wall clock over the steps (each synchronises)"),
+            "regions_of_rank0": [lo, hi], "gpu_launches": int(ctx.get_stats()["kernel_launches"]), "clocks": clocks}
 
 
 def launch_record(ctx_cfg, layout):
@@ -723,9 +769,11 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    n = args.events if args.shard == "replicas" else args.events // world
+    # replicas: a job per rank; events: one job, each rank drawing its shard; regions:
+    # one job, every rank holding all of its events
+    n = args.events // world if args.shard == "events" else args.events
     t_gen = time.perf_counter()
-    ev = synth.events("fullbody", n, args.seed + rank)
+    ev = synth.events("fullbody", n, args.seed + (0 if args.shard == "regions" else rank))
     lors = synth.sensitivity_lors("fullbody", args.lors, args.seed)
     t_gen = time.perf_counter() - t_gen
 
@@ -751,8 +799,11 @@ def run_ours(args):
     az, pol = (int(x) for x in args.dir_bins.split(","))
     if args.cell_order or (az, pol) != (1, 1):
         ctx.set_event_order(args.cell_order or -1, az, pol)
-    if args.shard == "events":
-        line = run_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n * world)
+    if args.shard in ("events", "regions"):
+        if args.shard == "events":
+            line = run_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n * world)
+        else:
+            line = run_region_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n)
         if rank == 0:
             print(json.dumps(line), flush=True)
         ctx.close()

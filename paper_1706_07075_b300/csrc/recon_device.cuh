@@ -238,11 +238,12 @@ __device__ __forceinline__ Walk make_walk(const GridDev& g, const Line& l, float
     const float inf = __int_as_float(0x7f800000);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
+        // estimate of the start voxel (an approximate division is enough: the
+        // correction below decides it), then the position at tau_in relative to the
+        // lower plane of that voxel: one voxel down or up when it lies outside [0, v)
         const float x = fmaf(a, uu[k], cc[k]);
-        float fi = floorf((x - lo[k]) / v[k]);
+        float fi = floorf(__fdividef(x - lo[k], v[k]));
         fi = fminf(fmaxf(fi, 0.f), (float)(n[k] - 1));   // also maps NaN of an invalid walk to 0
-        // position at tau_in relative to the lower plane of voxel fi; one voxel down
-        // or up when it lies outside [0, v)
         const float xl = lo[k] + fi * v[k];
         const float r = fmaf(a, uu[k], (cc[k] - xl) + cl[k]);
         fi += (r < 0.f && fi > 0.f) ? -1.f : ((r >= v[k] && fi < (float)(n[k] - 1)) ? 1.f : 0.f);

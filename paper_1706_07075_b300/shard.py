@@ -1,4 +1,6 @@
-"""Event-sharded list-mode MLEM over several ranks (one GPU per rank).
+"""List-mode MLEM of one job over several ranks (one GPU per rank).
+
+Event sharding (sharded_mlem):
 
 Each rank keeps its shard of the events resident in its own context, with the
 same grid and the same sensitivity image.  An iteration is one event pass per
@@ -10,6 +12,12 @@ ranks' C is the C of the whole list and the iteration is MLEM over all events
 (Sec. 2.4); only the order of the FP32 sums differs.  The first pass starts
 from the image 1 on {s_j > 0}: MLEM's first update from any uniform image is the
 same, so the ranks need not agree on a start value.
+
+Region sharding (region_block, regions_mlem_sharded): the body regions of the
+TOF-assisted division (Sec. 2.5) are reconstructed independently, so each rank
+takes a consecutive block of them, reconstructs its slabs, and the whole-body
+image is the sum of the ranks' stitched images (each holds only its own slabs):
+one sum at the end, no exchange between iterations.
 """
 
 
@@ -43,3 +51,24 @@ def torch_allreduce_sum(group=None):
         return float(t.item())
 
     return fn
+
+
+def region_block(n_regions, rank, world):
+    """The consecutive regions [lo, hi) of rank `rank` (blocks as equal as the
+    count allows; a rank may get none when there are more ranks than regions)."""
+    lo = rank * n_regions // world
+    hi = (rank + 1) * n_regions // world
+    return lo, hi
+
+
+def regions_mlem_sharded(ctx, regions, margin_mm, shell_mm, n_iter, image, rank, world, allreduce_image):
+    """This rank's block of the regions, reconstructed and stitched into `image`
+    (nx*ny*nz float32, zero outside its slabs), then summed over the ranks by
+    allreduce_image(image).  Returns the block (lo, hi)."""
+    lo, hi = region_block(len(regions), rank, world)
+    if hi > lo:
+        ctx.mlem_regions(None, regions[lo:hi], margin_mm, shell_mm, n_iter, image)
+    else:
+        image.zero_() if hasattr(image, "zero_") else image.fill(0)
+    allreduce_image(image)
+    return lo, hi

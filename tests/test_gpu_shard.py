@@ -119,3 +119,63 @@ def test_event_pass_and_update_equal_one_mlem_iteration():
         with pytest.raises(B.ReconError):
             ctx.update(None)
     assert rel_l2(img, ref) <= 1e-5
+
+
+def _region_rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    try:
+        import torch
+        import torch.distributed as dist
+        from paper_1706_07075_b300 import binding as Bb
+        from paper_1706_07075_b300 import synth as S
+        from paper_1706_07075_b300.shard import regions_mlem_sharded
+        from gpu_common import geometry as geo, grid_tuple as gt, workload_grid as wg
+        torch.cuda.set_device(0)
+        dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+        ev = S.events("tiny", N_EVENTS, SEED, workers=1)
+        lors = S.sensitivity_lors("tiny", 400_000, SEED, workers=1)
+        g = wg("tiny")
+        with Bb.Context(geo("tiny"), gt(g), 300.0) as ctx:
+            ctx.sensitivity(lors)
+            ctx.load_events(Bb.make_events(ev))
+            img = torch.zeros(g.n_vox, dtype=torch.float32)
+            block = regions_mlem_sharded(ctx, REGIONS, MARGIN, 6.0, N_ITER, img, rank, world,
+                                         lambda t: dist.all_reduce(t))
+        q.put((rank, img.numpy().copy(), block, None))
+        dist.destroy_process_group()
+    except Exception as e:  # reported by the parent
+        q.put((rank, None, None, repr(e)))
+
+
+REGIONS = [(0, 16), (16, 32), (32, 48)]
+MARGIN = 3.0 * 19.0965 + 6.0
+
+
+def test_region_sharded_ranks_equal_one_context():
+    # regions split over two ranks (one and two regions), the stitched images summed
+    # once at the end over gloo: equal to one context that reconstructs all three
+    world = 2
+    mpc = mp.get_context("spawn")
+    q = mpc.Queue()
+    port = _free_port()
+    procs = [mpc.Process(target=_region_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in range(world)), key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=120)
+    for rank, img, block, err in res:
+        assert err is None, (rank, err)
+    assert [r[2] for r in res] == [(0, 1), (1, 3)]
+    ev = synth.events("tiny", N_EVENTS, SEED, workers=1)
+    lors = synth.sensitivity_lors("tiny", 400_000, SEED, workers=1)
+    g = workload_grid("tiny")
+    with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx:
+        ctx.sensitivity(lors)
+        one = np.zeros(g.n_vox, np.float32)
+        ctx.mlem_regions(B.make_events(ev), REGIONS, MARGIN, 6.0, N_ITER, one)
+    for rank, img, _, _ in res:
+        assert rel_l2(img, one) <= 1e-5
+    np.testing.assert_array_equal(res[0][1], res[1][1])

@@ -109,3 +109,16 @@ def test_two_gloo_ranks_give_mlem_over_all_events():
             assert n_eff == pytest.approx(w.sum())
             assert ssum == pytest.approx(n_eff, rel=1e-12)        # count conservation over all events
     np.testing.assert_array_equal(res[0][1], res[1][1])            # the ranks hold the same image
+
+
+
+def test_region_blocks_cover_every_region_once():
+    sys.path.insert(0, ROOT)
+    from paper_1706_07075_b300.shard import region_block
+    for n in (1, 2, 9, 10):
+        for world in (1, 2, 3, 4, 8, 16):
+            blocks = [region_block(n, r, world) for r in range(world)]
+            covered = [k for lo, hi in blocks for k in range(lo, hi)]
+            assert covered == list(range(n))
+            sizes = [hi - lo for lo, hi in blocks]
+            assert max(sizes) - min(sizes) <= 1

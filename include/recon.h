@@ -337,6 +337,16 @@ recon_status recon_set_autotune(recon_ctx* ctx, int32_t on);
  * do not exist and are not counted.  Errors: EINVAL (n < 0). */
 recon_status recon_debug_fail_alloc(int64_t n);
 
+/* Out-of-range accesses caught by the bounds-checked build of this library
+ * (librecon_check.so, compiled with RECON_BOUNDS_CHECK; the paper has no counterpart):
+ * every voxel index a walk produces (event passes, the tiled pass, pre-processing, the
+ * sensitivity) is checked against its image before use, and an index outside is counted
+ * and its walk ended instead of reading or writing out of range.  *count_out receives
+ * the number counted on the current device since the last call (and clears it), or -1
+ * in the normal build, which has no checks.  The check build stands in for a memory
+ * sanitizer, with no trap and no fault.  Errors: EINVAL (NULL count_out). */
+recon_status recon_debug_bounds_violations(int64_t* count_out);
+
 recon_status recon_get_info(const recon_ctx* ctx, recon_info* out);
 recon_status recon_get_stats(const recon_ctx* ctx, recon_stats* out);
 recon_status recon_reset_stats(recon_ctx* ctx);

@@ -109,6 +109,7 @@ SIGNATURES = {
     "recon_region_slab_voxels": (C.c_int, [_CTX, C.c_int32, C.POINTER(recon_region), C.c_double,
                                            C.POINTER(C.c_int64)]),
     "recon_debug_fail_alloc": (C.c_int, [C.c_int64]),
+    "recon_debug_bounds_violations": (C.c_int, [C.POINTER(C.c_int64)]),
     "recon_split_regions_noalloc": (C.c_int, [C.POINTER(recon_grid), C.POINTER(recon_events), C.c_int32,
                                               C.POINTER(recon_region), C.c_double, _VP, _VP, _VP, C.c_int64, _VP]),
 }
@@ -118,20 +119,25 @@ _lock = threading.Lock()
 
 
 def library_path():
-    return _build.LIB
+    """librecon.so, or with RECON_BOUNDS_CHECK=1 in the environment the bounds-checked
+    build librecon_check.so."""
+    return _build.CHECK_LIB if os.environ.get("RECON_BOUNDS_CHECK") == "1" else _build.LIB
 
 
 def load():
-    """Load librecon.so, building it first when a source is newer."""
+    """Load the library (library_path()), building it first when a source is newer."""
     global _lib
     with _lock:
         if _lib is None:
-            if not _build.up_to_date():
+            path = library_path()
+            checked = path == _build.CHECK_LIB
+            if not _build.up_to_date(path):
                 try:
-                    _build.build()
+                    _build.build(checked=checked)
                 except Exception as e:  # no CPU fallback: the CUDA library is the only path
-                    raise ReconError(RECON_ECUDA, f"librecon.so is missing and could not be built: {e}") from e
-            lib = C.CDLL(_build.LIB)
+                    raise ReconError(RECON_ECUDA, f"{os.path.basename(path)} is missing and could not be built: "
+                                                  f"{e}") from e
+            lib = C.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(lib, name)
                 fn.restype = res
@@ -434,6 +440,13 @@ def recon_region_slab_voxels(ctx, regions, margin_mm):
 def recon_debug_fail_alloc(n):
     """Make the n-th device allocation of the library from now on fail (0: disarm)."""
     return check(None, load().recon_debug_fail_alloc(int(n)))
+
+
+def recon_debug_bounds_violations():
+    """Out-of-range voxel indices caught since the last call (-1: normal build)."""
+    c = C.c_int64(0)
+    check(None, load().recon_debug_bounds_violations(C.byref(c)))
+    return c.value
 
 
 def recon_split_regions_noalloc(grid, events, regions, shell_mm, code_out, offsets_out, idx_out, idx_capacity,

@@ -16,6 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "librecon.so")
 OBJ_DIR = os.path.join(HERE, "_build")
+# bounds-checked build: every voxel index of the walks checked before use (RECON_BOUNDS_CHECK)
+CHECK_LIB = os.path.join(HERE, "librecon_check.so")
+CHECK_OBJ_DIR = os.path.join(HERE, "_build_check")
 CUDA = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -32,16 +35,17 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def _compile(src, verbose):
-    obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + ".o")
-    cmd = [NVCC] + ARCH + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
+def _compile(src, verbose, checked=False):
+    obj = os.path.join(CHECK_OBJ_DIR if checked else OBJ_DIR, os.path.basename(src)[:-3] + ".o")
+    cmd = [NVCC] + ARCH + FLAGS + (["-DRECON_BOUNDS_CHECK"] if checked else []) + \
+        (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
@@ -68,26 +72,29 @@ def build_probe(force=False):
     return PROBE_LIB
 
 
-def build(force=False, verbose=False):
-    """Compile and link librecon.so unless it is newer than every source."""
-    build_probe(force)
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OBJ_DIR, exist_ok=True)
+def build(force=False, verbose=False, checked=False):
+    """Compile and link librecon.so (checked: librecon_check.so, the bounds-checked
+    build) unless it is newer than every source."""
+    lib = CHECK_LIB if checked else LIB
+    if not checked:
+        build_probe(force)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(CHECK_OBJ_DIR if checked else OBJ_DIR, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), _sources()))
+        results = list(ex.map(lambda s: _compile(s, verbose, checked), _sources()))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [NVCC] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + [o for o, _ in results] + \
         ["-Xlinker", "-rpath," + os.path.join(CUDA, "lib64")]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -599,4 +599,8 @@ cudaError_t launch_pass(PassKind kind, EventFmt fmt, const LaunchCfg& cfg, const
     return launch_kind<PASS_BACK, FMT_PACKED>(cfg, a, tbl, num_sms, s);
 }
 
+// Out-of-range voxel indices the walks of this file skipped since the last call
+// (bounds-checked build; 0 otherwise).
+unsigned long long oob_count_event_pass() { return oob_take(); }
+
 }  // namespace recon

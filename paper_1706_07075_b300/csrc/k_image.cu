@@ -88,6 +88,9 @@ __global__ void __launch_bounds__(256) k_sensitivity(const float* __restrict__ l
     for (int it = 0; it < max_steps; ++it) {
         const double tmin = fmin(tnext[0], fmin(tnext[1], tnext[2]));
         const double tn = fmax(fmin(tmin, b), tau);
+#ifdef RECON_BOUNDS_CHECK
+        if (!index_ok(j, (long long)g.nx * g.ny * g.nz)) break;
+#endif
         if (tn > tau) atomicAdd(s + j, tn - tau);
         if (tmin >= b) break;
         tau = tn;
@@ -353,5 +356,9 @@ cudaError_t launch_event_weights(const float4* ev_f32, const int4* ev_packed, lo
     k_event_weights<<<grid_for(n, kImgThreads), kImgThreads, 0, st>>>(ev_f32, ev_packed, n, out);
     return cudaGetLastError();
 }
+
+// Out-of-range voxel indices the walks of this file skipped since the last call
+// (bounds-checked build; 0 otherwise).
+unsigned long long oob_count_image() { return oob_take(); }
 
 }  // namespace recon

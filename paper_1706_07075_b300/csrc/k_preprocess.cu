@@ -83,4 +83,8 @@ cudaError_t launch_preprocess(void* events, int fmt, long long n, float lattice,
     return cudaGetLastError();
 }
 
+// Out-of-range voxel indices the walks of this file skipped since the last call
+// (bounds-checked build; 0 otherwise).
+unsigned long long oob_count_preprocess() { return oob_take(); }
+
 }  // namespace recon

@@ -557,4 +557,8 @@ cudaError_t launch_tile_pass(const PassArgs& a, const TileH& t, const unsigned* 
     return launch_tile_lanes<kLanesPerEvent>(a, t, list, n_list, begin, fit, st);
 }
 
+// Out-of-range voxel indices the walks of this file skipped since the last call
+// (bounds-checked build; 0 otherwise).
+unsigned long long oob_count_tile_pass() { return oob_take(); }
+
 }  // namespace recon

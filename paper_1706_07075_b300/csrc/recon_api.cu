@@ -12,6 +12,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "recon.h"
 #include "recon_kernels.h"
@@ -21,6 +22,15 @@ using namespace recon;
 namespace {
 
 thread_local std::string g_create_error;
+
+// A named NVTX range over a scope: entry points and their phases show up on a
+// profiler's timeline (no cost beyond a test when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct DevBuf {
     void* p = nullptr;
@@ -489,6 +499,7 @@ unsigned spread_multiplier(long long blocks)
 
 recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, LaunchCfg* best)
 {
+    NvtxRange nvtx_range("autotune");
     // flat and persistent grids, walking twice or replaying a shared-memory piece cache
     const std::vector<LaunchCfg> cands = {
         {128, 0, 0, 0, TAIL_FIT}, {256, 0, 0, 0, TAIL_FIT}, {96, 0, 0, 0, TAIL_FIT},
@@ -719,6 +730,7 @@ std::string plan_key(const recon_ctx* ctx, const IterPlan& p)
 // Run n_iter iterations of the plan: graph replay, or direct launches (timing).
 recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool reset_counter = true)
 {
+    NvtxRange nvtx_range("iterations");
     if (reset_counter) CK(cudaMemsetAsync(p.iter, 0, sizeof(int), ctx->stream));
     if (n_iter == 0) return RECON_OK;
     const bool legacy = ctx->stream == nullptr || ctx->stream == cudaStreamLegacy || ctx->stream == cudaStreamPerThread;
@@ -1084,6 +1096,7 @@ recon_status recon_set_median_filter(recon_ctx* ctx, int32_t on)
 recon_status recon_median_filter(recon_ctx* ctx, const float* image_in, float* image_out)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_median_filter");
     if (!image_in || !image_out) return fail(ctx, RECON_EINVAL, "image_in and image_out are required");
     const size_t bytes = sizeof(float) * (size_t)ctx->n_vox;
     // staged through context scratch (vec: input, med: output), so in and out may alias
@@ -1177,6 +1190,19 @@ recon_status recon_set_graphs(recon_ctx* ctx, int32_t on)
     return RECON_OK;
 }
 
+recon_status recon_debug_bounds_violations(int64_t* count_out)
+{
+    if (!count_out) return RECON_EINVAL;
+#ifdef RECON_BOUNDS_CHECK
+    const unsigned long long c =
+        oob_count_event_pass() + oob_count_tile_pass() + oob_count_preprocess() + oob_count_image();
+    *count_out = (int64_t)c;
+#else
+    *count_out = -1;
+#endif
+    return RECON_OK;
+}
+
 recon_status recon_debug_fail_alloc(int64_t n)
 {
     if (n < 0) return RECON_EINVAL;
@@ -1237,6 +1263,7 @@ recon_status recon_reset_stats(recon_ctx* ctx)
 recon_status recon_sensitivity(recon_ctx* ctx, const float* lor, int64_t n, int32_t on_device, double* sens_out)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_sensitivity");
     if (n < 0) return fail(ctx, RECON_EINVAL, "n is negative");
     if (n > 0 && !lor) return fail(ctx, RECON_EINVAL, "lor is NULL");
     // the image is rewritten: until it is complete the context has none
@@ -1274,6 +1301,7 @@ recon_status recon_sensitivity(recon_ctx* ctx, const float* lor, int64_t n, int3
 recon_status recon_set_sensitivity(recon_ctx* ctx, const double* sens, int32_t on_device)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_set_sensitivity");
     if (!sens) return fail(ctx, RECON_EINVAL, "sens is NULL");
     ctx->have_sens = false;
     ctx->sens_generation++;
@@ -1289,6 +1317,7 @@ recon_status recon_set_sensitivity(recon_ctx* ctx, const double* sens, int32_t o
 recon_status recon_load_events(recon_ctx* ctx, const recon_events* events)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_load_events");
     return load_events(ctx, events);
 }
 
@@ -1296,6 +1325,7 @@ recon_status recon_preprocess(recon_ctx* ctx, const recon_events* events, const 
                               int32_t apply, float* weight_out, uint8_t* keep_out, int64_t* n_kept)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_preprocess");
     if (!mu_map) return fail(ctx, RECON_EINVAL, "mu_map is NULL");
     if (!(z_reject >= 0.0) || !(z_reject <= 10.0)) return fail(ctx, RECON_EINVAL, "z_reject must be in [0, 10]");
     if (events) {
@@ -1330,6 +1360,7 @@ recon_status recon_preprocess(recon_ctx* ctx, const recon_events* events, const 
 recon_status recon_forward(recon_ctx* ctx, const recon_events* events, const float* image, float* p_out)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_forward");
     if (events) {
         recon_status s = load_events(ctx, events);
         if (s != RECON_OK) return s;
@@ -1365,6 +1396,7 @@ recon_status recon_forward(recon_ctx* ctx, const recon_events* events, const flo
 recon_status recon_backproject(recon_ctx* ctx, const recon_events* events, const float* r, float* image_out)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_backproject");
     if (events) {
         recon_status s = load_events(ctx, events);
         if (s != RECON_OK) return s;
@@ -1466,6 +1498,7 @@ bool tile_params(const recon_ctx* ctx, int mode, TileH* out)
 // Bin the resident events by cell (cached per event generation and window).
 recon_status prepare_tiles(recon_ctx* ctx, int mode)
 {
+    NvtxRange nvtx_range("event order binning");
     TilePrep& tp = ctx->tile_prep;
     TileH t;
     if (!ctx->have_ev || ctx->n_ev <= 0 || !tile_params(ctx, mode, &t)) {
@@ -1629,6 +1662,7 @@ recon_status begin_streamed_events(recon_ctx* ctx, const recon_events* e)
 
 recon_status stream_pass(recon_ctx* ctx, const recon_events* e, const IterPlan& p)
 {
+    NvtxRange nvtx_range("streamed first pass");
     if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
     for (int k = 0; k < 2; ++k) {
         if (!ctx->copied[k]) CK(cudaEventCreateWithFlags(&ctx->copied[k], cudaEventDisableTiming));
@@ -1973,6 +2007,7 @@ recon_status recon_mlem(recon_ctx* ctx, const recon_events* events, int32_t n_it
                         float* image_out, double* conservation_out)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_mlem");
     return mlem_impl(ctx, events, n_iter, init, image_out, conservation_out, nullptr);
 }
 
@@ -1980,6 +2015,7 @@ recon_status recon_event_pass(recon_ctx* ctx, const recon_events* events, const 
                               float* C_out, double* n_eff_out)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_event_pass");
     if (!C_out) return fail(ctx, RECON_EINVAL, "C_out is NULL");
     if (ctx->subsets != 1) return fail(ctx, RECON_EINVAL, "recon_event_pass runs MLEM passes (one subset)");
     const PassOnly po{image, from_start != 0, C_out, n_eff_out};
@@ -1989,6 +2025,7 @@ recon_status recon_event_pass(recon_ctx* ctx, const recon_events* events, const 
 recon_status recon_update(recon_ctx* ctx, const float* C_in, float* image_out, double* sum_s_lambda_out)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_update");
     if (!C_in) return fail(ctx, RECON_EINVAL, "C_in is NULL");
     if (!ctx->have_sens) return fail(ctx, RECON_ESTATE, "no sensitivity image (call recon_sensitivity first)");
     const long long nv = ctx->n_vox;
@@ -2024,6 +2061,7 @@ recon_status recon_split_regions(recon_ctx* ctx, const recon_events* events, int
                                  uint8_t* code_out, int64_t* offsets_out, int32_t* idx_out)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_split_regions");
     recon_status s = validate_regions(ctx, n_regions, regions, margin_mm, shell_mm);
     if (s != RECON_OK) return s;
     if (events) {
@@ -2065,6 +2103,7 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
                                 float* image_out, float* region_images_out, double* conservation_out)
 {
     CHECK_CTX();
+    NvtxRange nvtx_range("recon_mlem_regions");
     if (n_iter < 0) return fail(ctx, RECON_EINVAL, "n_iter is negative");
     recon_status s = validate_regions(ctx, n_regions, regions, margin_mm, shell_mm);
     if (s != RECON_OK) return s;

@@ -26,6 +26,29 @@
 
 namespace recon {
 
+// Bounds-checked build (RECON_BOUNDS_CHECK, librecon_check.so): every voxel index a
+// walk produces is checked against its image before it is used; an index outside is
+// counted here and its walk ends, so nothing is read or written out of range.  One
+// counter per compiled file (internal linkage); oob_take() reads and clears it.
+#ifdef RECON_BOUNDS_CHECK
+static __device__ unsigned long long g_oob_count;
+static inline unsigned long long oob_take()
+{
+    unsigned long long v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_oob_count, sizeof v) != cudaSuccess) v = ~0ULL;
+    cudaMemcpyToSymbol(g_oob_count, &zero, sizeof zero);
+    return v;
+}
+__device__ __forceinline__ bool index_ok(long long j, long long limit)
+{
+    if (j >= 0 && j < limit) return true;
+    atomicAdd(&g_oob_count, 1ULL);
+    return false;
+}
+#else
+static inline unsigned long long oob_take() { return 0; }
+#endif
+
 using GridDev = GridH;
 using TofDev = TofH;
 
@@ -286,6 +309,7 @@ struct LinearIndex {
     int j, sx, sy, sz;
     __device__ __forceinline__ explicit LinearIndex(const Walk& w) : j(w.j0), sx(w.sxl), sy(w.syl), sz(w.szl) {}
     __device__ __forceinline__ int get() const { return j; }
+    __device__ __forceinline__ static long long limit(const GridDev& g) { return (long long)g.nx * g.ny * g.nz; }
     __device__ __forceinline__ void step(bool bx, bool by, bool) { j += bx ? sx : (by ? sy : sz); }
 };
 
@@ -324,6 +348,10 @@ struct BrickIndex {
         axis(w.iz0 & 1, sz, 4, bx * by, dz, az);
     }
     __device__ __forceinline__ int get() const { return q; }
+    __device__ __forceinline__ static long long limit(const GridDev& g)
+    {
+        return 8LL * ((g.nx + 1) / 2) * ((g.ny + 1) / 2) * ((g.nz + 1) / 2);
+    }
     __device__ __forceinline__ void step(bool bx, bool by, bool bz)
     {
         q += bx ? dx : (by ? dy : dz);
@@ -371,6 +399,9 @@ __device__ __forceinline__ void walk_index(const GridDev& g, const TailF& tail, 
         } else {
             a = tn - tau;
         }
+#ifdef RECON_BOUNDS_CHECK
+        if (!index_ok(idx.get(), Index::limit(g))) break;
+#endif
         visit(idx.get(), a);
         if (last) break;
         tau = tn;

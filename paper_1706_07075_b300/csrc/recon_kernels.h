@@ -192,4 +192,11 @@ cudaError_t launch_region_gather(const float4* ev_f32, const int4* ev_packed, co
                                  const int* idx, long long total, float4* out_f32, int4* out_packed,
                                  cudaStream_t st);
 
+// Bounds-checked build: out-of-range voxel indices skipped by the walks of each
+// compiled file since the last call (0 in the normal build).
+unsigned long long oob_count_event_pass();
+unsigned long long oob_count_tile_pass();
+unsigned long long oob_count_preprocess();
+unsigned long long oob_count_image();
+
 }  // namespace recon

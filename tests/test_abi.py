@@ -30,6 +30,20 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_checked_build_exports_every_declared_symbol():
+    # librecon_check.so, the bounds-checked build, has the same boundary
+    from paper_1706_07075_b300 import build as lib_build
+    lib = C.CDLL(lib_build.build(checked=True))
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_normal_build_reports_no_bounds_checks():
+    # the host-side query needs no device in the normal build: -1, no checks compiled in
+    if os.environ.get("RECON_BOUNDS_CHECK") != "1":
+        assert B.recon_debug_bounds_violations() == -1
+
+
 def test_binding_covers_every_declared_symbol():
     assert sorted(B.SIGNATURES) == declared_functions()
     for name in declared_functions():

@@ -376,15 +376,22 @@ def run_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n_total):
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
+    host_ms = 1e3 * (time.perf_counter() - t0)
     clocks = sampler.stop()
-    ms = max_over_ranks(max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0)))
+    gpu_ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(max(gpu_ms, host_ms))
     value = n_total * args.iters * args.steps / (ms / 1e3)
+    launches = int(ctx.get_stats()["kernel_launches"])
+    launch = launch_record(ctx.get_launch(), ctx.get_layout())
+    # the same GPU's recon_mlem on this rank's events, for comparison
+    mlem_ms = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters)) / args.steps
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(args, n_total, world), parallelism=f"events{world}",
                            sharding="each rank a shard of the events; one all-reduce of C (54 MB) per iteration"),
-            "gpu_launches": int(ctx.get_stats()["kernel_launches"]), "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks, "gpu_event_ms_per_step": gpu_ms / args.steps,
+            "launch": launch, "recon_mlem_ms_per_step_this_rank": mlem_ms,
             "conservation_last": [float(x) for x in hist[-1]]}
 
 
@@ -419,9 +426,15 @@ def run_region_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n):
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
+    host_ms = 1e3 * (time.perf_counter() - t0)
     clocks = sampler.stop()
-    ms = max_over_ranks(1e3 * (time.perf_counter() - t0))
+    ms = max_over_ranks(host_ms)
     lo, hi = region_block(len(FULLBODY_REGIONS), rank, world)
+    launches = int(ctx.get_stats()["kernel_launches"])
+    launch = list(ctx.get_launch())
+    # the whole division on this rank alone, for comparison
+    whole_ms = _timed_steps(stream, args.steps, lambda: ctx.mlem_regions(None, FULLBODY_REGIONS, margin, 6.0,
+                                                                          args.iters)) / args.steps
     return {"metric": METRIC, "value": n_in * args.iters * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -429,7 +442,8 @@ def run_region_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n):
                            sharding="nine TOF body regions in consecutive blocks over the ranks; stitched images "
                                     "summed once per job", events_in_regions=n_in,
                            timing="host wall clock over the steps (each synchronises)"),
-            "regions_of_rank0": [lo, hi], "gpu_launches": int(ctx.get_stats()["kernel_launches"]), "clocks": clocks}
+            "regions_of_rank0": [lo, hi], "gpu_launches": launches, "clocks": clocks, "launch": launch,
+            "all_regions_on_this_rank_ms_per_step": whole_ms}
 
 
 def launch_record(ctx_cfg, layout):

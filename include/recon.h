@@ -492,6 +492,17 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
                                 const recon_region* regions, double margin_mm, double shell_mm, int32_t n_iter,
                                 float* image_out, float* region_images_out, double* conservation_out);
 
+/* Block of regions for later recon_mlem_regions calls: only regions [first, first +
+ * count) of the division are reconstructed (count = 0, first = 0: all, the default).
+ * The split still uses every region, so an event shared with a region outside the
+ * block keeps its weight 1/2 (Sec. 2.5); the pass walks only the block's events, the
+ * other regions' slab images start and stay at 0, and image_out holds the block's
+ * slabs only.  For jobs whose regions are divided over ranks: the sum of the ranks'
+ * images is the whole-body image.  Errors: EINVAL (block outside [0, 64), or count 0
+ * with first != 0; a block past the division's last region fails in
+ * recon_mlem_regions). */
+recon_status recon_set_region_block(recon_ctx* ctx, int32_t first, int32_t count);
+
 /* Total voxels of the region slabs of a division (for sizing region_images_out). */
 recon_status recon_region_slab_voxels(const recon_ctx* ctx, int32_t n_regions, const recon_region* regions,
                                       double margin_mm, int64_t* n_vox_out);

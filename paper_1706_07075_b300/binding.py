@@ -106,6 +106,7 @@ SIGNATURES = {
                                       C.c_double, C.c_double, _VP, _VP, _VP]),
     "recon_mlem_regions": (C.c_int, [_CTX, C.POINTER(recon_events), C.c_int32, C.POINTER(recon_region),
                                      C.c_double, C.c_double, C.c_int32, _VP, _VP, _VP]),
+    "recon_set_region_block": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "recon_region_slab_voxels": (C.c_int, [_CTX, C.c_int32, C.POINTER(recon_region), C.c_double,
                                            C.POINTER(C.c_int64)]),
     "recon_debug_fail_alloc": (C.c_int, [C.c_int64]),
@@ -428,6 +429,10 @@ def recon_mlem_regions(ctx, events, regions, margin_mm, shell_mm, n_iter, image_
     return check(ctx, load().recon_mlem_regions(ctx, C.byref(events) if events is not None else None, len(regions),
                                                 arr, float(margin_mm), float(shell_mm), int(n_iter), ptr(image_out),
                                                 ptr(region_images_out), ptr(conservation_out)))
+
+
+def recon_set_region_block(ctx, first, count):
+    return check(ctx, load().recon_set_region_block(ctx, int(first), int(count)))
 
 
 def recon_region_slab_voxels(ctx, regions, margin_mm):

@@ -166,6 +166,7 @@ struct recon_ctx {
     long long sens_generation = 0;
 
     // shared-memory tiled pass (plain MLEM with the exact projector)
+    int region_first = 0, region_count = 0;  // recon_mlem_regions reconstructs this block (count 0: all)
     int tile_mode = 2;    // 0 load order, 1 shared-memory tiles, 2 cell order (default)
     int tile_min_events = 256;  // cells with fewer events take the global-memory pass
     int tile_lanes = 1;         // threads per event in the tiled pass (1 or 8)
@@ -2084,6 +2085,17 @@ recon_status recon_split_regions(recon_ctx* ctx, const recon_events* events, int
     return RECON_OK;
 }
 
+recon_status recon_set_region_block(recon_ctx* ctx, int32_t first, int32_t count)
+{
+    CHECK_CTX();
+    if (first < 0 || count < 0 || first + count > kMaxRegions || (count == 0 && first != 0))
+        return fail(ctx, RECON_EINVAL, "region block outside [0, 64) (count 0 needs first 0)");
+    ctx->region_first = first;
+    ctx->region_count = count;
+    invalidate_graph(ctx);
+    return RECON_OK;
+}
+
 recon_status recon_region_slab_voxels(const recon_ctx* ctx, int32_t n_regions, const recon_region* regions,
                                       double margin_mm, int64_t* n_vox_out)
 {
@@ -2203,12 +2215,17 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
     const std::vector<int>& lo = rp.lo;
     const std::vector<int>& hi = rp.hi;
     const std::vector<long long>& rv = rp.rv;
-    const long long total = off[R];
+    // the block of regions to reconstruct (recon_set_region_block): its events are a
+    // contiguous range of the region-ordered copy; the other regions start at 0 and stay 0
+    const int b0 = ctx->region_count > 0 ? ctx->region_first : 0;
+    const int b1 = ctx->region_count > 0 ? ctx->region_first + ctx->region_count : R;
+    if (b1 > R) return fail(ctx, RECON_EINVAL, "the region block reaches past the division's regions");
+    const long long total = off[b1] - off[b0];
     const long long nvt = rv[R];
     // start image: uniform on each slab's mask with sum s lambda = sum w of its events
     for (int r = 0; r < R; ++r)
         CK(launch_fill_masked(ctx->lam_reg.as<float>() + rv[r], ctx->s_reg.as<float>() + rv[r], rv[r + 1] - rv[r],
-                              rp.start[r], ctx->stream));
+                              r >= b0 && r < b1 ? rp.start[r] : 0.f, ctx->stream));
     ctx->stats.kernel_launches += R;
     CK(cudaMemsetAsync(ctx->C_reg.p, 0, sizeof(float) * nvt, ctx->stream));
     if (ctx->bf16) {
@@ -2218,14 +2235,15 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
     }
 
     IterPlan p;
-    p.a = base_args(ctx, ctx->ev_reg.p, total);
+    const size_t rec = ctx->fmt == FMT_PACKED ? 16 : 32;
+    p.a = base_args(ctx, static_cast<const char*>(ctx->ev_reg.p) + (size_t)off[b0] * rec, total);
     p.a.lam = ctx->lam_reg.as<float>();
     p.a.lam_bf16 = ctx->bf16 ? ctx->bf16_reg.as<uint16_t>() : nullptr;
     p.a.C = ctx->C_reg.as<float>();
     p.a.work = ctx->work.as<unsigned long long>();
     memset(&p.tbl, 0, sizeof p.tbl);
     p.tbl.n = R;
-    for (int r = 0; r <= R; ++r) p.tbl.ev_begin[r] = off[r];
+    for (int r = 0; r <= R; ++r) p.tbl.ev_begin[r] = std::min(std::max(off[r] - off[b0], 0LL), total);
     for (int r = 0; r < R; ++r) p.tbl.grid[r] = grid_h(ctx->grid, lo[r], hi[r], rv[r]);
     CK(ensure(ctx->pass_partial, sizeof(double) * kNeffSlots * R));
     p.a.partial = ctx->pass_partial.as<double>();

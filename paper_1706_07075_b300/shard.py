@@ -64,10 +64,16 @@ def region_block(n_regions, rank, world):
 def regions_mlem_sharded(ctx, regions, margin_mm, shell_mm, n_iter, image, rank, world, allreduce_image):
     """This rank's block of the regions, reconstructed and stitched into `image`
     (nx*ny*nz float32, zero outside its slabs), then summed over the ranks by
-    allreduce_image(image).  Returns the block (lo, hi)."""
+    allreduce_image(image).  The division passed to the library is the whole one,
+    so events shared with a region of another rank keep their weight 1/2.
+    Returns the block (lo, hi)."""
     lo, hi = region_block(len(regions), rank, world)
     if hi > lo:
-        ctx.mlem_regions(None, regions[lo:hi], margin_mm, shell_mm, n_iter, image)
+        ctx.set_region_block(lo, hi - lo)
+        try:
+            ctx.mlem_regions(None, regions, margin_mm, shell_mm, n_iter, image)
+        finally:
+            ctx.set_region_block(0, 0)
     else:
         image.zero_() if hasattr(image, "zero_") else image.fill(0)
     allreduce_image(image)

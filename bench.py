@@ -26,8 +26,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "TOF-MLEM events x iterations / s (full-body, 146M events, 150x150x600 @ 4 mm)"
 # DRAM bytes per event of the fused pass: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture on 8 M full-body events (cell + direction order, 128 threads, series masses), per event
-TRAFFIC_BYTES_PER_EVENT = 49.3
+# capture on 8 M full-body events (cell + direction order, 128 threads, series masses, the walk
+# set-up with the TOF point as an FP32 pair), per event
+TRAFFIC_BYTES_PER_EVENT = 49.2
 # algorithmic FP32 operations per Siddon piece: ~25 for the step and the two
 # accumulations plus ~20 for the Gaussian mass of the piece
 ALU_OPS_PER_PIECE = 45.0

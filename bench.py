@@ -557,38 +557,37 @@ def time_packed_leg(ctx, B, synth, ev, n, args, stream, img_plain, bf16):
 def time_lut_leg(ctx, B, n, args, stream, img_exact):
     """The paper's own projector (Sec. 2.3): 32 equally spaced Gaussian samples
     per event, each deposited in its voxel, against the exact Siddon x Phi
-    projector on the same resident events.  Accuracy: relative L2 distance of
-    the sampled projector's image to the exact one after the same iterations
-    from the same start, and of the two forward projections of that image."""
+    projector on the same resident events.  The tuned launch (threads per block,
+    linear image or 2x2x2-brick copies) and, for comparison, both image layouts at
+    the tuned thread count.  Accuracy: relative L2 distance of the sampled
+    projector's image to the exact one after the same iterations from the same
+    start, and of the two forward projections of that image."""
     import numpy as np
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     ctx.set_projector(B.PROJ_SAMPLED, 32)
     cons = np.zeros((args.iters, 2))
-    ctx.mlem(None, args.iters, None, None, cons)     # warm-up
+    ctx.mlem(None, args.iters, None, None, cons)     # warm-up (+ autotune for this projector)
     st0 = ctx.get_stats()
     ms = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons))
     st1 = ctx.get_stats()
+    tuned = ctx.get_launch()
     img_lut = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
     ctx.mlem(None, args.iters, None, img_lut, cons)
-    # the same pass over 2x2x2-brick copies of lambda and C (one vector reduction per
-    # 16-byte brick half a lane visits in a row)
-    cons_b = np.zeros_like(cons)
-    ctx.set_brick_layout(1)
+    layouts = {}
     try:
-        ctx.mlem(None, args.iters, None, None, cons_b)     # warm-up
-        b0 = ctx.get_stats()
-        ms_b = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons_b))
-        b1 = ctx.get_stats()
-        img_b = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
-        ctx.mlem(None, args.iters, None, img_b, cons_b)
+        for name, red in (("linear", 0), ("bricks", 1)):
+            ctx.set_launch(tuned[0], 0, 0, 0, 0, red)
+            ctx.mlem(None, args.iters, None, None, cons)     # warm-up
+            ms_l = _timed_steps(stream, args.steps, lambda: ctx.mlem(None, args.iters, None, None, cons))
+            img_l = torch.empty(ctx.n_vox, dtype=torch.float32).pin_memory()
+            ctx.mlem(None, args.iters, None, img_l, cons)
+            layouts[name] = {"value": n * args.iters * args.steps / (ms_l / 1e3), "unit": UNIT,
+                             "ms_per_step": ms_l / args.steps,
+                             "image_rel_l2_vs_tuned": float(torch.linalg.vector_norm(img_l.double() - img_lut.double())
+                                                            / torch.linalg.vector_norm(img_lut.double()))}
     finally:
-        ctx.set_brick_layout(0)
-    bricks = {"value": n * args.iters * args.steps / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b / args.steps,
-              "gpu_launches": int(b1["kernel_launches"] - b0["kernel_launches"]),
-              "image_rel_l2_vs_linear": float(torch.linalg.vector_norm(img_b.double() - img_lut.double()) /
-                                              torch.linalg.vector_norm(img_lut.double())),
-              "conservation_last": [float(x) for x in cons_b[-1]]}
+        ctx.set_launch(None)
     p_lut = torch.empty(n, dtype=torch.float32, device=dev)
     p_ex = torch.empty(n, dtype=torch.float32, device=dev)
     lam = img_exact.to(dev)
@@ -600,10 +599,11 @@ def time_lut_leg(ctx, B, n, args, stream, img_exact):
     fwd_rel = float(torch.linalg.vector_norm(p_lut.double() - p_ex.double()) / torch.linalg.vector_norm(p_ex.double()))
     return {"workload": "fullbody, sampled TOF kernel, 32 samples (Sec. 2.3)", "value": n * args.iters * args.steps /
             (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "launch": {"threads": tuned[0], "layout": ["linear image", "2x2x2-brick copies"][tuned[5]]},
             "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
             "image_rel_l2_vs_exact": float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)),
             "forward_rel_l2_vs_exact": fwd_rel, "conservation_last": [float(x) for x in cons[-1]],
-            "steps": args.steps, "brick_layout": bricks}
+            "steps": args.steps, "layouts_at_tuned_threads": layouts}
 
 
 def time_osem_leg(ctx, B, n, args, stream, subsets=5):

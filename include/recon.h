@@ -106,12 +106,15 @@ typedef struct {
                                   the h^6 term (Hermite polynomials; error below 1e-7 of the window mass
                                   for pieces up to 0.4 sigma).  Without a fixed launch the library uses
                                   2 only when the voxel diagonal is at most 0.5 sigma, else 0 */
-    int32_t reduction;         /* exact projector in recon_mlem (one grid, FP32 gathers, flat grid, no piece
-                                  cache): 0 scalar FP32 reductions into the linear image; 1 lambda and C
-                                  in 2x2x2-voxel brick copies (one 32-byte sector per brick), each lane's
-                                  consecutive pieces within one 16-byte brick half gathered by one load
-                                  and reduced by one red.global.add.v4.f32 (same pieces and masses; the
-                                  sums run in another order).  Other passes use 0 */
+    int32_t reduction;         /* recon_mlem's pass over one grid with FP32 gathers: 0 the linear image
+                                  (exact projector: scalar FP32 reductions; sampled projector: x-adjacent
+                                  pairs as red.global.add.v2.f32); 1 lambda and C in 2x2x2-voxel brick
+                                  copies (one 32-byte sector per brick), each lane's consecutive visits
+                                  within one 16-byte brick half gathered by one load and reduced by one
+                                  red.global.add.v4.f32 (same visits and weights; the sums run in another
+                                  order; for the exact projector only with a flat grid and no piece
+                                  cache; for the sampled projector the same as recon_set_brick_layout(1)).
+                                  Other passes use 0 */
     int32_t image_tiling;      /* reported by recon_get_launch, ignored by recon_set_launch: 1 when the
                                   last MLEM pass held lambda and C in shared-memory tiles of the event's
                                   cell (recon_set_tiled_pass, or the autotuner's choice), 0 when it read
@@ -309,14 +312,15 @@ recon_status recon_set_timing(recon_ctx* ctx, int32_t on);
 /* Capture each MLEM iteration in a CUDA graph and replay it (1, default) or launch
  * kernels directly (0). */
 recon_status recon_set_graphs(recon_ctx* ctx, int32_t on);
-/* Let recon_mlem / recon_mlem_regions search launch configurations of the exact
- * projector's event pass on the resident events the first time they meet a new
- * (event count, format, voxel count, region count, event order) with at least 2^20
- * events (1, default), or use the default launch (0).  Candidates: threads per block,
+/* Let recon_mlem / recon_mlem_regions search launch configurations of the event pass
+ * on the resident events the first time they meet a new (event count, format, voxel
+ * count, region count, event order, projector) with at least 2^20 events (1, default),
+ * or use the default launch (0).  Candidates: threads per block,
  * flat or persistent grid, piece cache, piece-mass form and reduction form (scalar
  * into the linear image, or per-brick-half vector reductions over brick copies; the
  * latter with one grid and FP32 gathers), 15 in all, each timed over two passes (the
- * brick candidates with their copy kernels).  recon_mlem in the default event order
+ * brick candidates with their copy kernels).  For the sampled projector: 128, 192 or 256
+ * threads per block, each with the linear image or the brick copies.  recon_mlem in the default event order
  * then also times the shared-memory tiled pass (recon_set_tiled_pass) with 1 and 8
  * threads per event against the best of those, where tiles fit (exact projector, one
  * subset, FP32 gathers), and keeps the faster image layout for the key.  C and the

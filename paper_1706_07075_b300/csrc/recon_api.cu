@@ -501,8 +501,15 @@ unsigned spread_multiplier(long long blocks)
 recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, LaunchCfg* best)
 {
     NvtxRange nvtx_range("autotune");
-    // flat and persistent grids, walking twice or replaying a shared-memory piece cache
-    const std::vector<LaunchCfg> cands = {
+    // sampled projector: threads per block, and the linear image (x-pair vector
+    // reductions) or the brick copies (per-half vector reductions)
+    const std::vector<LaunchCfg> lut_cands = {
+        {128, 0, 0, 0, TAIL_FIT, 0}, {192, 0, 0, 0, TAIL_FIT, 0}, {256, 0, 0, 0, TAIL_FIT, 0},
+        {128, 0, 0, 0, TAIL_FIT, 1}, {192, 0, 0, 0, TAIL_FIT, 1}, {256, 0, 0, 0, TAIL_FIT, 1},
+    };
+    // exact projector: flat and persistent grids, walking twice or replaying a
+    // shared-memory piece cache, piece-mass forms, reduction forms
+    const std::vector<LaunchCfg> exact_cands = {
         {128, 0, 0, 0, TAIL_FIT}, {256, 0, 0, 0, TAIL_FIT}, {96, 0, 0, 0, TAIL_FIT},
         {192, 0, 0, 0, TAIL_FIT}, {128, 8, 64, 0, TAIL_FIT}, {64, 0, 0, 64, TAIL_FIT},
         {128, 0, 0, 0, TAIL_ERFC}, {256, 0, 0, 0, TAIL_ERFC}, {128, 0, 0, 0, TAIL_SERIES},
@@ -511,9 +518,10 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
         {128, 0, 0, 0, TAIL_SERIES, 1}, {192, 0, 0, 0, TAIL_SERIES, 1}, {256, 0, 0, 0, TAIL_SERIES, 1},
         {128, 0, 0, 0, TAIL_FIT, 1},
     };
+    const std::vector<LaunchCfg>& cands = a.lut.n > 0 ? lut_cands : exact_cands;
     // the brick form needs one grid at offset 0 and FP32 gathers; its candidates are
     // timed with the two copy kernels around the pass
-    const bool brick_ok = a.lut.n == 0 && tbl.n == 1 && tbl.grid[0].vox_offset == 0 && !a.lam_bf16;
+    const bool brick_ok = tbl.n == 1 && tbl.grid[0].vox_offset == 0 && !a.lam_bf16;
     const recon_grid& gr = ctx->grid;
     if (brick_ok) {
         const size_t nb = (size_t)brick_voxels(gr.nx, gr.ny, gr.nz);
@@ -533,7 +541,7 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
     for (const LaunchCfg& c : cands) {
         // the persistent work queue takes events in list order, which a spread list must not
         if (spread && c.blocks_per_sm > 0) continue;
-        if (c.tail == TAIL_SERIES && !series_ok(ctx)) continue;
+        if (a.lut.n == 0 && c.tail == TAIL_SERIES && !series_ok(ctx)) continue;
         if (c.reduction == 1 && !brick_ok) continue;
         float ms_min = 1e30f;
         PassArgs ac = a;
@@ -807,12 +815,20 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool 
     return RECON_OK;
 }
 
+// Autotuner cache key: event count, format, voxels, and in the last field the
+// number of regions, whether the list is spread-ordered (cell- or region-ordered lists
+// are tuned apart from lists in load order) and the sampled projector's sample count.
+std::tuple<long long, int, long long, int> tune_key(const recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl)
+{
+    return std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n + (a.block_mul == 1 ? (1 << 20) : 0) + (a.lut.n << 22));
+}
+
 // The launch choose_cfg would pick, without running the autotuner.
 LaunchCfg tuned_or_default(recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl)
 {
     if (ctx->user_cfg) return ctx->cfg;
-    if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg(ctx);
-    auto it = ctx->tuned.find(std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n + (a.block_mul == 1 ? (1 << 20) : 0)));
+    if (!ctx->autotune || a.n < (1LL << 20)) return default_cfg(ctx);
+    auto it = ctx->tuned.find(tune_key(ctx, a, tbl));
     return it != ctx->tuned.end() ? it->second : default_cfg(ctx);
 }
 
@@ -820,9 +836,8 @@ LaunchCfg choose_cfg(recon_ctx* ctx, const PassArgs& a, const RegionTable& tbl, 
 {
     *st = RECON_OK;
     if (ctx->user_cfg) return ctx->cfg;
-    if (a.lut.n > 0 || !ctx->autotune || a.n < (1LL << 20)) return default_cfg(ctx);
-    // spread (cell- or region-ordered) lists are tuned apart from lists in load order
-    auto key = std::make_tuple(a.n, ctx->fmt, ctx->n_vox, tbl.n + (a.block_mul == 1 ? (1 << 20) : 0));
+    if (!ctx->autotune || a.n < (1LL << 20)) return default_cfg(ctx);
+    auto key = tune_key(ctx, a, tbl);
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) return it->second;
     LaunchCfg best;
@@ -1840,7 +1855,8 @@ recon_status mlem_impl(recon_ctx* ctx, const recon_events* events, int32_t n_ite
     auto set_layout = [&]() -> recon_status {
         const bool exact_bricks = ctx->lut_n == 0 && p.cfg.reduction == 1 && !ctx->bf16 && p.cfg.blocks_per_sm == 0 &&
                                   p.cfg.cache == 0 && !(p.tiled && p.tile_mode == 1);
-        p.bricks = (ctx->bricks && ctx->lut_n > 0 && !ctx->bf16) || exact_bricks;
+        const bool lut_bricks = ctx->lut_n > 0 && !ctx->bf16 && (ctx->bricks || p.cfg.reduction == 1);
+        p.bricks = lut_bricks || exact_bricks;
         if (p.bricks) {
             const size_t nb = (size_t)brick_voxels(ctx->grid.nx, ctx->grid.ny, ctx->grid.nz);
             CK(ensure(ctx->lam_brick, sizeof(float) * nb));

@@ -284,3 +284,31 @@ def test_region_mlem_lut_with_sieve_matches_oracle():
     for r in range(3):
         for k in range(3):
             assert cons[k, r, 0] == pytest.approx(hists[r][k][0], abs=0.5)
+
+
+def test_mlem_lut_autotuned_matches_oracle():
+    # enough events for the autotuner (at least 2^20): it picks threads per block and
+    # the image layout (linear, or 2x2x2-brick copies with per-half vector reductions)
+    # for the sampled projector; whatever it picks, the image holds the plain gates
+    g = workload_grid("tiny")
+    ev = lut_unambiguous(g, synth.events("tiny", 1_400_000, 29), 32)
+    assert ev.shape[1] >= 1 << 20
+    lors = synth.sensitivity_lors("tiny", 1_000_000, 29)
+    s_ref = oracle.sensitivity(g, lors)
+    with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx:
+        ctx.set_sensitivity(s_ref)
+        ctx.set_projector(B.PROJ_SAMPLED, 32)
+        ctx.load_events(B.make_events(ev))
+        img = np.zeros(g.n_vox, np.float32)
+        cons = np.zeros((3, 2))
+        ctx.mlem(None, 3, None, img, cons)
+        launch = ctx.get_launch()
+        assert ctx.get_stats()["autotune_runs"] >= 1
+    assert launch[0] in (128, 192, 256) and launch[5] in (0, 1)
+    lam_ref, hist = oracle.mlem(g, ev.astype(np.float64), s_ref, 3, SIGMA, lut_samples=32)
+    print(f"\nsampled projector, tuned launch {launch}: rel L2 {rel_l2(img, lam_ref):.2e}")
+    assert rel_l2(img, lam_ref) <= 1e-4
+    assert max_rel_above(img, lam_ref, 0.01) <= 1e-3
+    for k in range(3):
+        assert cons[k, 0] == pytest.approx(hist[k][0], abs=0.5)
+        assert cons[k, 1] == pytest.approx(cons[k, 0], rel=1e-5)

@@ -738,6 +738,11 @@ def serve_leg(args, fb, fb_pinned, n_jobs, local):
     stats = srv.replay(jobs)
     clocks = sampler.stop()
     served_kind = by_kind(srv.done)
+    # the same stream without stream priorities (every job at the default priority)
+    ex.set_priorities(None)
+    srv0 = Server(ex, slots=3, hbm_budget_bytes=budget)
+    stats0 = srv0.replay(make_jobs())
+    ex.set_priorities(4_000_000)
     srv1 = Server(ex, slots=1, hbm_budget_bytes=budget)
     stats1 = srv1.replay(make_jobs())
     ex.close()
@@ -749,6 +754,11 @@ def serve_leg(args, fb, fb_pinned, n_jobs, local):
             "region_events": {k: int(kinds[k][2][0].shape[1]) for k in region_kinds},
             "fullbody_events": n_fb, "smallfov_events": 5_000_000, "serial_service_s": service,
             "latency_by_kind": served_kind,
+            "priorities": "region slabs and small fields of view on high-priority streams, full bodies on "
+                          "low-priority ones",
+            "without_priorities": {"p50_s": stats0["p50_s"], "p99_s": stats0["p99_s"],
+                                   "events_iters_per_s": stats0["events_iters_per_s"],
+                                   "latency_by_kind": by_kind(srv0.done)},
             "one_job_at_a_time": {"p50_s": stats1["p50_s"], "p99_s": stats1["p99_s"],
                                   "events_iters_per_s": stats1["events_iters_per_s"],
                                   "latency_by_kind": by_kind(srv1.done)},

@@ -6,9 +6,11 @@ free and the job's device-memory footprint fits the remaining HBM budget; a
 later, smaller job may pass an older one that does not fit yet (first fit in
 arrival order).  With `max_overtakes` set, a job that later jobs have passed
 that many times holds the line: no younger job starts until it does, so a
-large job cannot starve behind a stream of small ones.  Each slot owns a CUDA stream and a reconstruction context
-per image grid, so the upload, the MLEM iterations and the read-back of
-concurrent jobs overlap on the GPU.  Sensitivity images are computed once
+large job cannot starve behind a stream of small ones.  Each slot owns CUDA
+streams and a reconstruction context per image grid, so the upload, the MLEM
+iterations and the read-back of concurrent jobs overlap on the GPU; small grids
+run on high-priority streams, so a small job's kernels do not wait for a
+full-body pass to drain.  Sensitivity images are computed once
 per (scanner, grid) and stay resident on the device; contexts are kept and
 reused by later jobs on the same grid.
 
@@ -253,20 +255,29 @@ class Server:
 
 
 class LibreconExecutor:
-    """Runs jobs through librecon: one CUDA stream per slot, contexts reused per
-    grid, sensitivity images resident per key.  The device memory it holds is
+    """Runs jobs through librecon: CUDA streams per slot (a high-priority one for
+    small grids, a low-priority one for large ones), contexts reused per grid,
+    sensitivity images resident per key.  The device memory it holds is
     reported to the server: each cached context's buffers (recon_info's
     device_bytes, read after every job on the slot's own thread) and the
     sensitivity images."""
 
-    def __init__(self, slots, device=0, sensitivities=None, keep_results=True, launch=(128, 0, 0, 0, 2)):
+    def __init__(self, slots, device=0, sensitivities=None, keep_results=True, launch=(128, 0, 0, 0, 2),
+                 low_priority_voxels=4_000_000):
         import torch
         from . import binding as B
         self.B = B
         self.torch = torch
         self.device = device
         torch.cuda.set_device(device)
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        # two streams per slot: contexts on grids of more than low_priority_voxels voxels
+        # (full bodies) run on the low-priority one, the rest (region slabs, small
+        # fields of view) on the high-priority one, so that when a block slot frees up
+        # the GPU takes a small job's blocks before the next blocks of a long pass
+        # (None: every context on its slot's default-priority stream)
+        self.low_priority_voxels = low_priority_voxels
+        self.streams = [torch.cuda.Stream(device=device, priority=-1) for _ in range(slots)]
+        self.low_streams = [torch.cuda.Stream(device=device, priority=0) for _ in range(slots)]
         self.contexts = [dict() for _ in range(slots)]   # per slot: grid -> Context
         self.loaded = [dict() for _ in range(slots)]     # per slot: grid -> sensitivity key resident in it
         self.ctx_bytes = {}                               # (slot, grid) -> device bytes the context holds
@@ -282,6 +293,23 @@ class LibreconExecutor:
     @staticmethod
     def _key(job):
         return (tuple(job.grid), tuple(job.geometry))
+
+    def _stream_for(self, slot, grid):
+        """High-priority stream for grids up to low_priority_voxels voxels, low for
+        larger ones; every grid on the default-priority stream when the rule is off."""
+        if not self.low_priority_voxels:
+            return self.low_streams[slot]
+        nvox = grid[0] * grid[1] * grid[2]
+        return (self.low_streams if nvox > self.low_priority_voxels else self.streams)[slot]
+
+    def set_priorities(self, low_priority_voxels):
+        """Change the priority rule (None: every context on its slot's default-priority
+        stream) and move the cached contexts to the streams it gives.  Call between jobs."""
+        self.low_priority_voxels = low_priority_voxels
+        with self._lock:
+            for slot, per_slot in enumerate(self.contexts):
+                for (grid, _), ctx in per_slot.items():
+                    ctx.set_stream(self._stream_for(slot, grid).cuda_stream)
 
     def register_sensitivity(self, key, geometry, grid, lors):
         """Compute a sensitivity image once and keep it on the device."""
@@ -337,7 +365,7 @@ class LibreconExecutor:
             self.last_used[(slot, key)] = self._use
         if ctx is None:
             ctx = self.B.Context(job.geometry, job.grid)
-            ctx.set_stream(self.streams[slot].cuda_stream)
+            ctx.set_stream(self._stream_for(slot, job.grid).cuda_stream)
             if self.launch is not None:
                 ctx.set_launch(*self.launch)
             with self._lock:

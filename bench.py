@@ -301,7 +301,9 @@ def run_reference(args):
     import numpy as np
     import oracle
     from paper_1706_07075_b300 import synth
-    n_sample = args.cpu_sample
+    # each step a bounded sample: the whole --steps K run stays near 1.5 min of FP64 work
+    # on 16 cores (15 M events per step up to 10 steps, fewer per step beyond)
+    n_sample = min(args.cpu_sample, max(2_000_000, 150_000_000 // max(1, args.steps)))
     ev = synth.events("fullbody", n_sample, args.seed)
     lors = synth.sensitivity_lors("fullbody", 200_000, args.seed)
     g = oracle.Grid(*synth.grid_of("fullbody"))

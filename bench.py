@@ -452,7 +452,7 @@ def run_region_sharded(args, B, synth, rank, world, local, dev, stream, ctx, n):
 def launch_record(ctx_cfg, layout):
     """The event-pass launch the library used, every tuned dimension named."""
     return {"threads": ctx_cfg[0], "blocks_per_sm": ctx_cfg[1], "chunk": ctx_cfg[2], "cached_pieces": ctx_cfg[3],
-            "piece_mass": ["fitted erfc tails", "erfcf tails", "midpoint series"][ctx_cfg[4]],
+            "piece_mass": ["fitted erfc tails", "erfcf tails", "midpoint series through h^6", "midpoint series through h^4"][ctx_cfg[4]],
             "reduction": ["scalar, linear image", "per-brick-half vector, 2x2x2-brick copies"][ctx_cfg[5]],
             "image_tiling": ["global image (L2-resident)", "shared-memory tiles"][layout[0]],
             "threads_per_event": layout[1]}

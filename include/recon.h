@@ -104,8 +104,11 @@ typedef struct {
                                   degree-10 P (relative error ~6e-7 at K = 3), 1: CUDA's erfcf; or
                                   2: the Taylor series of the integral about the piece's midpoint through
                                   the h^6 term (Hermite polynomials; error below 1e-7 of the window mass
+                                  for pieces up to 0.4 sigma); 3: the same series through the h^4 term
+                                  (the omitted term is at most 96 h^6 / 322560 of a piece's mass, 1.2e-6
                                   for pieces up to 0.4 sigma).  Without a fixed launch the library uses
-                                  2 only when the voxel diagonal is at most 0.5 sigma, else 0 */
+                                  2 only when the voxel diagonal is at most 0.5 sigma, else 0; the
+                                  autotuner tries 3 where the diagonal is at most 0.4 sigma and K <= 3 */
     int32_t reduction;         /* recon_mlem's pass over one grid with FP32 gathers: 0 the linear image
                                   (exact projector: scalar FP32 reductions; sampled projector: x-adjacent
                                   pairs as red.global.add.v2.f32); 1 lambda and C in 2x2x2-voxel brick
@@ -318,7 +321,7 @@ recon_status recon_set_graphs(recon_ctx* ctx, int32_t on);
  * or use the default launch (0).  Candidates: threads per block,
  * flat or persistent grid, piece cache, piece-mass form and reduction form (scalar
  * into the linear image, or per-brick-half vector reductions over brick copies; the
- * latter with one grid and FP32 gathers), 15 in all, each timed over two passes (the
+ * latter with one grid and FP32 gathers), 17 in all, each timed over two passes (the
  * brick candidates with their copy kernels).  For the sampled projector: 128, 192 or 256
  * threads per block, each with the linear image or the brick copies.  recon_mlem in the default event order
  * then also times the shared-memory tiled pass (recon_set_tiled_pass) with 1 and 8

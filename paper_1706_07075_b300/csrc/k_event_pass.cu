@@ -200,8 +200,11 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
 
 template <int TailK>
 struct TailOf {
-    using type = typename std::conditional<TailK == TAIL_FIT, TailFit,
-                                           typename std::conditional<TailK == TAIL_ERFC, TailErfc, TailSeries>::type>::type;
+    using type = typename std::conditional<
+        TailK == TAIL_FIT, TailFit,
+        typename std::conditional<TailK == TAIL_ERFC, TailErfc,
+                                  typename std::conditional<TailK == TAIL_SERIES4, TailSeries4,
+                                                            TailSeries>::type>::type>::type;
 };
 
 template <int Kind, int Fmt, bool Persistent, bool Cached, int TailK, bool Brick = false>
@@ -516,6 +519,7 @@ cudaError_t launch_kind(const LaunchCfg& cfg, const PassArgs& a, const RegionTab
     if ((size_t)cfg.cache * cfg.threads * 8 > (size_t)kMaxCacheBytes) return cudaErrorInvalidValue;
     if (cfg.tail == TAIL_FIT) return launch_tail<Kind, Fmt, TAIL_FIT>(blocks, cfg, a, tbl, s);
     if (cfg.tail == TAIL_SERIES) return launch_tail<Kind, Fmt, TAIL_SERIES>(blocks, cfg, a, tbl, s);
+    if (cfg.tail == TAIL_SERIES4) return launch_tail<Kind, Fmt, TAIL_SERIES4>(blocks, cfg, a, tbl, s);
     return launch_tail<Kind, Fmt, TAIL_ERFC>(blocks, cfg, a, tbl, s);
 }
 

@@ -433,6 +433,14 @@ bool series_ok(const recon_ctx* c)
     return c->sigma_mm > 0 && diag <= 0.5 * c->sigma_mm;
 }
 
+// The series through h^4 drops He_6(m) h^6 / 322560, at most 96 h^6 / 322560 of a
+// piece's mass (|He_6| <= 96 on [0, 3]): below 1.2e-6 for pieces up to 0.4 sigma.
+bool series4_ok(const recon_ctx* c)
+{
+    const double diag = std::sqrt(c->grid.vx * c->grid.vx + c->grid.vy * c->grid.vy + c->grid.vz * c->grid.vz);
+    return c->sigma_mm > 0 && diag <= 0.4 * c->sigma_mm && c->k_sigma <= 3.0;
+}
+
 LaunchCfg default_cfg(const recon_ctx* c)
 {
     return series_ok(c) ? LaunchCfg{192, 0, 0, 0, TAIL_SERIES} : LaunchCfg{128, 0, 0, 0, TAIL_FIT};
@@ -447,7 +455,7 @@ bool valid_cfg(const recon_launch* c)
         return false;
     if (c->cached_pieces != 0 && (c->cached_pieces < 8 || c->cached_pieces > 256)) return false;
     if ((long long)c->cached_pieces * c->threads_per_block * 8 > 200 * 1024) return false;
-    if (c->tail_eval != TAIL_FIT && c->tail_eval != TAIL_ERFC && c->tail_eval != TAIL_SERIES) return false;
+    if (c->tail_eval < TAIL_FIT || c->tail_eval > TAIL_SERIES4) return false;
     if (c->reduction != 0 && c->reduction != 1) return false;
     if (c->reduction == 1 && (c->blocks_per_sm != 0 || c->cached_pieces != 0)) return false;
     return true;
@@ -515,6 +523,7 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
         {128, 0, 0, 0, TAIL_ERFC}, {256, 0, 0, 0, TAIL_ERFC}, {128, 0, 0, 0, TAIL_SERIES},
         {256, 0, 0, 0, TAIL_SERIES}, {192, 0, 0, 0, TAIL_SERIES},
         // brick copies of lambda and C with per-half vector reductions
+        {128, 0, 0, 0, TAIL_SERIES4}, {192, 0, 0, 0, TAIL_SERIES4},
         {128, 0, 0, 0, TAIL_SERIES, 1}, {192, 0, 0, 0, TAIL_SERIES, 1}, {256, 0, 0, 0, TAIL_SERIES, 1},
         {128, 0, 0, 0, TAIL_FIT, 1},
     };
@@ -542,6 +551,7 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
         // the persistent work queue takes events in list order, which a spread list must not
         if (spread && c.blocks_per_sm > 0) continue;
         if (a.lut.n == 0 && c.tail == TAIL_SERIES && !series_ok(ctx)) continue;
+        if (a.lut.n == 0 && c.tail == TAIL_SERIES4 && !series4_ok(ctx)) continue;
         if (c.reduction == 1 && !brick_ok) continue;
         float ms_min = 1e30f;
         PassArgs ac = a;

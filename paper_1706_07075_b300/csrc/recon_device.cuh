@@ -139,7 +139,12 @@ struct TailFit {
 // 1e-7 of the piece's mass over the +-3 sigma window.  One exponential per
 // piece and no carried boundary value; walk() calls piece() instead of
 // differencing two tails.  Returns 2 [Phi(b) - Phi(a)] like the tail forms.
-struct TailSeries {
+// Through6 = false stops at the h^4 term: the omitted He_6(m) h^6 / 322560 is at
+// most 96 (0.36)^6 / 322560 = 6.5e-7 of the piece's own mass for 4 mm voxels
+// (|He_6| <= 96 on [0, 3]), about the FP32 rounding of the sum, for 5 fewer
+// operations per piece.
+template <bool Through6>
+struct TailSeriesT {
     static constexpr bool kPiecewise = true;
     float inv_sigma_sqrt2;
     __device__ __forceinline__ Tail operator()(float) const { return Tail{0.f, 0.f}; }
@@ -152,12 +157,19 @@ struct TailSeries {
         const float h2 = h * h;
         const float c1 = (q - 1.f) * (1.f / 24.f);
         const float c2 = fmaf(q - 6.f, q, 3.f) * (1.f / 1920.f);
-        const float c3 = fmaf(fmaf(q - 15.f, q, 45.f), q, -15.f) * (1.f / 322560.f);
-        const float poly = fmaf(h2, fmaf(h2, fmaf(h2, c3, c2), c1), 1.f);
+        float poly;
+        if constexpr (Through6) {
+            const float c3 = fmaf(fmaf(q - 15.f, q, 45.f), q, -15.f) * (1.f / 322560.f);
+            poly = fmaf(h2, fmaf(h2, fmaf(h2, c3, c2), c1), 1.f);
+        } else {
+            poly = fmaf(h2, fmaf(h2, c2, c1), 1.f);
+        }
         // 2 phi(m) = sqrt(2/pi) exp(-m^2/2)
         return h * poly * (0.7978845608f * __expf(-0.5f * q));
     }
 };
+using TailSeries = TailSeriesT<true>;
+using TailSeries4 = TailSeriesT<false>;
 
 // Per-event walk state after clipping the line to the grid box and the TOF
 // window.  Everything the two sweeps (forward, back) need is here.

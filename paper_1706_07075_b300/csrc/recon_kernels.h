@@ -56,7 +56,7 @@ struct TileH {
 
 enum EventFmt { FMT_F32 = 0, FMT_PACKED = 1 };
 enum PassKind { PASS_FUSED = 0, PASS_FORWARD = 1, PASS_BACK = 2 };
-enum TailEval { TAIL_FIT = 0, TAIL_ERFC = 1, TAIL_SERIES = 2 };
+enum TailEval { TAIL_FIT = 0, TAIL_ERFC = 1, TAIL_SERIES = 2, TAIL_SERIES4 = 3 };
 
 struct LaunchCfg {
     int threads;       // threads per block (64, 128, 256)

@@ -150,10 +150,11 @@ def test_streamed_upload_matches_resident_events():
     np.testing.assert_allclose(ca[:, 1], ca[:, 0], rtol=1e-5)
 
 
-@pytest.mark.parametrize("tail_eval", [0, 1, 2])
+@pytest.mark.parametrize("tail_eval", [0, 1, 2, 3])
 def test_piece_mass_forms_match_oracle(tiny, tail_eval):
-    # the three evaluations of a piece's Gaussian mass (fitted tails, erfcf tails,
-    # midpoint Taylor series) against the oracle's libm erfc, forward and 3 iterations
+    # the four evaluations of a piece's Gaussian mass (fitted tails, erfcf tails,
+    # midpoint Taylor series through h^6 and through h^4) against the oracle's libm
+    # erfc, forward and 3 iterations
     g, ev, lors, s_ref, ctx = tiny
     ctx.set_launch(128, 0, 0, 0, tail_eval)
     rng = np.random.default_rng(30 + tail_eval)

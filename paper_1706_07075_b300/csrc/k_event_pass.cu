@@ -131,7 +131,8 @@ __device__ __forceinline__ float do_event_brick(const PassArgs& a, const Event& 
     Walk w;
     w.valid = false;
     if (event_line(e, ln)) w = make_walk(g, ln, -a.tof.half_window, a.tof.half_window);
-    const float hin = a.tof.half_inv_norm;
+    if constexpr (TailF::kSigmaUnits) scale_walk(w, tail.inv_sigma());
+    const float hin = a.tof.half_inv_norm * TailF::kMassScale;
     const BrickIndex bi(w, a.brick_bx, a.brick_by);
     HalfGather hg{reinterpret_cast<const float4*>(a.lam)};
     float p = 0.f;
@@ -158,9 +159,10 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
     Walk w;
     w.valid = false;
     if (event_line(e, ln)) w = make_walk(g, ln, -a.tof.half_window, a.tof.half_window);
-    // the walk hands over 2 [Phi(b) - Phi(a)] per piece; half_inv_norm turns it
-    // into the TOF mass, applied once to p_i and once to r_i
-    const float hin = a.tof.half_inv_norm;
+    if constexpr (TailF::kSigmaUnits) scale_walk(w, tail.inv_sigma());
+    // the walk hands over 2 [Phi(b) - Phi(a)] / kMassScale per piece; half_inv_norm
+    // times kMassScale turns it into the TOF mass, applied once to p_i and once to r_i
+    const float hin = a.tof.half_inv_norm * TailF::kMassScale;
     float* const Cb = a.C + g.vox_offset;
     if (Kind == PASS_BACK) {
         const float r = a.r_in[i] * hin;

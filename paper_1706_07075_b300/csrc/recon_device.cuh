@@ -95,6 +95,8 @@ struct Tail {
 // Tail from CUDA's erfcf.
 struct TailErfc {
     static constexpr bool kPiecewise = false;
+    static constexpr bool kSigmaUnits = false;
+    static constexpr float kMassScale = 1.f;
     float inv_sigma_sqrt2;
     __device__ __forceinline__ Tail operator()(float tau) const
     {
@@ -113,6 +115,8 @@ struct TailErfc {
 // K = 3 (2e-6 at K = 8), from ~20 FP32 operations and two MUFU operations.
 struct TailFit {
     static constexpr bool kPiecewise = false;
+    static constexpr bool kSigmaUnits = false;
+    static constexpr float kMassScale = 1.f;
     float inv_sigma_sqrt2;
     __device__ __forceinline__ Tail operator()(float tau) const
     {
@@ -130,6 +134,15 @@ struct TailFit {
     }
 };
 
+// 2^x by the PTX instruction ex2.approx.ftz.f32 (documented maximum relative error
+// about 2^-22 over the range used here; subnormal results flush to zero).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Piece mass from the Taylor expansion of the Gaussian integral about the
 // piece's midpoint (derivatives of phi are Hermite polynomials He_n times phi):
 //   Phi(b) - Phi(a) = h phi(m) [1 + He_2(m) h^2/24 + He_4(m) h^4/1920
@@ -138,34 +151,44 @@ struct TailFit {
 // (4 mm voxels at 300 ps: at most 0.36 sigma) the first omitted term is below
 // 1e-7 of the piece's mass over the +-3 sigma window.  One exponential per
 // piece and no carried boundary value; walk() calls piece() instead of
-// differencing two tails.  Returns 2 [Phi(b) - Phi(a)] like the tail forms.
+// differencing two tails.
 // Through6 = false stops at the h^4 term: the omitted He_6(m) h^6 / 322560 is at
 // most 96 (0.36)^6 / 322560 = 6.5e-7 of the piece's own mass for 4 mm voxels
-// (|He_6| <= 96 on [0, 3]), about the FP32 rounding of the sum, for 5 fewer
-// operations per piece.
+// (|He_6| <= 96 on [0, 3]), about the FP32 rounding of the sum.
+//
+// The walk runs in sigma units for this form (kSigmaUnits: the event pass scales
+// the walk's crossings by 1/sigma once per event), and the polynomials are written
+// in M = a + b = 2m, Q = M^2 = 4 m^2, so that each coefficient is one chain of
+// FMAs:  He_2(m)/24 = Q/96 - 1/24,  He_4(m)/1920 = Q^2/30720 - Q/1280 + 1/640,
+// He_6(m)/322560 = Q^3/20643840 - Q^2/344064 + Q/28672 - 1/21504, and
+// exp(-m^2/2) = 2^(-Q log2(e) / 8).  piece() returns h P exp(-m^2/2); the factor
+// sqrt(2/pi) that makes it 2 [Phi(b) - Phi(a)], what the tail forms return, is
+// kMassScale, applied once per event with the window normalisation.
 template <bool Through6>
 struct TailSeriesT {
     static constexpr bool kPiecewise = true;
+    static constexpr bool kSigmaUnits = true;
+    static constexpr float kMassScale = 0.7978845608f;   // sqrt(2/pi)
     float inv_sigma_sqrt2;
     __device__ __forceinline__ Tail operator()(float) const { return Tail{0.f, 0.f}; }
+    __device__ __forceinline__ float inv_sigma() const { return inv_sigma_sqrt2 * 1.41421356f; }
     __device__ __forceinline__ float piece(float ta, float tb) const
     {
-        const float inv_sigma = inv_sigma_sqrt2 * 1.41421356f;
-        const float h = (tb - ta) * inv_sigma;
-        const float m = (ta + tb) * (0.5f * inv_sigma);
-        const float q = m * m;
+        const float h = tb - ta;
+        const float M = ta + tb;
+        const float Q = M * M;
         const float h2 = h * h;
-        const float c1 = (q - 1.f) * (1.f / 24.f);
-        const float c2 = fmaf(q - 6.f, q, 3.f) * (1.f / 1920.f);
+        const float c1 = fmaf(Q, 1.f / 96.f, -1.f / 24.f);
+        const float c2 = fmaf(fmaf(Q, 1.f / 30720.f, -1.f / 1280.f), Q, 1.f / 640.f);
         float poly;
         if constexpr (Through6) {
-            const float c3 = fmaf(fmaf(q - 15.f, q, 45.f), q, -15.f) * (1.f / 322560.f);
+            const float c3 = fmaf(fmaf(fmaf(Q, 1.f / 20643840.f, -1.f / 344064.f), Q, 1.f / 28672.f), Q,
+                                  -1.f / 21504.f);
             poly = fmaf(h2, fmaf(h2, fmaf(h2, c3, c2), c1), 1.f);
         } else {
             poly = fmaf(h2, fmaf(h2, c2, c1), 1.f);
         }
-        // 2 phi(m) = sqrt(2/pi) exp(-m^2/2)
-        return h * poly * (0.7978845608f * __expf(-0.5f * q));
+        return h * poly * ex2_approx(Q * -0.18033688011f);   // log2(e) / 8
     }
 };
 using TailSeries = TailSeriesT<true>;
@@ -183,6 +206,21 @@ struct Walk {
     int ix0, iy0, iz0;        // start voxel per axis
     bool valid;
 };
+
+// The walk's parameter rescaled by s (tau -> s tau): clip range, first crossings
+// and crossing spacings; infinities stay infinite.  The voxel sequence and the
+// crossing counts do not change.
+__device__ __forceinline__ void scale_walk(Walk& w, float s)
+{
+    w.tau_in *= s;
+    w.tau_out *= s;
+    w.t0x *= s;
+    w.t0y *= s;
+    w.t0z *= s;
+    w.dtx *= s;
+    w.dty *= s;
+    w.dtz *= s;
+}
 
 // The TOF point c = M + d u of an event as an unevaluated sum c + c_lo of two
 // FP32 numbers.  FP32 alone rounds c to ulp(|c|), ~6e-5 mm at 1 m; a line nearly

@@ -32,7 +32,8 @@ def run(geo, g, ev, lors, extra=None):
     with B.Context(geo, grid_tuple(g), 300.0) as ctx:
         ctx.sensitivity(lors)
         ctx.load_events(B.make_events(ev))
-        for launch in [(128, 0, 0, 0, 2, 0), (128, 0, 0, 0, 2, 1), (96, 0, 0, 0, 0, 0), (128, 4, 64, 32, 1, 0)]:
+        for launch in [(128, 0, 0, 0, 2, 0), (128, 0, 0, 0, 3, 0), (128, 0, 0, 0, 3, 1), (96, 0, 0, 0, 0, 0),
+                       (128, 4, 64, 32, 1, 0)]:
             ctx.set_launch(*launch)
             ctx.mlem(None, 2)
         ctx.set_launch(None)

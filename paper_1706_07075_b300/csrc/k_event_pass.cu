@@ -101,28 +101,11 @@ struct HalfRed {
     }
 };
 
-// Gathers from a brick-layout image: the 16-byte brick half of the last gather
-// stays in registers, so a lane's consecutive pieces within one half cost one
-// 16-byte load.
-struct HalfGather {
-    const float4* base;
-    int half = -1;
-    float4 v;
-    __device__ __forceinline__ float get(int q)
-    {
-        const int h = q >> 2;
-        if (h != half) {
-            v = __ldg(base + h);
-            half = h;
-        }
-        const int slot = q & 3;
-        return slot == 0 ? v.x : (slot == 1 ? v.y : (slot == 2 ? v.z : v.w));
-    }
-};
-
 // One event of the exact projector over images in the brick layout (one grid,
-// FP32 gathers): the same pieces and masses as the linear pass; the gathers read
-// 16-byte brick halves and the reductions go out per brick half.
+// FP32 gathers): the same pieces and masses as the linear pass; the gathers are
+// scalar loads from the brick image (L1 keeps a lane's brick half; a 16-byte
+// half cached in registers cost more instructions than it saved) and the
+// reductions go out per brick half.
 template <class TailF>
 __device__ __forceinline__ float do_event_brick(const PassArgs& a, const Event& e, const GridDev& g,
                                                 const TailF& tail)
@@ -134,9 +117,9 @@ __device__ __forceinline__ float do_event_brick(const PassArgs& a, const Event& 
     if constexpr (TailF::kSigmaUnits) scale_walk(w, tail.inv_sigma());
     const float hin = a.tof.half_inv_norm * TailF::kMassScale;
     const BrickIndex bi(w, a.brick_bx, a.brick_by);
-    HalfGather hg{reinterpret_cast<const float4*>(a.lam)};
+    const float* const lb = a.lam;
     float p = 0.f;
-    walk_index<true>(g, tail, w, bi, [&](int q, float m) { p = fmaf(m, hg.get(q), p); });
+    walk_index<true>(g, tail, w, bi, [&](int q, float m) { p = fmaf(m, __ldg(lb + q), p); });
     p *= hin;
     if (!(p > 0.f)) return 0.f;
     const float r = e.w / p * hin;
@@ -174,17 +157,24 @@ __device__ __forceinline__ float do_event(const PassArgs& a, const SharedTable& 
     const int tid = threadIdx.x;
     const float* const lb = a.lam + g.vox_offset;
     const unsigned short* const hb = reinterpret_cast<const unsigned short*>(a.lam_bf16) + g.vox_offset;
-    walk<true>(g, a.tof, tail, w, [&](int j, float m) {
-        const float lam_j = bf16 ? __uint_as_float(((unsigned)__ldg(hb + j)) << 16) : __ldg(lb + j);
-        p = fmaf(m, lam_j, p);
-        if (Cached && Kind == PASS_FUSED) {
-            if (cnt < pc.cap) {
-                pc.j[cnt * pc.stride + tid] = j;
-                pc.a[cnt * pc.stride + tid] = m;
+    // the gather precision is uniform over the launch: one walk per form, so that
+    // the piece loop carries no select between them
+    auto forward = [&](auto gather) {
+        walk<true>(g, a.tof, tail, w, [&](int j, float m) {
+            p = fmaf(m, gather(j), p);
+            if (Cached && Kind == PASS_FUSED) {
+                if (cnt < pc.cap) {
+                    pc.j[cnt * pc.stride + tid] = j;
+                    pc.a[cnt * pc.stride + tid] = m;
+                }
+                ++cnt;
             }
-            ++cnt;
-        }
-    });
+        });
+    };
+    if (bf16)
+        forward([&](int j) { return __uint_as_float(((unsigned)__ldg(hb + j)) << 16); });
+    else
+        forward([&](int j) { return __ldg(lb + j); });
     p *= hin;
     if (Kind == PASS_FORWARD) {
         a.p_out[i] = p;

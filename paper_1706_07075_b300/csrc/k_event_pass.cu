@@ -315,6 +315,10 @@ __device__ __forceinline__ LutLine lut_line(const GridDev& g, const Event& e)
     l.bx = __fmul_rn(ux, ivx);
     l.by = __fmul_rn(uy, ivy);
     l.bz = __fmul_rn(uz, ivz);
+    // a NaN sample position would convert to voxel 0: drop lines with a
+    // non-finite coefficient instead
+    l.valid = l.valid && isfinite(l.ax) && isfinite(l.ay) && isfinite(l.az) && isfinite(l.bx) &&
+              isfinite(l.by) && isfinite(l.bz);
     return l;
 }
 
@@ -329,19 +333,20 @@ __device__ __forceinline__ void lut_walk(const GridDev& g, const LutH& lut, cons
                                          int bx = 0, int by = 0)
 {
     if (!l.valid) return;
-    const float fnx = (float)g.nx, fny = (float)g.ny, fnz = (float)g.nz;
     int prev = -1;
     float acc = 0.f;
     const int n = NS > 0 ? NS : lut.n;
 #pragma unroll
     for (int k = 0; k < n; ++k) {
         const float2 s = lut.s[k];
-        const float fx = floorf(__fmaf_rn(s.x, l.bx, l.ax));
-        const float fy = floorf(__fmaf_rn(s.x, l.by, l.ay));
-        const float fz = floorf(__fmaf_rn(s.x, l.bz, l.az));
-        const bool in = fx >= 0.f && fx < fnx && fy >= 0.f && fy < fny && fz >= 0.f && fz < fnz;
+        // floor to an integer in one conversion; a value beyond the int range
+        // saturates, so the unsigned range test drops it like any sample outside
+        const int ix = __float2int_rd(__fmaf_rn(s.x, l.bx, l.ax));
+        const int iy = __float2int_rd(__fmaf_rn(s.x, l.by, l.ay));
+        const int iz = __float2int_rd(__fmaf_rn(s.x, l.bz, l.az));
+        const bool in = (unsigned)ix < (unsigned)g.nx && (unsigned)iy < (unsigned)g.ny && (unsigned)iz < (unsigned)g.nz;
         int j = -1;
-        if (in) j = Brick ? brick_index((int)fx, (int)fy, (int)fz, bx, by) : (int)fx + g.nx * ((int)fy + g.ny * (int)fz);
+        if (in) j = Brick ? brick_index(ix, iy, iz, bx, by) : ix + g.nx * (iy + g.ny * iz);
         if (j != prev) {
             if (prev >= 0) visit(prev, acc);
             prev = j;
@@ -394,10 +399,11 @@ __device__ __forceinline__ float do_event_lut(const PassArgs& a, const SharedTab
     const float* const lb = a.lam + g.vox_offset;
     const unsigned short* const hb = reinterpret_cast<const unsigned short*>(a.lam_bf16) + g.vox_offset;
     float p = 0.f;
-    lut_walk<NS>(g, a.lut, l, [&](int j, float w) {
-        const float lam_j = bf16 ? __uint_as_float(((unsigned)__ldg(hb + j)) << 16) : __ldg(lb + j);
-        p = fmaf(w, lam_j, p);
-    });
+    if (bf16)
+        lut_walk<NS>(g, a.lut, l,
+                     [&](int j, float w) { p = fmaf(w, __uint_as_float(((unsigned)__ldg(hb + j)) << 16), p); });
+    else
+        lut_walk<NS>(g, a.lut, l, [&](int j, float w) { p = fmaf(w, __ldg(lb + j), p); });
     if (Kind == PASS_FORWARD) {
         a.p_out[i] = p;
         return 0.f;

@@ -57,7 +57,7 @@ __device__ __forceinline__ void tile_range(const TileH& t, int cx, int cy, int c
 template <int Fmt>
 __global__ void k_cell_codes(const void* __restrict__ ev, long long n, float lattice, TileH t, float half_window,
                              unsigned* __restrict__ code, unsigned* __restrict__ counts,
-                             unsigned long long* __restrict__ n_fallback)
+                             unsigned* __restrict__ rank, unsigned long long* __restrict__ n_fallback)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -110,7 +110,9 @@ __global__ void k_cell_codes(const void* __restrict__ ev, long long n, float lat
     }
     if (out == kCellNone) out = t.none_code;   // kept in a last bucket, or left out
     code[i] = out;
-    if (out < kCellFallback) atomicAdd(counts + out, 1u);
+    // the count before this event's increment is its place within its cell, so the
+    // scatter needs no second atomic
+    if (out < kCellFallback) rank[i] = atomicAdd(counts + out, 1u);
     else if (out == kCellFallback) atomicAdd(n_fallback, 1ull);
 }
 
@@ -215,7 +217,7 @@ __global__ void k_cell_list(unsigned* __restrict__ counts, long long n_cells, un
 
 template <int Fmt>
 __global__ void k_cell_scatter(const void* __restrict__ ev, long long n, const unsigned* __restrict__ code,
-                               const long long* __restrict__ begin, unsigned* __restrict__ cursor,
+                               const long long* __restrict__ begin, const unsigned* __restrict__ rank,
                                void* __restrict__ ev_cell, void* __restrict__ ev_fb,
                                unsigned long long* __restrict__ fb_cursor)
 {
@@ -225,7 +227,7 @@ __global__ void k_cell_scatter(const void* __restrict__ ev, long long n, const u
     long long pos;
     void* dst;
     if (c < kCellFallback && begin[c + 1] > begin[c]) {
-        pos = begin[c] + atomicAdd(cursor + c, 1u);
+        pos = begin[c] + rank[i];
         dst = ev_cell;
     } else if (c != kCellNone) {
         pos = (long long)atomicAdd(fb_cursor, 1ull);
@@ -464,16 +466,17 @@ __global__ void __launch_bounds__(Threads, 1) k_tile_pass(PassArgs a, TileH t, c
 }  // namespace
 
 cudaError_t launch_cell_codes(const void* ev, int fmt, long long n, float lattice, const TileH& t, float half_window,
-                              unsigned* code, unsigned* counts, unsigned long long* n_fallback, cudaStream_t st)
+                              unsigned* code, unsigned* counts, unsigned* rank, unsigned long long* n_fallback,
+                              cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const long long blocks = (n + 255) / 256;
     if (fmt == FMT_F32)
-        k_cell_codes<FMT_F32><<<(unsigned)blocks, 256, 0, st>>>(ev, n, lattice, t, half_window, code, counts,
+        k_cell_codes<FMT_F32><<<(unsigned)blocks, 256, 0, st>>>(ev, n, lattice, t, half_window, code, counts, rank,
                                                                n_fallback);
     else
         k_cell_codes<FMT_PACKED><<<(unsigned)blocks, 256, 0, st>>>(ev, n, lattice, t, half_window, code, counts,
-                                                                  n_fallback);
+                                                                  rank, n_fallback);
     return cudaGetLastError();
 }
 
@@ -501,16 +504,16 @@ cudaError_t launch_cell_list(unsigned* counts, long long n_cells, unsigned min_e
 }
 
 cudaError_t launch_cell_scatter(const void* ev, int fmt, long long n, const unsigned* code, const long long* begin,
-                                unsigned* cursor, void* ev_cell, void* ev_fb, unsigned long long* fb_cursor,
+                                const unsigned* rank, void* ev_cell, void* ev_fb, unsigned long long* fb_cursor,
                                 cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const long long blocks = (n + 255) / 256;
     if (fmt == FMT_F32)
-        k_cell_scatter<FMT_F32><<<(unsigned)blocks, 256, 0, st>>>(ev, n, code, begin, cursor, ev_cell, ev_fb,
+        k_cell_scatter<FMT_F32><<<(unsigned)blocks, 256, 0, st>>>(ev, n, code, begin, rank, ev_cell, ev_fb,
                                                                  fb_cursor);
     else
-        k_cell_scatter<FMT_PACKED><<<(unsigned)blocks, 256, 0, st>>>(ev, n, code, begin, cursor, ev_cell, ev_fb,
+        k_cell_scatter<FMT_PACKED><<<(unsigned)blocks, 256, 0, st>>>(ev, n, code, begin, rank, ev_cell, ev_fb,
                                                                     fb_cursor);
     return cudaGetLastError();
 }

@@ -98,7 +98,7 @@ struct TilePrep {
     long long n_binned = 0;
     int mode = 0;
     int subsets = 1;
-    DevBuf code, counts, cursor, begin, scratch, list, ev_cell, ev_fb, misc;
+    DevBuf code, counts, rank, begin, scratch, list, ev_cell, ev_fb, misc;
 };
 
 }  // namespace
@@ -286,7 +286,7 @@ std::vector<DevBuf*> device_buffers(recon_ctx* ctx)
             &ctx->red_partial, &ctx->vec, &ctx->med, &ctx->mu, &ctx->keep, &ctx->counter, &ctx->codes,
             &ctx->counts, &ctx->offsets, &ctx->base, &ctx->idx,
             &ctx->ev_reg, &ctx->lam_reg, &ctx->C_reg, &ctx->s_reg, &ctx->bf16_reg, &ctx->reg_vox_reg,
-            &ctx->tile_prep.code, &ctx->tile_prep.counts, &ctx->tile_prep.cursor, &ctx->tile_prep.begin,
+            &ctx->tile_prep.code, &ctx->tile_prep.counts, &ctx->tile_prep.rank, &ctx->tile_prep.begin,
             &ctx->tile_prep.scratch, &ctx->tile_prep.list, &ctx->tile_prep.ev_cell, &ctx->tile_prep.ev_fb,
             &ctx->tile_prep.misc};
 }
@@ -1549,7 +1549,7 @@ recon_status prepare_tiles(recon_ctx* ctx, int mode)
     const long long nb_max = (n + blocks - 1) / blocks;
     CK(ensure(tp.code, sizeof(unsigned) * (size_t)std::max(nb_max, 1LL)));
     CK(ensure(tp.counts, sizeof(unsigned) * (size_t)nc));
-    CK(ensure(tp.cursor, sizeof(unsigned) * (size_t)nc));
+    CK(ensure(tp.rank, sizeof(unsigned) * (size_t)std::max(nb_max, 1LL)));
     CK(ensure(tp.begin, sizeof(long long) * (size_t)(nc + 1)));
     CK(ensure(tp.scratch, sizeof(long long) * (size_t)scan_scratch_elems(nc)));
     CK(ensure(tp.list, sizeof(unsigned) * (size_t)nc));
@@ -1567,13 +1567,12 @@ recon_status prepare_tiles(recon_ctx* ctx, int mode)
             const void* src = static_cast<const char*>(ctx->ev.p) + (size_t)lo * rec;
             void* dst = static_cast<char*>(tp.ev_cell.p) + (size_t)lo * rec;
             CK(cudaMemsetAsync(tp.counts.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
-            CK(cudaMemsetAsync(tp.cursor.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
             CK(launch_cell_codes(src, ctx->fmt, hi - lo, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
-                                 tp.counts.as<unsigned>(), n_fb_dev, ctx->stream));
+                                 tp.counts.as<unsigned>(), tp.rank.as<unsigned>(), n_fb_dev, ctx->stream));
             CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
                                 ctx->stream));
             CK(launch_cell_scatter(src, ctx->fmt, hi - lo, tp.code.as<unsigned>(), tp.begin.as<long long>(),
-                                   tp.cursor.as<unsigned>(), dst, tp.ev_fb.p, fb_cursor, ctx->stream));
+                                   tp.rank.as<unsigned>(), dst, tp.ev_fb.p, fb_cursor, ctx->stream));
             ctx->stats.kernel_launches += 5;
         }
         tp.n_fb = 0;
@@ -1581,9 +1580,8 @@ recon_status prepare_tiles(recon_ctx* ctx, int mode)
         tp.n_binned = n;
     } else {
         CK(cudaMemsetAsync(tp.counts.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
-        CK(cudaMemsetAsync(tp.cursor.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
         CK(launch_cell_codes(ctx->ev.p, ctx->fmt, n, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
-                             tp.counts.as<unsigned>(), n_fb_dev, ctx->stream));
+                             tp.counts.as<unsigned>(), tp.rank.as<unsigned>(), n_fb_dev, ctx->stream));
         CK(launch_cell_list(tp.counts.as<unsigned>(), nc, (unsigned)ctx->tile_min_events, tp.list.as<unsigned>(),
                             n_list_dev, n_fb_dev, ctx->stream));
         CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
@@ -1599,7 +1597,7 @@ recon_status prepare_tiles(recon_ctx* ctx, int mode)
         CK(ensure(tp.ev_cell, rec * (size_t)std::max(binned, 1LL)));
         CK(ensure(tp.ev_fb, rec * (size_t)std::max(tp.n_fb, 1LL)));
         CK(launch_cell_scatter(ctx->ev.p, ctx->fmt, n, tp.code.as<unsigned>(), tp.begin.as<long long>(),
-                               tp.cursor.as<unsigned>(), tp.ev_cell.p, tp.ev_fb.p, fb_cursor, ctx->stream));
+                               tp.rank.as<unsigned>(), tp.ev_cell.p, tp.ev_fb.p, fb_cursor, ctx->stream));
         ctx->stats.kernel_launches += 7;
         tp.n_binned = binned;
     }

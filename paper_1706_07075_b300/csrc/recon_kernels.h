@@ -102,22 +102,24 @@ cudaError_t launch_pass(PassKind kind, EventFmt fmt, const LaunchCfg& cfg, const
                         const RegionTable& tbl, int num_sms, cudaStream_t s);
 
 // Tiled pass (k_tile_pass.cu).  Binning: code[i] = cell id, 0xFFFFFFFF (window misses
-// the grid) or 0xFFFFFFFE (fallback); counts[cell] += 1 (zero before); *n_fallback += 1.
+// the grid) or 0xFFFFFFFE (fallback); counts[cell] += 1 (zero before), rank[i] = the
+// count before event i's increment (its place within the cell); *n_fallback += 1.
 cudaError_t launch_cell_codes(const void* ev, int fmt, long long n, float lattice, const TileH& t, float half_window,
-                              unsigned* code, unsigned* counts, unsigned long long* n_fallback, cudaStream_t st);
+                              unsigned* code, unsigned* counts, unsigned* rank, unsigned long long* n_fallback,
+                              cudaStream_t st);
 // begin[c] = sum of counts before c (n_cells + 1 entries); block_sums: scratch of
 // scan_scratch_elems(n_cells) int64.
 long long scan_scratch_elems(long long n_cells);
 cudaError_t launch_cell_scan(const unsigned* counts, long long n_cells, long long* begin, long long* block_sums,
                              cudaStream_t st);
 // Cells with >= min_events events into list[*n_list]; smaller cells' counts are zeroed
-// and added to *n_fallback (run before the scan).  Scatter: events copied cell by cell
-// into ev_cell (cursor: n_cells zeros), the fallback events and those of zeroed cells
-// into ev_fb (*fb_cursor zero before).
+// and added to *n_fallback (run before the scan).  Scatter: event i of a kept cell c to
+// ev_cell[begin[c] + rank[i]], the fallback events and those of zeroed cells into
+// ev_fb (*fb_cursor zero before).
 cudaError_t launch_cell_list(unsigned* counts, long long n_cells, unsigned min_events, unsigned* list,
                              unsigned* n_list, unsigned long long* n_fallback, cudaStream_t st);
 cudaError_t launch_cell_scatter(const void* ev, int fmt, long long n, const unsigned* code, const long long* begin,
-                                unsigned* cursor, void* ev_cell, void* ev_fb, unsigned long long* fb_cursor,
+                                const unsigned* rank, void* ev_cell, void* ev_fb, unsigned long long* fb_cursor,
                                 cudaStream_t st);
 // One block per listed cell: events [begin[c], begin[c+1]) of ev_cell.  Shared memory:
 // 2 x tile_voxels floats.  Accumulates C and N_eff (a.partial, one region) like the fused pass.

@@ -37,18 +37,18 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-EVENT_BYTES = 68          # resident F32 event record (32 B), its cell-ordered copy (32 B) and cell code (4 B)
+EVENT_BYTES = 72          # resident F32 event record (32 B), its cell-ordered copy (32 B), cell code and rank (4 B each)
 IMAGE_BYTES_PER_VOXEL = 20  # lambda, C, s32 (4 B each) + s64 (8 B)
 # host events go up in chunks of at most 2^23 events through two staging halves of
 # 28 bytes per event each
 STAGING_CHUNK_EVENTS = 1 << 23
 STAGING_BYTES_PER_EVENT = 2 * 28
 # the library's default event order bins events by cells of 4^3 voxels and 16 x 8
-# direction bins; each bin key costs a count, a cursor, a list entry (4 B each) and
-# a 64-bit start
+# direction bins; each bin key costs a count, a list entry (4 B each) and a 64-bit
+# start
 ORDER_CELL_VOXELS = 4
 ORDER_DIRECTION_BINS = 16 * 8
-ORDER_KEY_BYTES = 20
+ORDER_KEY_BYTES = 16
 
 
 @dataclass

@@ -25,10 +25,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TOF-MLEM events x iterations / s (full-body, 146M events, 150x150x600 @ 4 mm)"
-# DRAM bytes per event of the fused pass: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture on 8 M full-body events (cell + direction order, 128 threads, series masses, the walk
-# set-up with the TOF point as an FP32 pair), per event
-TRAFFIC_BYTES_PER_EVENT = 49.2
+# Per event of the fused pass, from one ncu capture each on 8 M full-body events (cell and
+# direction order, 128 threads, series masses through h^4, walk in sigma units), by image
+# layout (0 linear, 1 2x2x2-brick copies): DRAM bytes (dram__bytes_read.sum +
+# dram__bytes_write.sum) and L2 requests (lts__t_requests_srcunit_tex_op_red.sum +
+# lts__t_requests_srcunit_tex_op_read.sum)
+NCU_PER_EVENT = {0: {"dram_bytes": 49.2, "l2_requests": 52.70},
+                 1: {"dram_bytes": 47.75, "l2_requests": 39.76}}
 # algorithmic FP32 operations per Siddon piece: ~25 for the step and the two
 # accumulations plus ~20 for the Gaussian mass of the piece
 ALU_OPS_PER_PIECE = 45.0
@@ -168,7 +171,7 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def roofline(n, visits, pass_ms, probes, hbm_peak_gbs, sm_mhz, traffic):
+def roofline(n, visits, pass_ms, probes, hbm_peak_gbs, sm_mhz, traffic, layout=0):
     """Roofline of the fused event pass as t_min / t_measured, t_min the largest of
     its algorithmic terms per launch: HBM (32 B per event), L2 reductions (one FP32
     reduction per Siddon piece at the live rate of scattered red.global.add.f32), L2
@@ -178,7 +181,14 @@ def roofline(n, visits, pass_ms, probes, hbm_peak_gbs, sm_mhz, traffic):
     reported but kept out of the maximum: it charges an L2 sector to every gather,
     while about a third of the gathers hit L1, so it is not a lower bound on the
     time.  `achieved` and `peak` are in the unit of the largest term; `traffic` is
-    the ncu DRAM bytes of the launch (or None)."""
+    the ncu DRAM bytes of the launch (or None).
+
+    The reduction rate is that of scattered reductions, one L2 request each.  In the
+    2x2x2-brick layout (layout 1) the lanes of a warp share sectors more often, so a
+    reduction costs less than one request and the element rate can pass that rate
+    (frac above 1).  `l2_requests` then reports the pass at the request level: the
+    ncu-measured requests per event of the layout, scaled to the launch, against the
+    same probe's request rate."""
     R, G, L2BW = probes.get("l2_red_gops"), probes.get("gather_gops"), probes.get("l2_stream_gbs")
     alu_peak = 148 * 128 * sm_mhz * 1e6                      # FP32 lane operations per second
     t = pass_ms / 1e3
@@ -198,7 +208,7 @@ def roofline(n, visits, pass_ms, probes, hbm_peak_gbs, sm_mhz, traffic):
         "bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk if pk else None,
         "traffic": traffic,
         "traffic_source": f"ncu capture of the same kernel on 8 M full-body events, "
-                          f"{TRAFFIC_BYTES_PER_EVENT:.1f} B per event, scaled to the launch's events",
+                          f"{NCU_PER_EVENT[layout]['dram_bytes']:.2f} B per event, scaled to the launch's events",
         "t_min_ms": 1e3 * terms[bound], "terms_ms": {k: 1e3 * v for k, v in terms.items()},
         "l2_sectors_ms_not_a_bound": sectors_ms,
         "per_launch": {"events": n, "pieces": visits, "gathers": visits, "reductions": visits,
@@ -208,6 +218,17 @@ def roofline(n, visits, pass_ms, probes, hbm_peak_gbs, sm_mhz, traffic):
                        "reads for the L2 bandwidth; HBM from MEASURED_PEAKS (driver-measured); ALU from "
                        "148 SMs x 128 lanes x the sampled SM clock",
         "mixed_probe_gsteps": probes.get("mixed_gsteps"),
+        "image_layout": ["linear", "2x2x2-brick copies"][layout],
+        "l2_requests": {"per_event": NCU_PER_EVENT[layout]["l2_requests"],
+                        "achieved_greq_s": NCU_PER_EVENT[layout]["l2_requests"] * n / t / 1e9,
+                        "ceiling_greq_s": R,
+                        "frac": NCU_PER_EVENT[layout]["l2_requests"] * n / t / 1e9 / R if R else None,
+                        "source": "reduction + read requests per event from ncu on 8 M full-body events "
+                                  "(this layout), scaled to the launch; ceiling: the scattered-reduction "
+                                  "probe, one request per reduction"},
+        "note": ("frac above 1: in the brick layout a warp's lanes share L2 sectors, so the reductions "
+                 "cost fewer requests than the scattered probe's one per reduction; see l2_requests"
+                 if R and visits / t / 1e9 > R else None),
         "secondary": {"hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak_gbs, "hbm_frac": hbm_gbs / hbm_peak_gbs}}
 
 
@@ -453,7 +474,7 @@ def launch_record(ctx_cfg, layout):
     """The event-pass launch the library used, every tuned dimension named."""
     return {"threads": ctx_cfg[0], "blocks_per_sm": ctx_cfg[1], "chunk": ctx_cfg[2], "cached_pieces": ctx_cfg[3],
             "piece_mass": ["fitted erfc tails", "erfcf tails", "midpoint series through h^6", "midpoint series through h^4"][ctx_cfg[4]],
-            "reduction": ["scalar, linear image", "per-brick-half vector, 2x2x2-brick copies"][ctx_cfg[5]],
+            "reduction": ["scalar, linear image", "scalar, 2x2x2-brick copies"][ctx_cfg[5]],
             "image_tiling": ["global image (L2-resident)", "shared-memory tiles"][layout[0]],
             "threads_per_event": layout[1]}
 
@@ -944,9 +965,10 @@ def run_ours(args):
         # The event pass issues one FP32 reduction into the L2-resident image per
         # Siddon piece (visits per launch = mean pieces per event x events) and
         # reads each 32-byte event record once from HBM.
-        traffic = TRAFFIC_BYTES_PER_EVENT * n if not args.samples else None
+        lay = int(cfg[5]) if not layout[0] else 0
+        traffic = NCU_PER_EVENT[lay]["dram_bytes"] * n if not args.samples and not layout[0] else None
         sm_mhz = (clocks.get("sm_mhz") or 2032.0) if isinstance(clocks, dict) else 2032.0
-        out["roofline"] = roofline(n, visits, pass_ms, probes, peaks["hbm_gbs"], sm_mhz, traffic)
+        out["roofline"] = roofline(n, visits, pass_ms, probes, peaks["hbm_gbs"], sm_mhz, traffic, lay)
         out["roofline"]["secondary"]["hbm_peak_source"] = src
         if args.samples:
             # the roofline above counts Siddon pieces: it describes the exact projector only

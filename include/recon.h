@@ -112,11 +112,12 @@ typedef struct {
     int32_t reduction;         /* recon_mlem's pass over one grid with FP32 gathers: 0 the linear image
                                   (exact projector: scalar FP32 reductions; sampled projector: x-adjacent
                                   pairs as red.global.add.v2.f32); 1 lambda and C in 2x2x2-voxel brick
-                                  copies (one 32-byte sector per brick), each lane's consecutive visits
-                                  within one 16-byte brick half gathered by one load and reduced by one
-                                  red.global.add.v4.f32 (same visits and weights; the sums run in another
-                                  order; for the exact projector only with a flat grid and no piece
-                                  cache; for the sampled projector the same as recon_set_brick_layout(1)).
+                                  copies (one 32-byte sector per brick), gathers and scalar FP32
+                                  reductions at brick-layout indices, so that the nearby lines of a
+                                  warp's events share sectors more often (same visits and weights; the
+                                  sums run in another order; for the exact projector only with a flat
+                                  grid and no piece cache; for the sampled projector the same as
+                                  recon_set_brick_layout(1)).
                                   Other passes use 0 */
     int32_t image_tiling;      /* reported by recon_get_launch, ignored by recon_set_launch: 1 when the
                                   last MLEM pass held lambda and C in shared-memory tiles of the event's
@@ -295,8 +296,8 @@ recon_status recon_set_gather_bf16(recon_ctx* ctx, int32_t on);
 
 /* Image layout of the sampled projector's MLEM pass (recon_mlem with RECON_PROJ_SAMPLED,
  * FP32 gathers): 0 (default) the linear layout; 1 copies of lambda and C in 2x2x2-voxel
- * bricks, one 32-byte sector per brick, so that a lane's consecutive samples within one
- * 16-byte brick half go out as one vector reduction (fewer L2 requests).  Each pass then
+ * bricks, one 32-byte sector per brick, so that the samples of a warp's nearby lines share
+ * sectors more often (fewer L2 requests, more L1 hits).  Each pass then
  * copies lambda into the bricks before and adds the brick copy of C into C after.  Same
  * visits and weights as the linear pass; the sums run in another order.  Not used by the
  * exact projector, with BF16 gathers, by recon_mlem_regions or by the first pass of a
@@ -320,8 +321,8 @@ recon_status recon_set_graphs(recon_ctx* ctx, int32_t on);
  * count, region count, event order, projector) with at least 2^20 events (1, default),
  * or use the default launch (0).  Candidates: threads per block,
  * flat or persistent grid, piece cache, piece-mass form and reduction form (scalar
- * into the linear image, or per-brick-half vector reductions over brick copies; the
- * latter with one grid and FP32 gathers), 17 in all, each timed over two passes (the
+ * into the linear image, or into 2x2x2-brick copies of lambda and C; the latter with one
+ * grid and FP32 gathers), 19 in all, each timed over two passes (the
  * brick candidates with their copy kernels).  For the sampled projector: 128, 192 or 256
  * threads per block, each with the linear image or the brick copies.  recon_mlem in the default event order
  * then also times the shared-memory tiled pass (recon_set_tiled_pass) with 1 and 8

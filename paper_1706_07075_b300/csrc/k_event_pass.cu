@@ -70,42 +70,14 @@ struct PieceCache {
     int stride;  // blockDim.x
 };
 
-// Reductions into a brick-layout image: a lane's consecutive visits that fall into
-// one 16-byte brick half are summed in registers and sent as one
-// red.global.add.v4.f32 (slots of the half it did not visit add 0).
-struct HalfRed {
-    float* base;
-    int half = -1;
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-    __device__ __forceinline__ void add(int q, float v)
-    {
-        const int h = q >> 2;
-        if (h != half) {
-            flush();
-            half = h;
-        }
-        const int slot = q & 3;
-        v0 += slot == 0 ? v : 0.f;
-        v1 += slot == 1 ? v : 0.f;
-        v2 += slot == 2 ? v : 0.f;
-        v3 += slot == 3 ? v : 0.f;
-    }
-    __device__ __forceinline__ void flush()
-    {
-        if (half >= 0)
-            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(base + 4LL * half), "f"(v0), "f"(v1),
-                         "f"(v2), "f"(v3)
-                         : "memory");
-        half = -1;
-        v0 = v1 = v2 = v3 = 0.f;
-    }
-};
-
 // One event of the exact projector over images in the brick layout (one grid,
-// FP32 gathers): the same pieces and masses as the linear pass; the gathers are
-// scalar loads from the brick image (L1 keeps a lane's brick half; a 16-byte
-// half cached in registers cost more instructions than it saved) and the
-// reductions go out per brick half.
+// FP32 gathers): the same pieces and masses as the linear pass, with gathers and
+// FP32 reductions at brick-layout indices.  A 32-byte sector holds a 2x2x2 brick,
+// so the nearby lines of a warp's events share sectors more often than in rows
+// of 8 voxels: fewer L2 requests per reduction and more L1 hits per gather.
+// (Merging a lane's consecutive visits of one 16-byte brick half into one
+// red.global.add.v4.f32, or caching the half for the gathers, cost more
+// instructions than it saved.)
 template <class TailF>
 __device__ __forceinline__ float do_event_brick(const PassArgs& a, const Event& e, const GridDev& g,
                                                 const TailF& tail)
@@ -123,9 +95,8 @@ __device__ __forceinline__ float do_event_brick(const PassArgs& a, const Event& 
     p *= hin;
     if (!(p > 0.f)) return 0.f;
     const float r = e.w / p * hin;
-    HalfRed hr{a.C};
-    walk_index<true>(g, tail, w, bi, [&](int q, float m) { hr.add(q, m * r); });
-    hr.flush();
+    float* const Cb = a.C;
+    walk_index<true>(g, tail, w, bi, [&](int q, float m) { atomicAdd(Cb + q, m * r); });
     return e.w;
 }
 
@@ -358,9 +329,8 @@ __device__ __forceinline__ void lut_walk(const GridDev& g, const LutH& lut, cons
 }
 
 // Fused pass over an image in the brick layout (one grid, FP32 gathers): the same
-// visits and weights as the linear pass; the reductions go out per brick half.  (A
-// register cache of the last 16-byte half for the gathers, as in the exact pass,
-// measured slower here: +24% instructions for 31% fewer L2 read requests.)
+// visits and weights as the linear pass, gathers and FP32 reductions at
+// brick-layout indices (see do_event_brick).
 template <int Fmt, int NS>
 __device__ __forceinline__ float do_event_lut_brick(const PassArgs& a, const SharedTable& t, long long i,
                                                     int& region)
@@ -375,10 +345,9 @@ __device__ __forceinline__ float do_event_lut_brick(const PassArgs& a, const Sha
         g, a.lut, l, [&](int q, float w) { p = fmaf(w, __ldg(lb + q), p); }, a.brick_bx, a.brick_by);
     if (!(p > 0.f)) return 0.f;
     const float r = e.w / p;
-    HalfRed hr{a.C};
+    float* const Cb = a.C;
     lut_walk<NS, true>(
-        g, a.lut, l, [&](int q, float w) { hr.add(q, w * r); }, a.brick_bx, a.brick_by);
-    hr.flush();
+        g, a.lut, l, [&](int q, float w) { atomicAdd(Cb + q, w * r); }, a.brick_bx, a.brick_by);
     return e.w;
 }
 

@@ -510,7 +510,7 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
 {
     NvtxRange nvtx_range("autotune");
     // sampled projector: threads per block, and the linear image (x-pair vector
-    // reductions) or the brick copies (per-half vector reductions)
+    // reductions) or the brick copies
     const std::vector<LaunchCfg> lut_cands = {
         {128, 0, 0, 0, TAIL_FIT, 0}, {192, 0, 0, 0, TAIL_FIT, 0}, {256, 0, 0, 0, TAIL_FIT, 0},
         {128, 0, 0, 0, TAIL_FIT, 1}, {192, 0, 0, 0, TAIL_FIT, 1}, {256, 0, 0, 0, TAIL_FIT, 1},
@@ -522,9 +522,10 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
         {192, 0, 0, 0, TAIL_FIT}, {128, 8, 64, 0, TAIL_FIT}, {64, 0, 0, 64, TAIL_FIT},
         {128, 0, 0, 0, TAIL_ERFC}, {256, 0, 0, 0, TAIL_ERFC}, {128, 0, 0, 0, TAIL_SERIES},
         {256, 0, 0, 0, TAIL_SERIES}, {192, 0, 0, 0, TAIL_SERIES},
-        // brick copies of lambda and C with per-half vector reductions
         {128, 0, 0, 0, TAIL_SERIES4}, {192, 0, 0, 0, TAIL_SERIES4},
-        {128, 0, 0, 0, TAIL_SERIES, 1}, {192, 0, 0, 0, TAIL_SERIES, 1}, {256, 0, 0, 0, TAIL_SERIES, 1},
+        // brick copies of lambda and C (a 2x2x2 brick per 32-byte sector)
+        {128, 0, 0, 0, TAIL_SERIES4, 1}, {192, 0, 0, 0, TAIL_SERIES4, 1}, {256, 0, 0, 0, TAIL_SERIES4, 1},
+        {128, 0, 0, 0, TAIL_SERIES, 1}, {192, 0, 0, 0, TAIL_SERIES, 1},
         {128, 0, 0, 0, TAIL_FIT, 1},
     };
     const std::vector<LaunchCfg>& cands = a.lut.n > 0 ? lut_cands : exact_cands;

@@ -64,8 +64,8 @@ struct LaunchCfg {
     int chunk;         // events per work-queue grab (persistent), multiple of 32
     int cache;         // pieces per thread kept in shared memory for the backprojection (0: walk twice)
     int tail;          // TailEval: how the Gaussian tails are evaluated
-    int reduction;     // 0: scalar reductions into the linear image; 1: lambda and C in 2x2x2-brick copies,
-                       // gathers of 16-byte brick halves and one vector reduction per brick half
+    int reduction;     // 0: the linear image; 1: lambda and C in 2x2x2-brick copies (one brick per
+                       // 32-byte sector), gathers and scalar reductions at brick-layout indices
 };
 
 struct PassArgs {

@@ -1,7 +1,6 @@
 """The exact projector's pass over 2x2x2-voxel brick copies of lambda and C
 (recon_launch.reduction = 1): the same Siddon pieces and TOF masses as the linear
-pass; each lane's consecutive pieces within one 16-byte brick half are gathered by
-one 16-byte load and reduced by one vector reduction, so the sums run in another
+pass, gathered and reduced at brick-layout indices, so the FP32 sums run in another
 order.  Held to the plain gates against the FP64 oracle (Sec. 2.4 MLEM) and to
 1e-5 relative L2 against the linear pass (FP32 summation order only)."""
 import numpy as np

@@ -133,7 +133,7 @@ def _oracle_lut_mlem_tiny(g, ev, s_ref):
 @pytest.mark.parametrize("graphs", [1, 0])
 def test_mlem_lut_brick_layout_matches_oracle(tiny, graphs):
     # the sampled pass over 2x2x2-brick copies of lambda and C: the same visits and
-    # weights, reductions per 16-byte brick half.  Resident events (every pass in
+    # weights at brick-layout indices.  Resident events (every pass in
     # bricks) and host events (the streamed first pass linear, the rest in bricks).
     g, ev, lors, ctx = tiny
     ev = lut_unambiguous(g, ev, 32)
@@ -288,7 +288,7 @@ def test_region_mlem_lut_with_sieve_matches_oracle():
 
 def test_mlem_lut_autotuned_matches_oracle():
     # enough events for the autotuner (at least 2^20): it picks threads per block and
-    # the image layout (linear, or 2x2x2-brick copies with per-half vector reductions)
+    # the image layout (linear, or 2x2x2-brick copies of lambda and C)
     # for the sampled projector; whatever it picks, the image holds the plain gates
     g = workload_grid("tiny")
     ev = lut_unambiguous(g, synth.events("tiny", 1_400_000, 29), 32)

@@ -100,6 +100,16 @@ def test_bench_roofline_terms_and_fraction():
     r2 = bench.roofline(n, visits, pass_ms, slow, 6506.9, 2032.0, None)
     assert r2["bound"] == "l2_gathers" and r2["unit"] == "Ggather/s" and r2["traffic"] is None
     assert r2["frac"] == pytest.approx(r2["terms_ms"]["l2_gathers"] / pass_ms)
+    # request level: the layout's ncu requests per event over the same probe rate; no
+    # note while the element rate stays below the scattered rate
+    q = r["l2_requests"]
+    assert q["achieved_greq_s"] == pytest.approx(bench.NCU_PER_EVENT[0]["l2_requests"] * n / (pass_ms / 1e3) / 1e9)
+    assert q["frac"] == pytest.approx(q["achieved_greq_s"] / 230.8) and r["note"] is None
+    # the brick layout at 26.6 ms: more reductions per second than the scattered probe
+    # (frac above 1, with the note), while its requests stay below the request rate
+    rb = bench.roofline(n, visits, 26.57, probes, 6506.9, 2032.0, None, layout=1)
+    assert rb["frac"] > 1.0 and rb["note"] and rb["image_layout"] == "2x2x2-brick copies"
+    assert rb["l2_requests"]["frac"] < 1.0
 
 
 def test_fullsize_sampled_voxel_references_match_brute_force():

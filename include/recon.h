@@ -109,7 +109,8 @@ typedef struct {
                                   for pieces up to 0.4 sigma).  Without a fixed launch the library uses
                                   2 only when the voxel diagonal is at most 0.5 sigma, else 0; the
                                   autotuner tries 3 where the diagonal is at most 0.4 sigma and K <= 3 */
-    int32_t reduction;         /* recon_mlem's pass over one grid with FP32 gathers: 0 the linear image
+    int32_t reduction;         /* the MLEM pass with FP32 gathers (recon_mlem; for the exact projector
+                                  also recon_mlem_regions, each slab in its own brick copy): 0 the linear image
                                   (exact projector: scalar FP32 reductions; sampled projector: x-adjacent
                                   pairs as red.global.add.v2.f32); 1 lambda and C in 2x2x2-voxel brick
                                   copies (one 32-byte sector per brick), gathers and scalar FP32
@@ -321,8 +322,8 @@ recon_status recon_set_graphs(recon_ctx* ctx, int32_t on);
  * count, region count, event order, projector) with at least 2^20 events (1, default),
  * or use the default launch (0).  Candidates: threads per block,
  * flat or persistent grid, piece cache, piece-mass form and reduction form (scalar
- * into the linear image, or into 2x2x2-brick copies of lambda and C; the latter with one
- * grid and FP32 gathers), 19 in all, each timed over two passes (the
+ * into the linear image, or into 2x2x2-brick copies of lambda and C; the latter with FP32
+ * gathers, one brick copy per region slab), 19 in all, each timed over two passes (the
  * brick candidates with their copy kernels).  For the sampled projector: 128, 192 or 256
  * threads per block, each with the linear image or the brick copies.  recon_mlem in the default event order
  * then also times the shared-memory tiled pass (recon_set_tiled_pass) with 1 and 8

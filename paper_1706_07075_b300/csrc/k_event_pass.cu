@@ -89,13 +89,14 @@ __device__ __forceinline__ float do_event_brick(const PassArgs& a, const Event& 
     if constexpr (TailF::kSigmaUnits) scale_walk(w, tail.inv_sigma());
     const float hin = a.tof.half_inv_norm * TailF::kMassScale;
     const BrickIndex bi(w, a.brick_bx, a.brick_by);
-    const float* const lb = a.lam;
+    // a region's slab: its grid's voxel offset is the slab's place in the brick copies
+    const float* const lb = a.lam + g.vox_offset;
     float p = 0.f;
     walk_index<true>(g, tail, w, bi, [&](int q, float m) { p = fmaf(m, __ldg(lb + q), p); });
     p *= hin;
     if (!(p > 0.f)) return 0.f;
     const float r = e.w / p * hin;
-    float* const Cb = a.C;
+    float* const Cb = a.C + g.vox_offset;
     walk_index<true>(g, tail, w, bi, [&](int q, float m) { atomicAdd(Cb + q, m * r); });
     return e.w;
 }
@@ -456,9 +457,9 @@ cudaError_t launch_tail(int blocks, const LaunchCfg& cfg, const PassArgs& a, con
 {
     const bool persistent = cfg.blocks_per_sm > 0;
     if (a.brick_bx > 0) {
-        // brick layout: fused pass over one grid, FP32 gathers, flat grid, no piece cache
-        if (Kind != PASS_FUSED || tbl.n != 1 || a.lam_bf16 || tbl.grid[0].vox_offset != 0 || persistent ||
-            cfg.cache > 0)
+        // brick layout: fused pass, FP32 gathers, flat grid, no piece cache; each grid's
+        // voxel offset is its slab's offset in the brick copies
+        if (Kind != PASS_FUSED || tbl.n < 1 || a.lam_bf16 || persistent || cfg.cache > 0)
             return cudaErrorInvalidValue;
         if constexpr (Kind == PASS_FUSED) {
             k_event_pass<PASS_FUSED, Fmt, false, false, TailK, true><<<blocks, cfg.threads, 0, s>>>(a, tbl, cfg.chunk,

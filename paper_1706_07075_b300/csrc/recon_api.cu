@@ -461,6 +461,41 @@ bool valid_cfg(const recon_launch* c)
     return true;
 }
 
+// The brick copies of a table's slabs (2x2x2 bricks per slab, slabs one after the
+// other): bt is t with each grid's voxel offset replaced by its slab's offset in the
+// copies; returns the brick voxels of all slabs.
+long long brick_table(const RegionTable& t, RegionTable& bt)
+{
+    bt = t;
+    long long off = 0;
+    for (int r = 0; r < t.n; ++r) {
+        bt.grid[r].vox_offset = off;
+        off += brick_voxels(t.grid[r].nx, t.grid[r].ny, t.grid[r].nz);
+    }
+    return off;
+}
+
+// lambda of every slab into its brick copy, and the brick copies of C added into C.
+cudaError_t to_bricks_all(const float* lin, float* br, const RegionTable& t, const RegionTable& bt, cudaStream_t s)
+{
+    for (int r = 0; r < t.n; ++r) {
+        const cudaError_t e = launch_to_bricks(lin + t.grid[r].vox_offset, br + bt.grid[r].vox_offset, t.grid[r].nx,
+                                               t.grid[r].ny, t.grid[r].nz, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t from_bricks_add_all(float* br, float* lin, const RegionTable& t, const RegionTable& bt, cudaStream_t s)
+{
+    for (int r = 0; r < t.n; ++r) {
+        const cudaError_t e = launch_from_bricks_add(br + bt.grid[r].vox_offset, lin + t.grid[r].vox_offset,
+                                                     t.grid[r].nx, t.grid[r].ny, t.grid[r].nz, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 RegionTable single_table(const recon_ctx* ctx)
 {
     RegionTable t;
@@ -529,15 +564,15 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
         {128, 0, 0, 0, TAIL_FIT, 1},
     };
     const std::vector<LaunchCfg>& cands = a.lut.n > 0 ? lut_cands : exact_cands;
-    // the brick form needs one grid at offset 0 and FP32 gathers; its candidates are
-    // timed with the two copy kernels around the pass
-    const bool brick_ok = tbl.n == 1 && tbl.grid[0].vox_offset == 0 && !a.lam_bf16;
-    const recon_grid& gr = ctx->grid;
+    // the brick form needs FP32 gathers (and one grid for the sampled projector); its
+    // candidates are timed with the copy kernels around the pass
+    const bool brick_ok = !a.lam_bf16 && (tbl.n == 1 ? tbl.grid[0].vox_offset == 0 : a.lut.n == 0);
+    RegionTable btbl;
+    const long long nb = brick_table(tbl, btbl);
     if (brick_ok) {
-        const size_t nb = (size_t)brick_voxels(gr.nx, gr.ny, gr.nz);
-        CK(ensure(ctx->lam_brick, sizeof(float) * nb));
-        CK(ensure(ctx->C_brick, sizeof(float) * nb));
-        CK(cudaMemsetAsync(ctx->C_brick.p, 0, sizeof(float) * nb, ctx->stream));
+        CK(ensure(ctx->lam_brick, sizeof(float) * (size_t)nb));
+        CK(ensure(ctx->C_brick, sizeof(float) * (size_t)nb));
+        CK(cudaMemsetAsync(ctx->C_brick.p, 0, sizeof(float) * (size_t)nb, ctx->stream));
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -561,24 +596,22 @@ recon_status autotune(recon_ctx* ctx, PassArgs a, const RegionTable& tbl, Launch
         if (c.reduction == 1) {
             ab.lam = ctx->lam_brick.as<float>();
             ab.C = ctx->C_brick.as<float>();
-            ab.brick_bx = (gr.nx + 1) / 2;
-            ab.brick_by = (gr.ny + 1) / 2;
+            ab.brick_bx = (tbl.grid[0].nx + 1) / 2;
+            ab.brick_by = (tbl.grid[0].ny + 1) / 2;
         }
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
             CK(cudaEventRecord(e0, ctx->stream));
-            if (c.reduction == 1) {
-                CK(launch_to_bricks(ac.lam, ctx->lam_brick.as<float>(), gr.nx, gr.ny, gr.nz, ctx->stream));
-            }
-            CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, c, c.reduction == 1 ? ab : ac, tbl, ctx->num_sms,
-                           ctx->stream));
-            if (c.reduction == 1) CK(launch_from_bricks_add(ab.C, ac.C, gr.nx, gr.ny, gr.nz, ctx->stream));
+            if (c.reduction == 1) CK(to_bricks_all(ac.lam, ctx->lam_brick.as<float>(), tbl, btbl, ctx->stream));
+            CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, c, c.reduction == 1 ? ab : ac,
+                           c.reduction == 1 ? btbl : tbl, ctx->num_sms, ctx->stream));
+            if (c.reduction == 1) CK(from_bricks_add_all(ab.C, ac.C, tbl, btbl, ctx->stream));
             CK(cudaEventRecord(e1, ctx->stream));
             CK(cudaEventSynchronize(e1));
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, e0, e1));
             ms_min = std::min(ms_min, ms);
-            ctx->stats.kernel_launches += c.reduction == 1 ? 3 : 1;
+            ctx->stats.kernel_launches += c.reduction == 1 ? 1 + 2 * tbl.n : 1;
         }
         if (ms_min < best_ms) {
             best_ms = ms_min;
@@ -665,21 +698,23 @@ recon_status launch_event_pass_layout(recon_ctx* ctx, const IterPlan& p, const P
 }
 
 // The event pass in the image layout of the plan: with bricks, lambda is copied into
-// the brick layout first, the pass reduces into the brick copy of C, and that copy
-// is added into C (and cleared) afterwards.
+// the brick layout first (each region's slab into its own brick copy), the pass
+// reduces into the brick copies of C, and those are added into C (and cleared)
+// afterwards.
 recon_status launch_event_pass(recon_ctx* ctx, const IterPlan& p, const PassArgs& a, const RegionTable& t)
 {
     if (!p.bricks) return launch_event_pass_layout(ctx, p, a, t);
-    const recon_grid& g = ctx->grid;
-    CK(launch_to_bricks(a.lam, ctx->lam_brick.as<float>(), g.nx, g.ny, g.nz, ctx->stream));
+    RegionTable bt;
+    brick_table(t, bt);
+    CK(to_bricks_all(a.lam, ctx->lam_brick.as<float>(), t, bt, ctx->stream));
     PassArgs ab = a;
     ab.lam = ctx->lam_brick.as<float>();
     ab.C = ctx->C_brick.as<float>();
-    ab.brick_bx = (g.nx + 1) / 2;
-    ab.brick_by = (g.ny + 1) / 2;
-    recon_status s = launch_event_pass_layout(ctx, p, ab, t);
+    ab.brick_bx = (t.grid[0].nx + 1) / 2;
+    ab.brick_by = (t.grid[0].ny + 1) / 2;
+    recon_status s = launch_event_pass_layout(ctx, p, ab, bt);
     if (s != RECON_OK) return s;
-    CK(launch_from_bricks_add(ctx->C_brick.as<float>(), a.C, g.nx, g.ny, g.nz, ctx->stream));
+    CK(from_bricks_add_all(ctx->C_brick.as<float>(), a.C, t, bt, ctx->stream));
     return RECON_OK;
 }
 
@@ -781,7 +816,7 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool 
                 CK(launch_finalize(p.a.partial, kNeffSlots, ctx->upd_partial.as<double>(), p.upd_bpr, p.n_regions,
                                    p.hist, p.iter, p.hist_cap, ctx->stream));
                 ctx->stats.kernel_launches += (a.n > 0 ? 3 : 2) + (p.med && b == B - 1 ? 1 : 0) +
-                                              (p.tiled && p.n_fb > 0 ? 1 : 0) + (p.bricks ? 2 : 0);
+                                              (p.tiled && p.n_fb > 0 ? 1 : 0) + (p.bricks ? 2 * p.tbl.n : 0);
             }
         }
         if (ctx->timing) {
@@ -820,7 +855,7 @@ recon_status run_iterations(recon_ctx* ctx, const IterPlan& p, int n_iter, bool 
     }
     for (int k = 0; k < n_iter; ++k) {
         CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
-        ctx->stats.kernel_launches += (long long)p.subsets * ((p.pass_blocks > 0 ? 3 : 2) + (p.bricks ? 2 : 0)) +
+        ctx->stats.kernel_launches += (long long)p.subsets * ((p.pass_blocks > 0 ? 3 : 2) + (p.bricks ? 2 * p.tbl.n : 0)) +
                                       (p.med ? 1 : 0) + (p.tiled && p.n_fb > 0 ? 1 : 0);
     }
     return RECON_OK;
@@ -1649,7 +1684,7 @@ recon_status time_event_pass(recon_ctx* ctx, const IterPlan& p, float* ms_out)
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, e0, e1));
         best = std::min(best, ms);
-        ctx->stats.kernel_launches += 1 + (p.tiled && p.n_fb > 0 ? 1 : 0) + (p.bricks ? 2 : 0);
+        ctx->stats.kernel_launches += 1 + (p.tiled && p.n_fb > 0 ? 1 : 0) + (p.bricks ? 2 * p.tbl.n : 0);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1985,7 +2020,7 @@ recon_status mlem_impl(recon_ctx* ctx, const recon_events* events, int32_t n_ite
         ctx->last_lanes = ctx->last_tiling ? p.lanes : 1;
         s = launch_event_pass(ctx, p, p.a, p.tbl);
         if (s != RECON_OK) return s;
-        ctx->stats.kernel_launches += 1 + (p.tiled && p.n_fb > 0 ? 1 : 0) + (p.bricks ? 2 : 0);
+        ctx->stats.kernel_launches += 1 + (p.tiled && p.n_fb > 0 ? 1 : 0) + (p.bricks ? 2 * p.tbl.n : 0);
         CK(cudaMemcpyAsync(po->C_out, ctx->C.p, sizeof(float) * nv, cudaMemcpyDefault, ctx->stream));
         double n_eff = 0;
         s = host_sum(ctx, ctx->pass_partial.as<double>(), kNeffSlots, &n_eff);
@@ -2279,6 +2314,16 @@ recon_status recon_mlem_regions(recon_ctx* ctx, const recon_events* events, int3
         p.cfg = choose_cfg(ctx, ta, p.tbl, &s);
     }
     if (s != RECON_OK) return s;
+    // the exact projector's brick layout (the launch's reduction form): each slab in its
+    // own 2x2x2-brick copy
+    p.bricks = ctx->lut_n == 0 && p.cfg.reduction == 1 && !ctx->bf16 && p.cfg.blocks_per_sm == 0 && p.cfg.cache == 0;
+    if (p.bricks) {
+        RegionTable bt;
+        const long long nb = brick_table(p.tbl, bt);
+        CK(ensure(ctx->lam_brick, sizeof(float) * (size_t)nb));
+        CK(ensure(ctx->C_brick, sizeof(float) * (size_t)nb));
+        CK(cudaMemsetAsync(ctx->C_brick.p, 0, sizeof(float) * (size_t)nb, ctx->stream));
+    }
     CK(cudaMemsetAsync(ctx->C_reg.p, 0, sizeof(float) * nvt, ctx->stream));
     CK(cudaMemsetAsync(ctx->pass_partial.p, 0, sizeof(double) * kNeffSlots * R, ctx->stream));
     p.pass_blocks = pass_blocks(p.cfg, total, ctx->num_sms);

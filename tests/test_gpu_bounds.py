@@ -51,6 +51,9 @@ def run(geo, g, ev, lors, extra=None):
         nz = g.nz
         regions = [(0, nz // 3), (nz // 3, 2 * nz // 3), (2 * nz // 3, nz)]
         ctx.mlem_regions(None, regions, 3 * 19.0965 + 6.0, 6.0, 2)
+        ctx.set_launch(128, 0, 0, 0, 3, 1)            # every slab over its own brick copies
+        ctx.mlem_regions(None, regions, 3 * 19.0965 + 6.0, 6.0, 2)
+        ctx.set_launch(None)
         ctx.preprocess(None, np.full(g.n_vox, 0.0096, np.float32), 1.96, 0)
         if extra:
             extra(ctx)

@@ -65,7 +65,10 @@ def test_split_bitexact_fullbody(packed):
     assert counts.min() > 0 and offs[-1] >= n * 0.95
 
 
-def test_region_mlem_matches_oracle_tiny():
+@pytest.mark.parametrize("launch", [None, (128, 0, 0, 0, 2, 1), (192, 0, 0, 0, 3, 1)])
+def test_region_mlem_matches_oracle_tiny(launch):
+    # launch None: the default; the others run every slab over its own 2x2x2-brick
+    # copies of lambda and C (reduction 1) with the two series mass forms
     ev = synth.events("tiny", 120_000, 17)
     lors = synth.sensitivity_lors("tiny", 500_000, 17)
     g = workload_grid("tiny")
@@ -81,7 +84,11 @@ def test_region_mlem_matches_oracle_tiny():
         img = np.zeros(g.n_vox, np.float32)
         slabs = np.zeros(nslab, np.float32)
         cons = np.zeros((3, 3, 2))
+        if launch:
+            ctx.set_launch(*launch)
         ctx.mlem_regions(B.make_events(ev), regions, margin, 6.0, 3, img, slabs, cons)
+        if launch:
+            assert tuple(ctx.get_launch())[:6] == launch
     assert rel_l2(img, img_ref) <= 1e-4
     assert max_rel_above(img, img_ref, 0.01) <= 1e-3
     assert rel_l2(slabs, np.concatenate(imgs_ref)) <= 1e-4

@@ -98,6 +98,11 @@ struct TilePrep {
     long long n_binned = 0;
     int mode = 0;
     int subsets = 1;
+    // cell codes, ranks and counts of the event order computed during a streamed
+    // upload (stream_pass), for this event generation, cell geometry and window
+    long long codes_gen = -1;
+    TileH codes_th{};
+    double codes_hw = 0;
     DevBuf code, counts, rank, begin, scratch, list, ev_cell, ev_fb, misc;
 };
 
@@ -1602,14 +1607,23 @@ recon_status prepare_tiles(recon_ctx* ctx, int mode)
             if (hi <= lo) continue;
             const void* src = static_cast<const char*>(ctx->ev.p) + (size_t)lo * rec;
             void* dst = static_cast<char*>(tp.ev_cell.p) + (size_t)lo * rec;
-            CK(cudaMemsetAsync(tp.counts.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
-            CK(launch_cell_codes(src, ctx->fmt, hi - lo, (float)ctx->lattice, t, (float)hw, tp.code.as<unsigned>(),
-                                 tp.counts.as<unsigned>(), tp.rank.as<unsigned>(), n_fb_dev, ctx->stream));
+            // a streamed upload may have computed the codes already, chunk by chunk
+            const bool have_codes = blocks == 1 && tp.codes_gen == ctx->ev_generation && tp.codes_hw == hw &&
+                                    tp.codes_th.cs == t.cs && tp.codes_th.ncx == t.ncx && tp.codes_th.ncy == t.ncy &&
+                                    tp.codes_th.ncz == t.ncz && tp.codes_th.dir_az == t.dir_az &&
+                                    tp.codes_th.dir_pol == t.dir_pol;
+            tp.codes_gen = -1;
+            if (!have_codes) {
+                CK(cudaMemsetAsync(tp.counts.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
+                CK(launch_cell_codes(src, ctx->fmt, hi - lo, (float)ctx->lattice, t, (float)hw,
+                                     tp.code.as<unsigned>(), tp.counts.as<unsigned>(), tp.rank.as<unsigned>(), n_fb_dev,
+                                     ctx->stream));
+            }
             CK(launch_cell_scan(tp.counts.as<unsigned>(), nc, tp.begin.as<long long>(), tp.scratch.as<long long>(),
                                 ctx->stream));
             CK(launch_cell_scatter(src, ctx->fmt, hi - lo, tp.code.as<unsigned>(), tp.begin.as<long long>(),
                                    tp.rank.as<unsigned>(), dst, tp.ev_fb.p, fb_cursor, ctx->stream));
-            ctx->stats.kernel_launches += 5;
+            ctx->stats.kernel_launches += have_codes ? 4 : 5;
         }
         tp.n_fb = 0;
         tp.n_list = 0;
@@ -1720,7 +1734,7 @@ recon_status begin_streamed_events(recon_ctx* ctx, const recon_events* e)
     return RECON_OK;
 }
 
-recon_status stream_pass(recon_ctx* ctx, const recon_events* e, const IterPlan& p)
+recon_status stream_pass(recon_ctx* ctx, const recon_events* e, const IterPlan& p, bool bin_after)
 {
     NvtxRange nvtx_range("streamed first pass");
     if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
@@ -1737,6 +1751,23 @@ recon_status stream_pass(recon_ctx* ctx, const recon_events* e, const IterPlan& 
     // staging may still be read by earlier work on ctx->stream
     CK(cudaEventRecord(ctx->ready, ctx->stream));
     CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ready, 0));
+    // when iterations in the default event order follow, the events' cell codes are
+    // computed chunk by chunk as the chunks arrive (hidden under the copies), so the
+    // binning after the upload only scans and scatters
+    TilePrep& tp = ctx->tile_prep;
+    tp.codes_gen = -1;
+    TileH tc{};
+    const double hw = (double)make_tof(ctx).half_window;
+    const bool codes = bin_after && ctx->tile_mode == 2 && ctx->subsets == 1 && tile_params(ctx, 2, &tc);
+    if (codes) {
+        const long long nc = (long long)tc.ncx * tc.ncy * tc.ncz * tc.dir_az * tc.dir_pol + 1;
+        CK(ensure(tp.code, sizeof(unsigned) * (size_t)n));
+        CK(ensure(tp.rank, sizeof(unsigned) * (size_t)n));
+        CK(ensure(tp.counts, sizeof(unsigned) * (size_t)nc));
+        CK(ensure(tp.misc, 64));
+        CK(cudaMemsetAsync(tp.counts.p, 0, sizeof(unsigned) * (size_t)nc, ctx->stream));
+        CK(cudaMemsetAsync(tp.misc.p, 0, 64, ctx->stream));
+    }
     int q = 0;
     for (long long lo = 0; lo < n; lo += chunk, q ^= 1) {
         const long long m = std::min(chunk, n - lo);
@@ -1770,6 +1801,17 @@ recon_status stream_pass(recon_ctx* ctx, const recon_events* e, const IterPlan& 
         if (p.cfg.blocks_per_sm > 0) CK(cudaMemsetAsync(ctx->work.p, 0, 8, ctx->stream));
         CK(launch_pass(PASS_FUSED, (EventFmt)ctx->fmt, p.cfg, a, t, ctx->num_sms, ctx->stream));
         ctx->stats.kernel_launches += 2;
+        if (codes) {
+            CK(launch_cell_codes(a.events, ctx->fmt, m, (float)ctx->lattice, tc, (float)hw,
+                                 tp.code.as<unsigned>() + lo, tp.counts.as<unsigned>(), tp.rank.as<unsigned>() + lo,
+                                 tp.misc.as<unsigned long long>(), ctx->stream));
+            ctx->stats.kernel_launches += 1;
+        }
+    }
+    if (codes) {
+        tp.codes_gen = ctx->ev_generation;
+        tp.codes_th = tc;
+        tp.codes_hw = hw;
     }
     // first update (the pass above was its event pass)
     CK(cudaMemsetAsync(p.iter, 0, sizeof(int), ctx->stream));
@@ -2032,7 +2074,7 @@ recon_status mlem_impl(recon_ctx* ctx, const recon_events* events, int32_t n_ite
         return RECON_OK;
     }
     if (streamed) {
-        s = stream_pass(ctx, events, p);
+        s = stream_pass(ctx, events, p, n_iter > 1);
         if (s != RECON_OK) return s;
         ctx->have_ev = true;
         if (n_iter > 1) {

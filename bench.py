@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="run the served-reconstruction workload (Poisson stream of mixed jobs) instead")
     ap.add_argument("--serve-jobs", type=int, default=200)
+    ap.add_argument("--smallfov-only", action="store_true",
+                    help="time only the small field of view (128^3 voxels of 0.5 mm, 5 M events); with --launch "
+                         "the launch is fixed instead of tuned")
     ap.add_argument("--shard", default="replicas", choices=["replicas", "events", "regions"],
                     help="with N GPUs: replicas (each rank reconstructs its own 146M events, weak scaling), "
                          "events (one 146M-event job, each rank a shard of the events, one all-reduce of C per "
@@ -490,6 +493,10 @@ def time_smallfov_leg(B, synth, args, stream):
         c.set_stream(stream.cuda_stream)
         c.sensitivity(lors)
         c.load_events(B.make_events(ev))
+        if args.smallfov_only and args.launch:
+            c.set_launch(*[int(x) for x in args.launch.split(",")])
+        if args.smallfov_only and args.no_graphs:
+            c.set_graphs(0)
         cons = np.zeros((args.iters, 2))
         c.mlem(None, args.iters, None, None, cons)          # warm-up (+ autotune for this key)
         ms = _timed_steps(stream, args.steps, lambda: c.mlem(None, args.iters, None, None, cons))
@@ -992,6 +999,13 @@ def main():
         return run_reference(args)
     if args.serve:
         return run_serve(args)
+    if args.smallfov_only:
+        import torch
+        from paper_1706_07075_b300 import binding as B
+        from paper_1706_07075_b300 import synth
+        stream = torch.cuda.Stream()
+        print(json.dumps({"smallfov": time_smallfov_leg(B, synth, args, stream)}), flush=True)
+        return 0
     return run_ours(args)
 
 

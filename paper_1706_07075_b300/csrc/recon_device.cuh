@@ -207,9 +207,26 @@ struct Walk {
     bool valid;
 };
 
+// tau_out lowered to the first crossing past each axis's budget, computed as the
+// walk computes its crossings: after r_k crossings on axis k the walk's next
+// crossing there is fmaf(r_k, dt_k, t0_k), and fmaf is monotone in its first
+// argument (dt_k > 0), so every crossing past the budget lies at or beyond tau_out
+// and the walk ends before it steps out of the grid.  This replaces a budget test
+// per piece and axis.  Within the grid the exit crossing and the clipped tau_out
+// agree up to rounding.  An axis with no crossing has t0 = inf; a NaN exit (an
+// infinite spacing) is ignored by fminf, and such an axis is stepped at most once.
+__device__ __forceinline__ void clip_to_budgets(Walk& w)
+{
+    const float ex = w.rx > 0.f ? fmaf(w.rx, w.dtx, w.t0x) : w.t0x;
+    const float ey = w.ry > 0.f ? fmaf(w.ry, w.dty, w.t0y) : w.t0y;
+    const float ez = w.rz > 0.f ? fmaf(w.rz, w.dtz, w.t0z) : w.t0z;
+    w.tau_out = fminf(w.tau_out, fminf(ex, fminf(ey, ez)));
+}
+
 // The walk's parameter rescaled by s (tau -> s tau): clip range, first crossings
 // and crossing spacings; infinities stay infinite.  The voxel sequence and the
-// crossing counts do not change.
+// crossing counts do not change; the budget clip is taken again on the scaled
+// values, which the walk then steps with.
 __device__ __forceinline__ void scale_walk(Walk& w, float s)
 {
     w.tau_in *= s;
@@ -220,6 +237,7 @@ __device__ __forceinline__ void scale_walk(Walk& w, float s)
     w.dtx *= s;
     w.dty *= s;
     w.dtz *= s;
+    clip_to_budgets(w);
 }
 
 // The TOF point c = M + d u of an event as an unevaluated sum c + c_lo of two
@@ -350,12 +368,14 @@ __device__ __forceinline__ Walk make_walk(const GridDev& g, const Line& l, float
     w.t0x = t0[0]; w.t0y = t0[1]; w.t0z = t0[2];
     w.dtx = dt[0]; w.dty = dt[1]; w.dtz = dt[2];
     w.rx = rem[0]; w.ry = rem[1]; w.rz = rem[2];
+    clip_to_budgets(w);
     return w;
 }
 
 // Index of the current voxel as the walk steps: the linear index
 // ix + nx (iy + ny iz), stepped by +-1, +-nx, +-nx ny.
 struct LinearIndex {
+    static constexpr bool kBudgetTests = true;
     int j, sx, sy, sz;
     __device__ __forceinline__ explicit LinearIndex(const Walk& w) : j(w.j0), sx(w.sxl), sy(w.syl), sz(w.szl) {}
     __device__ __forceinline__ int get() const { return j; }
@@ -380,6 +400,7 @@ __device__ __forceinline__ int brick_index(int ix, int iy, int iz, int bx, int b
 // two alternate along an axis, so each axis keeps the delta of its next step and
 // the sum of both, and a step swaps the delta for sum - delta.
 struct BrickIndex {
+    static constexpr bool kBudgetTests = false;
     int q, dx, dy, dz, ax, ay, az;
     __device__ __forceinline__ static void axis(int bit, int dir, int unit, int stride, int& d, int& a)
     {
@@ -426,7 +447,6 @@ __device__ __forceinline__ void walk_index(const GridDev& g, const TailF& tail, 
                                            Visit&& visit)
 {
     if (!w.valid) return;
-    const float inf = __int_as_float(0x7f800000);
     float mx = 0.f, my = 0.f, mz = 0.f;
     float tx = w.t0x, ty = w.t0y, tz = w.t0z;
     float tau = w.tau_in;
@@ -462,12 +482,20 @@ __device__ __forceinline__ void walk_index(const GridDev& g, const TailF& tail, 
         mx += bx ? 1.f : 0.f;
         my += by ? 1.f : 0.f;
         mz += bz ? 1.f : 0.f;
-        const float nx_ = mx < w.rx ? fmaf(mx, w.dtx, w.t0x) : inf;
-        const float ny_ = my < w.ry ? fmaf(my, w.dty, w.t0y) : inf;
-        const float nz_ = mz < w.rz ? fmaf(mz, w.dtz, w.t0z) : inf;
-        tx = bx ? nx_ : tx;
-        ty = by ? ny_ : ty;
-        tz = bz ? nz_ : tz;
+        if constexpr (Index::kBudgetTests) {
+            // an axis past its budget gets no further crossing (redundant with the
+            // clip of tau_out; measured faster in the linear-layout pass)
+            const float inf = __int_as_float(0x7f800000);
+            tx = bx ? (mx < w.rx ? fmaf(mx, w.dtx, w.t0x) : inf) : tx;
+            ty = by ? (my < w.ry ? fmaf(my, w.dty, w.t0y) : inf) : ty;
+            tz = bz ? (mz < w.rz ? fmaf(mz, w.dtz, w.t0z) : inf) : tz;
+        } else {
+            // no budget test: tau_out was clipped to the first crossing past each
+            // axis's budget (clip_to_budgets), so the walk ends before it
+            tx = bx ? fmaf(mx, w.dtx, w.t0x) : tx;
+            ty = by ? fmaf(my, w.dty, w.t0y) : ty;
+            tz = bz ? fmaf(mz, w.dtz, w.t0z) : tz;
+        }
     }
 }
 

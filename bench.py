@@ -26,12 +26,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "TOF-MLEM events x iterations / s (full-body, 146M events, 150x150x600 @ 4 mm)"
 # Per event of the fused pass, from one ncu capture each on 8 M full-body events (cell and
-# direction order, 128 threads, series masses through h^4, walk in sigma units), by image
+# direction order, 128 threads, series masses through h^4, walk in sigma units; the brick
+# walk with tau_out clipped to the crossing budgets), by image
 # layout (0 linear, 1 2x2x2-brick copies): DRAM bytes (dram__bytes_read.sum +
 # dram__bytes_write.sum) and L2 requests (lts__t_requests_srcunit_tex_op_red.sum +
 # lts__t_requests_srcunit_tex_op_read.sum)
 NCU_PER_EVENT = {0: {"dram_bytes": 49.2, "l2_requests": 52.70},
-                 1: {"dram_bytes": 47.75, "l2_requests": 39.76}}
+                 1: {"dram_bytes": 47.78, "l2_requests": 39.71}}
 # algorithmic FP32 operations per Siddon piece: ~25 for the step and the two
 # accumulations plus ~20 for the Gaussian mass of the piece
 ALU_OPS_PER_PIECE = 45.0

@@ -486,9 +486,12 @@ __device__ __forceinline__ void walk_index(const GridDev& g, const TailF& tail, 
             // an axis past its budget gets no further crossing (redundant with the
             // clip of tau_out; measured faster in the linear-layout pass)
             const float inf = __int_as_float(0x7f800000);
-            tx = bx ? (mx < w.rx ? fmaf(mx, w.dtx, w.t0x) : inf) : tx;
-            ty = by ? (my < w.ry ? fmaf(my, w.dty, w.t0y) : inf) : ty;
-            tz = bz ? (mz < w.rz ? fmaf(mz, w.dtz, w.t0z) : inf) : tz;
+            const float nx_ = mx < w.rx ? fmaf(mx, w.dtx, w.t0x) : inf;
+            const float ny_ = my < w.ry ? fmaf(my, w.dty, w.t0y) : inf;
+            const float nz_ = mz < w.rz ? fmaf(mz, w.dtz, w.t0z) : inf;
+            tx = bx ? nx_ : tx;
+            ty = by ? ny_ : ty;
+            tz = bz ? nz_ : tz;
         } else {
             // no budget test: tau_out was clipped to the first crossing past each
             // axis's budget (clip_to_budgets), so the walk ends before it

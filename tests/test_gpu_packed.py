@@ -38,10 +38,12 @@ def packed_case():
     return g, ev, lors, rec, lam_q, hist_q, lam_f
 
 
-def run(g, lors, events, bf16):
+def run(g, lors, events, bf16, launch=None):
     with B.Context(geometry("tiny"), grid_tuple(g), 300.0) as ctx:
         ctx.sensitivity(lors)
         ctx.set_gather_bf16(bf16)
+        if launch:
+            ctx.set_launch(*launch)
         img = np.zeros(g.n_vox, np.float32)
         cons = np.zeros((5, 2))
         ctx.mlem(events, 5, None, img, cons)
@@ -56,6 +58,20 @@ def test_packed_events_fp32_gather_match_dequantized_oracle(packed_case):
     assert cons[-1, 1] == pytest.approx(cons[-1, 0], rel=1e-5)
     print(f"\npacked FP32-gather: rel L2 vs dequantized oracle {rel_l2(img, lam_q):.2e}, "
           f"vs unquantized FP64 oracle {rel_l2(img, lam_f):.2e}")
+
+
+def test_packed_events_brick_layout_match_dequantized_oracle(packed_case):
+    # packed events over the 2x2x2-brick copies (the layout the autotuner picks for
+    # packed events with FP32 gathers on the full body): the first pass streams the
+    # host events in the linear layout, the later passes run over the bricks
+    g, ev, lors, rec, lam_q, hist_q, lam_f = packed_case
+    img, cons = run(g, lors, B.make_events(rec, packed=True, lattice_mm=synth.LATTICE_MM), False,
+                    launch=(128, 0, 0, 0, 3, 1))
+    assert rel_l2(img, lam_q) <= 1e-4
+    assert max_rel_above(img, lam_q, 0.01) <= 1e-3
+    for k in range(5):
+        assert cons[k, 0] == pytest.approx(hist_q[k][0], abs=0.5)
+        assert cons[k, 1] == pytest.approx(cons[k, 0], rel=1e-5)
 
 
 def test_packed_events_bf16_gather_error_is_bounded(packed_case):
